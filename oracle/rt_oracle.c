@@ -1,0 +1,747 @@
+/*
+ * Reference oracle for one radiative-transfer (RT) step of the M1 moment
+ * method of Rosdahl et al. 2013 (RAMSES-RT), on a uniform Cartesian grid.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, scalar FP64 CPU
+ * statement of what the RT step computes.  Only the test-suite, the package
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or constant with the CUDA library: every
+ * constant below is retyped from the paper.
+ *
+ * Paper map (sections of the paper, equation labels in brackets):
+ *   injection        Sec. 3.1, Eq. (injnum): N += L dt / V
+ *   transport        Sec. 3.2, Eqs. (dUdt), (dUdt_sol), (hll), (glf)
+ *   M1 closure       Sec. 2,   Eqs. (edd2), (eddTens), (Udir)
+ *   thermochemistry  Sec. 3.3 and App. A: Eqs. (SIE photons),
+ *                    (T integration num eq 2), (xhii_update_2),
+ *                    (xhei_update), (xheii_update), (xheiii_update)
+ *   10% rule         Sec. 3.3.1 and App. A, task 5
+ *   OTSA             Sec. 3.3.2 (case B rates, no recombination photons)
+ *   Courant step     Sec. 4.1, Eq. (dt_courant)
+ *   rate fits        appendix "Interaction rate coefficients"
+ *
+ * Readings where the paper is silent or garbled are marked READING below.
+ *
+ * Parity pins: every function here is pinned by a CPU test against the
+ * paper's printed numbers, closed forms or invariants, except the cooling
+ * fits that have no printed value (see tests/test_oracle_rates.py); those
+ * are pinned only through derivative consistency and the relation
+ * eta_HeII = k_B T alpha_HeII printed beside them ("parity partially
+ * unpinned" for the remaining cooling fits).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "rt_oracle.h"
+
+/* ---- physical constants (cgs), retyped from the paper / CODATA ---- */
+static const double K_BOLTZ = 1.380649e-16;    /* erg/K */
+static const double M_H = 1.67262192e-24;      /* g, "m_H the proton mass" (App. A) */
+static const double EV = 1.602176634e-12;      /* erg */
+static const double GAMMA_AD = 5.0 / 3.0;      /* App. A, ratio of specific heats */
+/* ionisation energies, table "Photoionization energies" */
+static const double EPS_ION_EV[3] = {13.60, 24.59, 54.42};
+
+/* READING: floors frozen for the 10% rule denominators and the state. */
+static const double FLOOR_N = 1e-30;        /* photons / cm^3 */
+static const double XHII_MIN = 1e-6;        /* Sec. 6 test 2: default minimum x_HII */
+static const double NE_FLOOR_FRAC = 1e-6;   /* n_e floor = 1e-6 n_H */
+static const double T_FLOOR = 1.0;          /* K */
+
+/* =====================================================================
+ * Rate coefficients, appendix "Interaction rate coefficients".
+ * Every fit returns its value and its derivative with respect to T.
+ * ===================================================================== */
+
+/* Cen (1992) form A sqrt(T) (1+sqrt(T/1e5))^-1 exp(-T0/T); used for beta
+ * (collisional ionisation) and zeta (collisional ionisation cooling). */
+static void fit_cen(double A, double T0, double T, double *v, double *dv)
+{
+    double sq = sqrt(T);
+    double q = sqrt(T / 1e5);
+    double e = exp(-T0 / T);
+    double val = A * sq / (1.0 + q) * e;
+    /* d ln v / dT = 1/(2T) - q/(2T(1+q)) + T0/T^2 */
+    double dl = 0.5 / T - q / (2.0 * T * (1.0 + q)) + T0 / (T * T);
+    *v = val;
+    *dv = val * dl;
+}
+
+/* Hui & Gnedin (1997) form A lam^p / (1 + (lam/l0)^r)^s, lam = T1/T. */
+static void fit_hg(double A, double T1, double p, double l0, double r, double s,
+                   double T, double *v, double *dv)
+{
+    double lam = T1 / T;
+    double w = pow(lam / l0, r);
+    double val = A * pow(lam, p) / pow(1.0 + w, s);
+    /* d ln v / d lam = p/lam - s r w / (lam (1+w));  d lam/dT = -lam/T */
+    double dl_dlam = p / lam - s * r * w / (lam * (1.0 + w));
+    *v = val;
+    *dv = val * dl_dlam * (-lam / T);
+}
+
+/* Pure power law A lam^p, lam = T1/T. */
+static void fit_pow(double A, double T1, double p, double T, double *v, double *dv)
+{
+    double lam = T1 / T;
+    double val = A * pow(lam, p);
+    *v = val;
+    *dv = val * (-p / T);
+}
+
+void oracle_rates(double T, double a_exp, int case_b, double *r, double *dr)
+{
+    double v, dv;
+    /* collisional ionisation rates beta [cm^3/s] */
+    fit_cen(5.85e-11, 157809.1, T, &r[R_BETA_HI], &dr[R_BETA_HI]);
+    fit_cen(2.38e-11, 285335.4, T, &r[R_BETA_HEI], &dr[R_BETA_HEI]);
+    fit_cen(5.68e-12, 631515.0, T, &r[R_BETA_HEII], &dr[R_BETA_HEII]);
+
+    /* recombination rates alpha [cm^3/s]; OTSA replaces case A by case B */
+    if (case_b) {
+        fit_hg(2.753e-14, 315614.0, 1.5, 2.74, 0.407, 2.242, T, &r[R_ALPHA_HII], &dr[R_ALPHA_HII]);
+        fit_pow(1.26e-14, 570670.0, 0.75, T, &r[R_ALPHA_HEII], &dr[R_ALPHA_HEII]);
+        fit_hg(5.506e-14, 1263030.0, 1.5, 2.74, 0.407, 2.242, T, &r[R_ALPHA_HEIII], &dr[R_ALPHA_HEIII]);
+    } else {
+        fit_hg(1.269e-13, 315614.0, 1.503, 0.522, 0.47, 1.923, T, &r[R_ALPHA_HII], &dr[R_ALPHA_HII]);
+        fit_pow(3e-14, 570670.0, 0.654, T, &r[R_ALPHA_HEII], &dr[R_ALPHA_HEII]);
+        fit_hg(2.538e-13, 1263030.0, 1.503, 0.522, 0.47, 1.923, T, &r[R_ALPHA_HEIII], &dr[R_ALPHA_HEIII]);
+    }
+
+    /* collisional ionisation cooling zeta [erg cm^3/s] */
+    fit_cen(1.27e-21, 157809.1, T, &r[R_ZETA_HI], &dr[R_ZETA_HI]);
+    fit_cen(9.38e-22, 285335.4, T, &r[R_ZETA_HEI], &dr[R_ZETA_HEI]);
+    fit_cen(4.95e-22, 631515.0, T, &r[R_ZETA_HEII], &dr[R_ZETA_HEII]);
+
+    /* recombination cooling eta [erg cm^3/s]: A T lam^p/(1+(lam/l0)^r)^s */
+    if (case_b) {
+        fit_hg(3.435e-30, 315614.0, 1.97, 2.25, 0.376, 3.72, T, &v, &dv);
+        r[R_ETA_HII] = T * v;
+        dr[R_ETA_HII] = v + T * dv;
+        fit_hg(8.0 * 3.435e-30, 1263030.0, 1.97, 2.25, 0.376, 3.72, T, &v, &dv);
+        r[R_ETA_HEIII] = T * v;
+        dr[R_ETA_HEIII] = v + T * dv;
+    } else {
+        fit_hg(1.778e-29, 315614.0, 1.965, 0.541, 0.502, 2.697, T, &v, &dv);
+        r[R_ETA_HII] = T * v;
+        dr[R_ETA_HII] = v + T * dv;
+        fit_hg(8.0 * 1.778e-29, 1263030.0, 1.965, 0.541, 0.502, 2.697, T, &v, &dv);
+        r[R_ETA_HEIII] = T * v;
+        dr[R_ETA_HEIII] = v + T * dv;
+    }
+    /* eta_HeII = k_B T alpha_HeII (same case as alpha) */
+    r[R_ETA_HEII] = K_BOLTZ * T * r[R_ALPHA_HEII];
+    dr[R_ETA_HEII] = K_BOLTZ * (r[R_ALPHA_HEII] + T * dr[R_ALPHA_HEII]);
+
+    /* collisional excitation cooling psi [erg cm^3/s] */
+    {
+        double q = sqrt(T / 1e5);
+        double e = exp(-118348.0 / T);
+        double val = 7.5e-19 / (1.0 + q) * e;
+        r[R_PSI_HI] = val;
+        dr[R_PSI_HI] = val * (-q / (2.0 * T * (1.0 + q)) + 118348.0 / (T * T));
+        e = exp(-473638.0 / T);
+        val = 5.54e-17 * pow(T, -0.397) / (1.0 + q) * e;
+        r[R_PSI_HEII] = val;
+        dr[R_PSI_HEII] = val * (-0.397 / T - q / (2.0 * T * (1.0 + q)) + 473638.0 / (T * T));
+    }
+
+    /* bremsstrahlung theta [erg cm^3/s]; the cooling sum weights it by
+     * (n_HII + n_HeII + 4 n_HeIII) */
+    r[R_THETA] = 1.42e-27 * sqrt(T);
+    dr[R_THETA] = 0.5 * r[R_THETA] / T;
+
+    /* Compton varpi(T, a) [erg/s], multiplies n_e; signed (heats below T_cmb) */
+    {
+        double Tg = 2.727 / a_exp;
+        double Tg4 = Tg * Tg * Tg * Tg;
+        r[R_VARPI] = 1.017e-37 * Tg4 * (T - Tg);
+        dr[R_VARPI] = 1.017e-37 * Tg4;
+    }
+
+    /* dielectronic recombination cooling omega_HeII [erg cm^3/s] */
+    {
+        double e1 = exp(-470000.0 / T);
+        double e2 = exp(-94000.0 / T);
+        double base = 1.24e-13 * pow(T, -1.5) * e1;
+        double val = base * (1.0 + 0.3 * e2);
+        r[R_OMEGA_HEII] = val;
+        dr[R_OMEGA_HEII] = val * (-1.5 / T + 470000.0 / (T * T))
+                         + base * 0.3 * e2 * 94000.0 / (T * T);
+    }
+}
+
+/* =====================================================================
+ * M1 closure, Sec. 2, Eqs. (edd2), (eddTens), (Udir)
+ * ===================================================================== */
+double oracle_chi(double f)
+{
+    return (3.0 + 4.0 * f * f) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f * f));
+}
+
+/* Eddington tensor D (row-major 3x3) of a cell with photon density N and
+ * flux F, at light speed c.  READING: f := 0 when N <= 0 or F = 0 (the
+ * direction is then irrelevant), and f is clamped to 1 in chi. */
+void oracle_eddington(double c, double N, const double F[3], double D[9],
+                      double *f_out, double n_out[3])
+{
+    double Fmag = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    double f = 0.0;
+    double n[3] = {0.0, 0.0, 0.0};
+    if (N > 0.0 && Fmag > 0.0) {
+        f = Fmag / (c * N);
+        if (f > 1.0) f = 1.0;
+        n[0] = F[0] / Fmag;
+        n[1] = F[1] / Fmag;
+        n[2] = F[2] / Fmag;
+    }
+    double chi = oracle_chi(f);
+    double a = 0.5 * (1.0 - chi);
+    double b = 0.5 * (3.0 * chi - 1.0);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            D[3 * i + j] = (i == j ? a : 0.0) + b * n[i] * n[j];
+    if (f_out) *f_out = f;
+    if (n_out) { n_out[0] = n[0]; n_out[1] = n[1]; n_out[2] = n[2]; }
+}
+
+/* Bilinear lookup of the HLL eigenvalue table (lambda_min, lambda_max in
+ * units of c) at reduced flux f and direction cosine mu.  Table layout:
+ * [nf][nmu][2], f_k = k/(nf-1), mu_j = -1 + 2j/(nmu-1). */
+void oracle_hll_lookup(const double *tab, int nf, int nmu, double f, double mu,
+                       double *lmin, double *lmax)
+{
+    double fx = f * (double)(nf - 1);
+    int k = (int)floor(fx);
+    if (k < 0) k = 0;
+    if (k > nf - 2) k = nf - 2;
+    double wf = fx - (double)k;
+    double mx = (mu + 1.0) * 0.5 * (double)(nmu - 1);
+    int j = (int)floor(mx);
+    if (j < 0) j = 0;
+    if (j > nmu - 2) j = nmu - 2;
+    double wm = mx - (double)j;
+    for (int c = 0; c < 2; c++) {
+        double t00 = tab[((size_t)k * nmu + j) * 2 + c];
+        double t01 = tab[((size_t)k * nmu + j + 1) * 2 + c];
+        double t10 = tab[((size_t)(k + 1) * nmu + j) * 2 + c];
+        double t11 = tab[((size_t)(k + 1) * nmu + j + 1) * 2 + c];
+        double lo = t00 + wm * (t01 - t00);
+        double hi = t10 + wm * (t11 - t10);
+        double v = lo + wf * (hi - lo);
+        if (c == 0) *lmin = v; else *lmax = v;
+    }
+}
+
+/* =====================================================================
+ * Transport, Sec. 3.2: explicit first-order Godunov, unsplit in 3-D.
+ * ===================================================================== */
+
+typedef struct {
+    double U[4];      /* N, Fx, Fy, Fz */
+    double P[9];      /* c^2 N D (row-major) */
+    double lmin[3];   /* per direction, times c */
+    double lmax[3];
+} cellq;
+
+static void cell_quantities(const oracle_cfg *cfg, double N, double Fx, double Fy,
+                            double Fz, cellq *q)
+{
+    double F[3] = {Fx, Fy, Fz};
+    double D[9], f, n[3];
+    double c = cfg->cr;
+    oracle_eddington(c, N, F, D, &f, n);
+    q->U[0] = N; q->U[1] = Fx; q->U[2] = Fy; q->U[3] = Fz;
+    for (int i = 0; i < 9; i++) q->P[i] = c * c * N * D[i];
+    for (int d = 0; d < 3; d++) {
+        if (cfg->flux == ORACLE_HLL) {
+            double lo, hi;
+            oracle_hll_lookup(cfg->hll_table, cfg->hll_nf, cfg->hll_nmu, f, n[d], &lo, &hi);
+            q->lmin[d] = lo * c;
+            q->lmax[d] = hi * c;
+        } else {
+            q->lmin[d] = -c;
+            q->lmax[d] = c;
+        }
+    }
+}
+
+/* Directional flux vector of Eq. (dUdt): [F_d, c^2 P_{d,x}, c^2 P_{d,y}, c^2 P_{d,z}]
+ * (here P already carries the c^2). */
+static void dir_flux(const cellq *q, int d, double out[4])
+{
+    out[0] = q->U[1 + d];
+    out[1] = q->P[3 * d + 0];
+    out[2] = q->P[3 * d + 1];
+    out[3] = q->P[3 * d + 2];
+}
+
+/* Intercell flux at the face between left cell l and right cell r along d:
+ * HLL, Eq. (hll), or GLF, Eq. (glf) (HLL with lambda = -c, +c). */
+static void face_flux(const oracle_cfg *cfg, const cellq *l, const cellq *r, int d,
+                      double out[4])
+{
+    double Fl[4], Fr[4];
+    dir_flux(l, d, Fl);
+    dir_flux(r, d, Fr);
+    if (cfg->flux == ORACLE_HLL) {
+        double lp = fmax(0.0, fmax(l->lmax[d], r->lmax[d]));
+        double lm = fmin(0.0, fmin(l->lmin[d], r->lmin[d]));
+        if (lp - lm > 0.0) {
+            for (int k = 0; k < 4; k++)
+                out[k] = (lp * Fl[k] - lm * Fr[k] + lp * lm * (r->U[k] - l->U[k])) / (lp - lm);
+        } else {
+            /* READING: both wave speeds vanish only for f = 1 beams parallel
+             * to the face, where both fluxes are zero. */
+            for (int k = 0; k < 4; k++) out[k] = 0.5 * (Fl[k] + Fr[k]);
+        }
+    } else {
+        double c = cfg->cr;
+        for (int k = 0; k < 4; k++)
+            out[k] = 0.5 * (Fl[k] + Fr[k]) - 0.5 * c * (r->U[k] - l->U[k]);
+    }
+}
+
+static size_t cidx(const oracle_cfg *cfg, int i, int j, int k)
+{
+    return ((size_t)k * cfg->ny + j) * cfg->nx + i;
+}
+
+/* Ghost state beyond a boundary face of direction d.  READING (no boundary
+ * conditions are stated for the tests): outflow = zero-gradient copy,
+ * reflect = copy with the normal flux component negated, periodic = wrap. */
+static void ghost_state(int bc, int d, const double Uin[4], const double Uwrap[4],
+                        double Ug[4])
+{
+    if (bc == ORACLE_BC_PERIODIC) {
+        for (int k = 0; k < 4; k++) Ug[k] = Uwrap[k];
+    } else {
+        for (int k = 0; k < 4; k++) Ug[k] = Uin[k];
+        if (bc == ORACLE_BC_REFLECT) Ug[1 + d] = -Ug[1 + d];
+    }
+}
+
+/* One transport step of one photon group in place.  N: [cells], F: [3][cells].
+ * Returns the outflow (photons, outward positive) through the box faces. */
+static double transport_group(const oracle_cfg *cfg, double dt, double *N, double *F)
+{
+    const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
+    const size_t nc = (size_t)nx * ny * nz;
+    const int dims[3] = {nx, ny, nz};
+    const double dx = cfg->dx;
+    double *U0 = (double *)malloc(sizeof(double) * 4 * nc);
+    cellq *Q = (cellq *)malloc(sizeof(cellq) * nc);
+    double *acc = (double *)calloc(4 * nc, sizeof(double));
+    double outflow = 0.0;
+
+    for (size_t c = 0; c < nc; c++) {
+        U0[4 * c + 0] = N[c];
+        U0[4 * c + 1] = F[c];
+        U0[4 * c + 2] = F[nc + c];
+        U0[4 * c + 3] = F[2 * nc + c];
+    }
+#pragma omp parallel for schedule(static) if (cfg->nthreads > 1) num_threads(cfg->nthreads > 0 ? cfg->nthreads : 1)
+    for (long c = 0; c < (long)nc; c++)
+        cell_quantities(cfg, U0[4 * c], U0[4 * c + 1], U0[4 * c + 2], U0[4 * c + 3], &Q[c]);
+
+    /* face loop: for every direction d and every face between cell m-1 and m
+     * (m = 0 .. n_d, with ghosts at both ends), flux leaves the left cell and
+     * enters the right cell, Eq. (dUdt_sol). */
+    for (int d = 0; d < 3; d++) {
+        int nd = dims[d];
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    int ijk[3] = {i, j, k};
+                    int m = ijk[d];
+                    /* each cell handles its low face; the last cell also
+                     * handles its high face */
+                    for (int side = 0; side < 2; side++) {
+                        if (side == 1 && m != nd - 1) continue;
+                        const cellq *L, *R;
+                        cellq G;
+                        int face_m = (side == 0) ? m : m + 1; /* face index 0..nd */
+                        size_t cself = cidx(cfg, i, j, k);
+                        if (face_m == 0 || face_m == nd) {
+                            int lo = (face_m == 0);
+                            int bc = cfg->bc[2 * d + (lo ? 0 : 1)];
+                            int w[3] = {i, j, k};
+                            w[d] = lo ? nd - 1 : 0;
+                            size_t cw = cidx(cfg, w[0], w[1], w[2]);
+                            double Ug[4];
+                            ghost_state(bc, d, &U0[4 * cself], &U0[4 * cw], Ug);
+                            cell_quantities(cfg, Ug[0], Ug[1], Ug[2], Ug[3], &G);
+                            if (lo) { L = &G; R = &Q[cself]; }
+                            else    { L = &Q[cself]; R = &G; }
+                            double fl[4];
+                            face_flux(cfg, L, R, d, fl);
+                            double sgn = lo ? -1.0 : 1.0; /* outward normal */
+                            if (bc != ORACLE_BC_PERIODIC)
+                                outflow += sgn * fl[0] * dx * dx * dt;
+                            for (int q = 0; q < 4; q++) {
+                                if (lo) acc[4 * cself + q] += fl[q];
+                                else    acc[4 * cself + q] -= fl[q];
+                            }
+                        } else {
+                            int w[3] = {i, j, k};
+                            w[d] = m - 1;
+                            size_t cl = cidx(cfg, w[0], w[1], w[2]);
+                            double fl[4];
+                            face_flux(cfg, &Q[cl], &Q[cself], d, fl);
+                            for (int q = 0; q < 4; q++) {
+                                acc[4 * cl + q] -= fl[q];
+                                acc[4 * cself + q] += fl[q];
+                            }
+                        }
+                    }
+                }
+    }
+
+    /* U^{n+1} = U^n + dt/dx (sum of in-fluxes - out-fluxes), then the
+     * READING: realisability |F| <= c N restored by rescaling F (it only
+     * acts at rounding level for CFL <= 1), and N >= 0. */
+    const double c = cfg->cr;
+    for (size_t q = 0; q < nc; q++) {
+        double Nn = U0[4 * q + 0] + dt / dx * acc[4 * q + 0];
+        double fx = U0[4 * q + 1] + dt / dx * acc[4 * q + 1];
+        double fy = U0[4 * q + 2] + dt / dx * acc[4 * q + 2];
+        double fz = U0[4 * q + 3] + dt / dx * acc[4 * q + 3];
+        if (Nn < 0.0) { Nn = 0.0; fx = fy = fz = 0.0; }
+        double Fm = sqrt(fx * fx + fy * fy + fz * fz);
+        if (Fm > c * Nn) {
+            double s = (Fm > 0.0) ? c * Nn / Fm : 0.0;
+            fx *= s; fy *= s; fz *= s;
+        }
+        N[q] = Nn;
+        F[q] = fx;
+        F[nc + q] = fy;
+        F[2 * nc + q] = fz;
+    }
+    free(U0);
+    free(Q);
+    free(acc);
+    return outflow;
+}
+
+/* =====================================================================
+ * Thermochemistry, Sec. 3.3 and App. A
+ * ===================================================================== */
+
+static double mu_of(double X, double x, double y2, double y3)
+{
+    double Y = 1.0 - X;
+    return 1.0 / (X * (1.0 + x) + 0.25 * Y * (1.0 + y2 + 2.0 * y3));
+}
+
+static double ne_of(double nH, double nHe, double x, double y2, double y3)
+{
+    return x * nH + (y2 + 2.0 * y3) * nHe;
+}
+
+static void note_margin(double v, double thr, double *margin)
+{
+    double m = fabs(v - thr) / thr;
+    if (m < *margin) *margin = m;
+}
+
+/* One thermo_step of App. A over sub-step h.  On success returns 1, fills
+ * the new state and *maxrel (largest relative change of N_i, T/mu, x_HII,
+ * n_e).  Returns 0 if the 10% rule is broken (caller halves h). */
+static int thermo_step(const oracle_cfg *cfg, double h, double nH,
+                       const double *s0 /* x, y2, y3, T */, const double *N0,
+                       double *s1, double *N1, double *Fscale, double *absorbed,
+                       double *maxrel, double *margin, int fixed_photons)
+{
+    const int G = cfg->G;
+    const double X = cfg->X, Y = 1.0 - X;
+    const double nHe = (Y > 0.0) ? nH * Y / (4.0 * X) : 0.0;
+    const double cr = cfg->cr;
+    const int case_b = cfg->otsa ? 1 : 0;
+    double x = s0[0], y2 = s0[1], y3 = s0[2], T = s0[3];
+    double rel_max = 0.0;
+
+    /* backwards-in-time absorber densities */
+    double nHI = nH * (1.0 - x);
+    double nHeI = nHe * (1.0 - y2 - y3);
+    double nHeII = nHe * y2;
+    double nHeIII = nHe * y3;
+    double nHII = nH * x;
+    double ne = ne_of(nH, nHe, x, y2, y3);
+
+    /* task 1: photon density and flux, Eq. (SIE photons); OTSA => C_i = 0 */
+    for (int i = 0; i < G; i++) {
+        double Di = cr * (cfg->sigN[3 * i + 0] * nHI + cfg->sigN[3 * i + 1] * nHeI
+                          + cfg->sigN[3 * i + 2] * nHeII);
+        if (fixed_photons) {
+            N1[i] = N0[i];
+            Fscale[i] = 1.0;
+            absorbed[i] = 0.0;
+            continue;
+        }
+        N1[i] = N0[i] / (1.0 + h * Di);
+        Fscale[i] = 1.0 / (1.0 + h * Di);
+        double rel = fabs(N1[i] - N0[i]) / fmax(N0[i], FLOOR_N);
+        note_margin(rel, 0.1, margin);
+        if (rel > 0.1) return 0;
+        if (rel > rel_max) rel_max = rel;
+        absorbed[i] = h * Di * N1[i];
+    }
+
+    /* photoionisation rates with the forward photon densities */
+    double Gam[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < G; i++)
+        for (int j = 0; j < 3; j++) Gam[j] += cfg->sigN[3 * i + j] * cr * N1[i];
+
+    /* task 2: thermal update, Eqs. (Tmu), (mu), (T integration num eq 2) */
+    double mu = mu_of(X, x, y2, y3);
+    double Tmu = T / mu;
+    double Tmu1 = Tmu;
+    double r[R_COUNT], dr[R_COUNT];
+    if (!cfg->isothermal) {
+        oracle_rates(T, cfg->a_exp, case_b, r, dr);
+        /* photoheating, Eq. (PHeat2), forward N, backward n_j */
+        const double nj[3] = {nHI, nHeI, nHeII};
+        double Hh = 0.0;
+        for (int j = 0; j < 3; j++) {
+            double sj = 0.0;
+            for (int i = 0; i < G; i++)
+                sj += cr * N1[i] * (cfg->egy[i] * cfg->sigE[3 * i + j]
+                                    - EPS_ION_EV[j] * EV * cfg->sigN[3 * i + j]);
+            Hh += nj[j] * sj;
+        }
+        /* primordial cooling, Eq. (rate_cooling); READING: the fits are
+         * magnitudes and cooling counts negative, Lambda = H + L. */
+        double Lsum = (r[R_ZETA_HI] + r[R_PSI_HI]) * ne * nHI
+                    + r[R_ZETA_HEI] * ne * nHeI
+                    + (r[R_ZETA_HEII] + r[R_PSI_HEII] + r[R_ETA_HEII] + r[R_OMEGA_HEII]) * ne * nHeII
+                    + r[R_ETA_HII] * ne * nHII
+                    + r[R_ETA_HEIII] * ne * nHeIII
+                    + r[R_THETA] * ne * (nHII + nHeII + 4.0 * nHeIII)
+                    + r[R_VARPI] * ne;
+        double dLsum = (dr[R_ZETA_HI] + dr[R_PSI_HI]) * ne * nHI
+                     + dr[R_ZETA_HEI] * ne * nHeI
+                     + (dr[R_ZETA_HEII] + dr[R_PSI_HEII] + dr[R_ETA_HEII] + dr[R_OMEGA_HEII]) * ne * nHeII
+                     + dr[R_ETA_HII] * ne * nHII
+                     + dr[R_ETA_HEIII] * ne * nHeIII
+                     + dr[R_THETA] * ne * (nHII + nHeII + 4.0 * nHeIII)
+                     + dr[R_VARPI] * ne;
+        double Lam = Hh - Lsum;
+        double dLam_dTmu = mu * (-dLsum);   /* heating has no T dependence */
+        /* K = (gamma-1) m_H / (rho k_B), rho = n_H m_H / X */
+        double rho = nH * M_H / X;
+        double K = (GAMMA_AD - 1.0) * M_H / (rho * K_BOLTZ);
+        double dT = Lam * K * h / (1.0 - dLam_dTmu * K * h);
+        Tmu1 = Tmu + dT;
+        double rel = fabs(dT) / Tmu;
+        note_margin(rel, 0.1, margin);
+        if (rel > 0.1) return 0;
+        double first = fabs(K * Lam * h) / Tmu;
+        note_margin(first, 0.1, margin);
+        if (first > 0.1) return 0;
+        if (rel > rel_max) rel_max = rel;
+    }
+
+    /* task 3: x_HII update, Eq. (xhii_update_2), rates at T = Tmu' mu(x(t)) */
+    double T1 = cfg->isothermal ? T : Tmu1 * mu;
+    oracle_rates(T1, cfg->a_exp, case_b, r, dr);
+    double Cc = r[R_BETA_HI] * ne + Gam[0];
+    double Dd = r[R_ALPHA_HII] * ne;
+    double dC = nH * r[R_BETA_HI];
+    double dD = nH * r[R_ALPHA_HII];
+    if (!cfg->isothermal) {
+        dC -= ne * Tmu1 * mu * mu * X * dr[R_BETA_HI];
+        dD -= ne * Tmu1 * mu * mu * X * dr[R_ALPHA_HII];
+    }
+    double J = dC - (Cc + Dd) - x * (dC + dD);
+    double xdot = Cc - x * (Cc + Dd);
+    double x1 = x + h * xdot / (1.0 - J * h);
+    if (x1 < XHII_MIN) x1 = XHII_MIN;
+    if (x1 > 1.0) x1 = 1.0;
+    {
+        double xden = fmax(x, XHII_MIN);
+        double rel = fabs(x1 - x) / xden;
+        note_margin(rel, 0.1, margin);
+        if (rel > 0.1) return 0;
+        double first = fabs(xdot) * h / xden;
+        note_margin(first, 0.1, margin);
+        if (first > 0.1) return 0;
+        if (rel > rel_max) rel_max = rel;
+    }
+
+    /* task 4: helium, Eqs. (xhei_update), (xheii_update), (xheiii_update).
+     * n_e and mu are recomputed from the forward abundances before each
+     * update; rates are taken at T = Tmu' mu. */
+    double y2n = y2, y3n = y3;
+    if (Y > 0.0) {
+        double xHeI = 1.0 - y2 - y3;
+        double ne2 = ne_of(nH, nHe, x1, y2, y3);
+        double mu2 = mu_of(X, x1, y2, y3);
+        double T2 = cfg->isothermal ? T : Tmu1 * mu2;
+        oracle_rates(T2, cfg->a_exp, case_b, r, dr);
+        /* READING: photoionisation destroys HeI, so D = beta ne + sum sigma c N */
+        double C1 = y2 * r[R_ALPHA_HEII] * ne2;
+        double D1 = r[R_BETA_HEI] * ne2 + Gam[1];
+        double xHeI1 = (xHeI + C1 * h) / (1.0 + D1 * h);
+
+        double C2 = xHeI1 * (r[R_BETA_HEI] * ne2 + Gam[1]) + y3 * r[R_ALPHA_HEIII] * ne2;
+        double D2 = r[R_BETA_HEII] * ne2 + r[R_ALPHA_HEII] * ne2 + Gam[2];
+        y2n = (y2 + C2 * h) / (1.0 + D2 * h);
+
+        double ne3 = ne_of(nH, nHe, x1, y2n, y3);
+        double mu3 = mu_of(X, x1, y2n, y3);
+        double T3 = cfg->isothermal ? T : Tmu1 * mu3;
+        oracle_rates(T3, cfg->a_exp, case_b, r, dr);
+        double C3 = y2n * (r[R_BETA_HEII] * ne3 + Gam[2]);
+        double D3 = r[R_ALPHA_HEIII] * ne3;
+        y3n = (y3 + C3 * h) / (1.0 + D3 * h);
+
+        /* conservation: lower the largest fraction (x_HeI largest => no
+         * stored change), then clamp to [0, 1] */
+        if (y2n >= xHeI1 && y2n >= y3n) {
+            y2n = 1.0 - xHeI1 - y3n;
+        } else if (y3n >= xHeI1 && y3n > y2n) {
+            y3n = 1.0 - xHeI1 - y2n;
+        }
+        if (y2n < 0.0) y2n = 0.0;
+        if (y2n > 1.0) y2n = 1.0;
+        if (y3n < 0.0) y3n = 0.0;
+        if (y3n > 1.0) y3n = 1.0;
+    }
+
+    /* final 10% check on the electron density */
+    {
+        double ne1 = ne_of(nH, nHe, x1, y2n, y3n);
+        double rel = fabs(ne1 - ne) / fmax(ne, NE_FLOOR_FRAC * nH);
+        note_margin(rel, 0.1, margin);
+        if (rel > 0.1) return 0;
+        if (rel > rel_max) rel_max = rel;
+    }
+
+    double T1fin = cfg->isothermal ? T : Tmu1 * mu_of(X, x1, y2n, y3n);
+    if (T1fin < T_FLOOR) T1fin = T_FLOOR;
+    s1[0] = x1;
+    s1[1] = y2n;
+    s1[2] = y3n;
+    s1[3] = T1fin;
+    *maxrel = rel_max;
+    return 1;
+}
+
+/* Sub-cycled thermochemistry of one cell over dt_rt, Sec. 3.3.1 and App. A
+ * task 5: first try dt_TC = dt_rt; halve and redo on a broken 10% rule;
+ * double the next dt_TC after a sub-step whose largest change is < 5%. */
+int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s,
+                       double *N, double *F /* [G][3] */, int fixed_photons,
+                       int *attempts_out, double *absorbed_out, double *margin_out)
+{
+    const int G = cfg->G;
+    double N1[ORACLE_MAXG], Fs[ORACLE_MAXG], ab[ORACLE_MAXG], s1[4];
+    double t_left = dt_rt, dt_tc = dt_rt;
+    double margin = 1e300;
+    int attempts = 0;
+    int status = 0;
+    for (int i = 0; i < G; i++) absorbed_out[i] = 0.0;
+    while (t_left > 0.0) {
+        if (attempts >= cfg->max_subcycles) { status = ORACLE_ESUBCYCLE; break; }
+        double h = (dt_tc < t_left) ? dt_tc : t_left;
+        double maxrel = 0.0;
+        attempts++;
+        int ok = thermo_step(cfg, h, nH, s, N, s1, N1, Fs, ab, &maxrel, &margin, fixed_photons);
+        if (!ok) { dt_tc = 0.5 * h; continue; }
+        for (int q = 0; q < 4; q++) s[q] = s1[q];
+        for (int i = 0; i < G; i++) {
+            N[i] = N1[i];
+            F[3 * i + 0] *= Fs[i];
+            F[3 * i + 1] *= Fs[i];
+            F[3 * i + 2] *= Fs[i];
+            absorbed_out[i] += ab[i];
+        }
+        t_left = (h == t_left) ? 0.0 : t_left - h;
+        note_margin(maxrel, 0.05, &margin);
+        dt_tc = (maxrel < 0.05) ? 2.0 * h : h;
+    }
+    if (attempts_out) *attempts_out = attempts;
+    if (margin_out) *margin_out = margin;
+    return status;
+}
+
+/* =====================================================================
+ * Full RT step: injection -> transport -> thermochemistry (Sec. 3)
+ * ===================================================================== */
+double oracle_courant_dt(double cfl, double dx, double cr)
+{
+    return cfl * dx / (3.0 * cr);   /* Eq. (dt_courant) */
+}
+
+int oracle_step(const oracle_cfg *cfg, double dt, const double *nH, double *xHII,
+                double *xHeII, double *xHeIII, double *T, double *N, double *F,
+                int nsrc, const int32_t *src_ijk, const double *src_L,
+                double *budget, int32_t *subcycles, double *margins)
+{
+    const int G = cfg->G;
+    const size_t nc = (size_t)cfg->nx * cfg->ny * cfg->nz;
+    const double V = cfg->dx * cfg->dx * cfg->dx;
+    int status = 0;
+    if (G < 1 || G > ORACLE_MAXG) return ORACLE_EINVAL;
+    for (int i = 0; i < 4 * G; i++) budget[i] = 0.0;
+
+    /* 1. injection, Eq. (injnum) with point sources of fixed luminosity */
+    for (int s = 0; s < nsrc; s++) {
+        size_t c = cidx(cfg, src_ijk[3 * s], src_ijk[3 * s + 1], src_ijk[3 * s + 2]);
+        for (int i = 0; i < G; i++) {
+            N[(size_t)i * nc + c] += src_L[(size_t)s * G + i] * dt / V;
+            budget[4 * i + 3] += src_L[(size_t)s * G + i] * dt;
+        }
+    }
+
+    /* 2. transport, every group independently */
+    for (int i = 0; i < G; i++)
+        budget[4 * i + 2] = transport_group(cfg, dt, N + (size_t)i * nc, F + (size_t)3 * i * nc);
+
+    /* 3. thermochemistry, each cell independently */
+    if (!cfg->skip_thermo) {
+        double *absorbed = (double *)calloc(nc * G, sizeof(double));
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) if (cfg->nthreads > 1) num_threads(cfg->nthreads > 0 ? cfg->nthreads : 1) reduction(| : bad)
+        for (long c = 0; c < (long)nc; c++) {
+            double s[4] = {xHII[c], xHeII[c], xHeIII[c], T[c]};
+            double Nc[ORACLE_MAXG], Fc[3 * ORACLE_MAXG], ab[ORACLE_MAXG];
+            for (int i = 0; i < G; i++) {
+                Nc[i] = N[(size_t)i * nc + c];
+                for (int d = 0; d < 3; d++) Fc[3 * i + d] = F[((size_t)3 * i + d) * nc + c];
+            }
+            int att = 0;
+            double mg = 0.0;
+            int st = oracle_thermo_cell(cfg, dt, nH[c], s, Nc, Fc, 0, &att, ab, &mg);
+            if (st) bad = 1;
+            xHII[c] = s[0]; xHeII[c] = s[1]; xHeIII[c] = s[2]; T[c] = s[3];
+            for (int i = 0; i < G; i++) {
+                N[(size_t)i * nc + c] = Nc[i];
+                for (int d = 0; d < 3; d++) F[((size_t)3 * i + d) * nc + c] = Fc[3 * i + d];
+                absorbed[(size_t)i * nc + c] = ab[i];
+            }
+            if (subcycles) subcycles[c] = att;
+            if (margins) margins[c] = mg;
+        }
+        if (bad) status = ORACLE_ESUBCYCLE;
+        for (int i = 0; i < G; i++) {
+            double a = 0.0;
+            for (size_t c = 0; c < nc; c++) a += absorbed[(size_t)i * nc + c];
+            budget[4 * i + 1] = a * V;
+        }
+        free(absorbed);
+    }
+
+    /* 4. budget: photons left in the box */
+    for (int i = 0; i < G; i++) {
+        double a = 0.0;
+        for (size_t c = 0; c < nc; c++) a += N[(size_t)i * nc + c];
+        budget[4 * i + 0] = a * V;
+    }
+    return status;
+}
