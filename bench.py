@@ -1,0 +1,351 @@
+"""Benchmark of the RT step (injection + transport + thermochemistry +
+photon budget) on GB300 through the rtgb C-ABI.
+
+Metric: cell-group RT updates per second = cells x groups x steps / time.
+Default workload: the 128^3, 3-group, H+He, evolving-temperature HLL
+cosmological box with 16 sources (synthetic seeded log-normal density),
+200 steps from its initial state, FP64.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-group RT updates/s (transport+thermochem)"
+UNIT = "cell-group updates/s"
+
+# Denominators.  HBM: the measured copy bandwidth of this GB300 pool
+# (MEASURED_PEAKS.json when present).  FP64: 152 SMs x 2 FP64 FMA per SM
+# per clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s, matching the 1.25 TFLOP/s
+# measured by an FMA-chain probe on the same part.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP64 flops executed per thermochemistry attempt, from ncu
+# (smsp__sass_thread_inst_executed_op_d{fma x2, add, mul}) divided by the
+# attempts of the same launches; see profiles/thermo_cosmo128.md.
+FP64_FLOP_PER_ATTEMPT = None
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name):
+    from paper_1304_7126_gb300 import workloads as W
+    return {"cosmo128": W.cosmo128, "stromgren32": W.stromgren32, "cosmo256": W.cosmo256}[name]()
+
+
+def run_reference(args):
+    """FP64 CPU oracle on a bounded sample: one RT step of a 32^3 sub-box of
+    the workload's density field (with the sources that fall inside it) per
+    benchmark step, on all host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w = workload(args.workload)
+    sub = _subbox(w, 32)
+    cores = os.cpu_count() or 1
+    p = O.Problem(sub.shape, sub.dx, sub.G, sub.cr, sub.sigN, sub.sigE, sub.egy, X=sub.X,
+                  isothermal=sub.isothermal, otsa=sub.otsa, flux=sub.flux, bc=sub.bc, nthreads=cores)
+    dt = O.courant_dt(sub.cfl, sub.dx, sub.cr)
+    s = sub.state()
+    for _ in range(args.warmup):
+        p.step(s, dt, sub.src_ijk, sub.src_L)
+    s = sub.state()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p.step(s, dt, sub.src_ijk, sub.src_L)
+    t = time.perf_counter() - t0
+    val = sub.ncells * sub.G * args.steps / t
+    sample = "one oracle RT step per benchmark step on a 32^3 sub-box (corner of the %s field, %d sources)" % (
+        w.name, len(sub.src_ijk))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _subbox(w, m):
+    """The m^3 corner of a workload (same cell size and physics)."""
+    from paper_1304_7126_gb300 import workloads as W
+    nz, ny, nx = w.shape
+    m = min(m, nz, ny, nx)
+    nH = w.nH.reshape(w.shape)[:m, :m, :m].copy()
+    s = W.Workload(name=w.name + "_sub%d" % m, shape=(m, m, m), dx=w.dx, G=w.G, cr=w.cr, sigN=w.sigN,
+                   sigE=w.sigE, egy=w.egy, X=w.X, isothermal=w.isothermal, otsa=w.otsa, flux=w.flux,
+                   bc=w.bc, steps=w.steps, cfl=w.cfl)
+    nc = m ** 3
+    s.nH = nH.reshape(-1)
+    s.xHII = w.xHII.reshape(w.shape)[:m, :m, :m].reshape(-1).copy()
+    s.xHeII = np.zeros(nc)
+    s.xHeIII = np.zeros(nc)
+    s.T = w.T.reshape(w.shape)[:m, :m, :m].reshape(-1).copy()
+    inside = np.all(w.src_ijk < m, axis=1)
+    if inside.any():
+        s.src_ijk, s.src_L = w.src_ijk[inside], w.src_L[inside]
+    else:   # keep the sample's photo-ionisation work: move the brightest source in
+        s.src_ijk = W.densest_cells(nH, 1)
+        s.src_L = w.src_L[:1]
+    return s
+
+
+def _config(w):
+    nz, ny, nx = w.shape
+    return {"workload": "%s: %dx%dx%d cells, %d groups, %s, %s, X=%.2f, %d sources, c_r=c/%g, %d steps"
+            % (w.name, nx, ny, nz, w.G, "HLL" if w.flux == 1 else "GLF",
+               "isothermal" if w.isothermal else "evolving T", w.X, len(w.src_ijk),
+               round(2.99792458e10 / w.cr), w.steps),
+            "cells": w.ncells, "groups": w.G, "precision": "fp64",
+            "l2": "inputs larger than L2 (state %.0f MB)" % ((5 + 8 * w.G) * w.ncells * 8 / 1e6)}
+
+
+def cpu_baseline(w, seconds_hint=20.0):
+    """The oracle on this host's cores: RT steps of the full workload from its
+    initial state (as many as fit the hint, at least one)."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    p = O.Problem(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, X=w.X, isothermal=w.isothermal,
+                  otsa=w.otsa, flux=w.flux, bc=w.bc, nthreads=cores)
+    dt = O.courant_dt(w.cfl, w.dx, w.cr)
+    s = w.state()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        p.step(s, dt, w.src_ijk, w.src_L)
+        n += 1
+        if time.perf_counter() - t0 > seconds_hint or n >= 3:
+            break
+    t = time.perf_counter() - t0
+    return {"value": w.ncells * w.G * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d RT step(s) of the same %s workload from its initial state" % (n, w.name)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cosmo128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1304_7126_gb300 import rt as R
+
+    w = workload(args.workload)
+    hbm_peak, peak_kind = _peaks()
+    sim = R.RT.from_workload(w)
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream.cuda_stream)
+    dt = sim.courant_dt()
+    init = w.state()
+    dev_init = {k: torch.from_numpy(v).cuda() for k, v in init.items()}
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (also captures the CUDA graph of a pair of steps)
+    sim.run(dt, max(args.warmup, 3))
+    sim.sync()
+    sim.set_state(dev_init)
+    sim.sync()
+
+    # ---- timed region: K steps from the initial state, device-resident ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        sim.run(dt, args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    sim.sync()
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    units = w.ncells * w.G * args.steps * ws
+    value = units / t
+    clocks = clk.summary()
+
+    # ---- per-kernel breakdown: same K steps, eager launches with events ----
+    sim.set_state(dev_init)
+    sim.set_profiling(True)
+    attempts = 0
+    att_max = 0
+    queued = 0
+    queued_att = 0
+    sub = torch.empty(w.ncells, dtype=torch.int32, device="cuda")
+    for _ in range(args.steps):
+        sim.step(dt)
+        sim.L.rt_get_subcycles(sim.h, sub.data_ptr(), 1)
+        attempts += int(sub.sum().item())
+        att_max = max(att_max, int(sub.max().item()))
+        q = sub > 6
+        queued += int(q.sum().item())
+        queued_att += int(sub[q].sum().item())
+    prof = sim.profile()
+    sim.set_profiling(False)
+    phases = {k: {"ms_total": round(v[0], 4), "launches": v[1],
+                  "ms_per_launch": round(v[0] / v[1], 5) if v[1] else None} for k, v in prof.items()}
+    dominant = max(prof, key=lambda k: prof[k][0])
+    ms_launch = prof[dominant][0] / max(prof[dominant][1], 1)
+    cg = w.ncells * w.G
+    if dominant == "transport":
+        alg = 64.0 * cg   # FP64: N, F read and written once per cell-group
+        ach = alg / (ms_launch / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "traffic": None, "kernel": "transport", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": alg}
+    else:
+        # thermochemistry is FP64-ALU bound: flops per attempt x attempts
+        att_per_launch = attempts / args.steps
+        fpa = FP64_FLOP_PER_ATTEMPT
+        ach = (fpa * att_per_launch / (ms_launch / 1e3) / 1e9) if fpa else None
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": (ach / FP64_PEAK_GFLOPS) if ach else None, "traffic": None, "kernel": dominant,
+                "peak_kind": "derived FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "attempts_per_step": att_per_launch}
+
+    # ---- end to end: host buffers through the C-ABI, copies in the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in init.items()}
+        host = {k: v.numpy() for k, v in pin.items()}
+        outp = {k: torch.empty_like(v).pin_memory() for k, v in pin.items()}
+        outh = {k: v.numpy() for k, v in outp.items()}
+        sim.set_state(dev_init)
+        sim.sync()
+        h2d = sum(v.nbytes for v in host.values())
+        d2h = sum(v.nbytes for v in outh.values())
+        barrier()
+        t0 = time.perf_counter()
+        cur_in, cur_out = host, outh
+        for _ in range(args.steps):
+            sim.set_state(cur_in)           # H2D of the step's input state
+            sim.step(dt)
+            sim.get_state(cur_out)          # D2H of the step's result
+            cur_in, cur_out = cur_out, cur_in
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": units / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "how": "per step: rt_set_state from pinned host buffers, rt_step, rt_get_state to pinned host"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        cfg = _config(w)
+        cfg["parallelism"] = "replicas x%d" % ws if ws > 1 else "single GPU"
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clocks, "phases": phases,
+                "thermo_attempts": {"per_step": attempts / args.steps, "max_per_cell": att_max,
+                                    "queued_cells_per_step": queued / args.steps,
+                                    "queued_attempts_per_step": queued_att / args.steps}}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * rtgb: GB300 (sm_103a) radiative-transfer step of the M1 moment method
+ * (Rosdahl et al. 2013, "RAMSES-RT"), on a uniform Cartesian grid.
+ *
+ * One RT step over a time step dt is, in order (paper Sec. 3):
+ *   1. injection       N_i += L_i dt / V in each source cell    (Sec. 3.1, Eq. (injnum))
+ *   2. transport       explicit first-order Godunov update of (N_i, F_i)
+ *                      with the M1 closure and GLF or HLL intercell fluxes,
+ *                      unsplit over the six faces          (Sec. 3.2, Eqs. (dUdt_sol),
+ *                                                          (hll), (glf); Sec. 2, Eqs. (edd2)-(Udir))
+ *   3. thermochemistry per-cell semi-implicit update of N_i, F_i, T, x_HII,
+ *                      x_HeII, x_HeIII, sub-cycled under the 10% rule
+ *                                                          (Sec. 3.3, App. A)
+ * with dt bounded by the Courant condition dt <= CFL dx / (3 c_r)
+ * (Sec. 4.1, Eq. (dt_courant)) and c_r the reduced speed of light.
+ *
+ * Units are cgs.  Layouts (x fastest, row-major, no padding):
+ *   scalar fields      [nz][ny][nx]                 (cells = nx*ny*nz)
+ *   photon density N   [G][nz][ny][nx]              photons / cm^3
+ *   photon flux F      [G][3][nz][ny][nx]           photons / cm^2 / s  (x, y, z)
+ *   group constants    sigN, sigE [G][3] cm^2 (species HI, HeI, HeII), egy [G] erg
+ *
+ * Ownership: the handle owns all device memory it allocates.  Every input
+ * is copied at the call; every get_* copies into caller buffers.  With
+ * device_ptrs = 1, pointers are CUDA device pointers on the handle's device
+ * and are read/written on the handle's stream.
+ *
+ * Errors: every int-returning call returns RT_OK (0) or a negative code.
+ * Device-side failures (sub-cycle cap, queue overflow, non-finite values)
+ * set a sticky status word that the next rt_step / rt_get_* / rt_sync
+ * reports as its return code; the state is then undefined until
+ * rt_set_state.  rt_last_error gives a one-line message.
+ */
+#ifndef RTGB_RT_H
+#define RTGB_RT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_OK 0
+#define RT_EINVAL -1     /* bad sizes / options / non-finite or out-of-range inputs */
+#define RT_EDT -2        /* dt above the Courant limit */
+#define RT_ESUBCYCLE -3  /* a cell exceeded max_subcycles thermochemistry attempts */
+#define RT_EQUEUE -4     /* work-queue overflow */
+#define RT_ECUDA -5      /* a CUDA runtime call failed */
+#define RT_ENOMEM -6     /* device or host allocation failed */
+#define RT_ENONFINITE -7 /* a NaN/Inf appeared in the state */
+
+#define RT_MAX_GROUPS 8
+
+enum { RT_BC_OUTFLOW = 0, RT_BC_REFLECT = 1, RT_BC_PERIODIC = 2 };
+enum { RT_GLF = 0, RT_HLL = 1 };
+enum { RT_FP64 = 0, RT_MIXED = 1 };
+
+typedef struct rt_handle rt_handle;
+
+/* Uniform grid.  bc[] = boundary condition of the faces -x, +x, -y, +y, -z,
+ * +z: outflow (zero-gradient ghost), reflect (ghost with the normal flux
+ * component negated) or periodic. */
+typedef struct {
+    int nx, ny, nz;
+    double dx_cm;
+    int bc[6];
+} rt_grid;
+
+/* Options.  X: hydrogen mass fraction (Y = 1 - X; helium is skipped when
+ * Y = 0).  isothermal: T held fixed.  otsa: on-the-spot approximation
+ * (case-B rates, no recombination photons; Sec. 3.3.2) - must be 1.
+ * flux: RT_GLF (default) or RT_HLL.  cfl: Courant factor (0.8).
+ * precision: RT_FP64 or RT_MIXED (FP32 transport with compensated face
+ * sums, FP64 thermochemistry).  a_exp: expansion factor in the Compton
+ * term (1).  max_subcycles: thermochemistry attempts allowed per cell and
+ * step (1e6).  smooth: must be 0. */
+typedef struct {
+    double X;
+    int isothermal;
+    int otsa;
+    int flux;
+    double cfl;
+    int precision;
+    double a_exp;
+    int max_subcycles;
+    int smooth;
+} rt_options;
+
+/* Fill *o with the defaults listed above (X = 0.76). */
+void rt_default_options(rt_options *o);
+
+/* Create a handle on the current CUDA device.  n_groups in 1..RT_MAX_GROUPS,
+ * c_r > 0 the reduced light speed [cm/s]; sigN, sigE [G][3] group cross
+ * sections (Eqs. (csn_multi), (cse_multi)) and egy [G] mean photon energies
+ * (Eq. (egy_multi)), host pointers, copied.  The state starts at zero
+ * photons, n_H = 0, and must be set with rt_set_state before rt_step. */
+int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c_r,
+              const double *sigN, const double *sigE, const double *egy, rt_handle **out);
+
+/* Free the handle and all its device memory.  NULL is allowed. */
+void rt_destroy(rt_handle *h);
+
+/* Use `stream` (a cudaStream_t, may be NULL for the legacy default stream)
+ * for all later work of this handle. */
+int rt_set_stream(rt_handle *h, void *stream);
+
+/* Set the full state (all pointers required).  nH > 0; x_HII in
+ * [1e-6, 1]; x_HeII, x_HeIII >= 0 with sum <= 1; T > 0; N >= 0;
+ * |F| <= c_r N (1 + 1e-8).  Validated on the host for host pointers;
+ * device pointers are copied without validation.  Resets the budget. */
+int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const double *xHeII,
+                 const double *xHeIII, const double *T, const double *N, const double *F,
+                 int device_ptrs);
+
+/* Copy the state out; any pointer may be NULL to skip that field.
+ * Synchronises the handle's stream and reports sticky device errors. */
+int rt_get_state(rt_handle *h, double *nH, double *xHII, double *xHeII, double *xHeIII,
+                 double *T, double *N, double *F, int device_ptrs);
+
+/* Replace the point-source list: n sources, ijk [n][3] = (i, j, k) cell
+ * indices (x, y, z), L [n][G] photons/s, host pointers.  Sources sharing a
+ * cell are merged (luminosities summed in the given order). */
+int rt_set_sources(rt_handle *h, int n, const int32_t *ijk, const double *L);
+
+/* Courant time step CFL dx / (3 c_r), Eq. (dt_courant). */
+int rt_courant_dt(const rt_handle *h, double *dt);
+
+/* One RT step (injection, transport, thermochemistry, budget) of length
+ * dt; dt <= 0 takes the Courant step; dt above it returns RT_EDT.
+ * Asynchronous on the handle's stream. */
+int rt_step(rt_handle *h, double dt);
+
+/* nsteps RT steps of length dt (as rt_step), launched as a CUDA graph
+ * captured once per (dt, source list). */
+int rt_run(rt_handle *h, double dt, int nsteps);
+
+/* Photon budget per group, out [G][4]: photons in the box now, and since
+ * the last rt_set_state the photons absorbed by the gas, the net outflow
+ * through the box faces (negative = inflow), and the photons emitted by
+ * the sources.  Conservation: in_box(now) = in_box(at set_state) +
+ * emitted - absorbed - outflow, up to rounding.  Synchronises. */
+int rt_get_budget(rt_handle *h, double *out);
+
+/* Thermochemistry attempts (successful and rejected thermo_step calls) of
+ * each cell in the last step, [nz][ny][nx] int32.  Synchronises. */
+int rt_get_subcycles(rt_handle *h, int32_t *per_cell, int device_ptr);
+
+/* Wait for the handle's stream and report sticky device errors. */
+int rt_sync(rt_handle *h);
+
+/* One-line description of the last error on this handle (never NULL). */
+const char *rt_last_error(const rt_handle *h);
+
+/* Host-side HLL wave-speed table used by RT_HLL: extreme eigenvalues of the
+ * M1 flux Jacobian (Sec. 3.2) in units of c, out [nf][nmu][2] =
+ * (lambda_min, lambda_max) at f = k/(nf-1), mu = -1 + 2j/(nmu-1).
+ * Needs no GPU. */
+int rt_hll_table(int nf, int nmu, double *out);
+
+/* Per-phase timing (diagnostics; not part of the RT method).  With enable
+ * != 0, rt_step records CUDA events on the handle's stream around each of
+ * its phases (rt_run does not).  Phases: 0 injection, 1 transport,
+ * 2 thermochemistry first pass, 3 thermochemistry queue drain, 4 photon
+ * reduction, 5 budget finalisation.  Enabling resets the counters. */
+#define RT_NPHASES 6
+int rt_set_profiling(rt_handle *h, int enable);
+
+/* Accumulated milliseconds and launch counts per phase since profiling was
+ * enabled, ms [RT_NPHASES], launches [RT_NPHASES].  Synchronises. */
+int rt_get_profile(rt_handle *h, double *ms, int64_t *launches);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTGB_RT_H */

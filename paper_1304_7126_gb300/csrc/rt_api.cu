@@ -1,0 +1,594 @@
+// C-ABI of the rtgb library (declared in include/rt.h): handle lifetime,
+// state transfer, source list, and the RT step (paper Sec. 3: injection,
+// transport, thermochemistry over the same dt), optionally replayed as a
+// CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rt_internal.h"
+
+using namespace rtgb;
+
+struct rt_handle {
+    GridDev g{};
+    int G = 0;
+    rt_options opt{};
+    double cr = 0.0;
+    GroupConsts gc{};
+    int device = 0;
+    int n_sm = 1;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+
+    double *nH = nullptr, *xHII = nullptr, *xHeII = nullptr, *xHeIII = nullptr, *T = nullptr;
+    double *N[2] = {nullptr, nullptr};
+    double *F[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *hll = nullptr;
+    int32_t *subcycles = nullptr;
+    Queue q{};
+    Partials part{};
+    double *budget = nullptr;
+    unsigned *status = nullptr;
+    unsigned *status_host = nullptr;   // pinned mirror, refreshed after every step
+
+    int nsrc = 0;
+    long long *src_cell = nullptr;
+    double *src_L = nullptr;
+    std::vector<double> src_Lsum_host;   // total luminosity per group
+
+    bool state_set = false;
+    cudaGraphExec_t graph = nullptr;
+    double graph_dt = 0.0;
+    int graph_cur0 = 0;     // ping-pong buffer the captured pair of steps starts from
+    std::string err;
+
+    // per-phase profiling (rt_set_profiling)
+    bool prof = false;
+    cudaEvent_t ev[RT_NPHASES + 1][2] = {};
+    bool ev_made = false;
+    double prof_ms[RT_NPHASES] = {0};
+    int64_t prof_n[RT_NPHASES] = {0};
+    std::vector<cudaEvent_t> pending;   // [start, stop] pairs per phase, flattened
+    std::vector<int> pending_phase;
+};
+
+namespace {
+
+const char *kNoHandle = "null handle";
+
+int fail(rt_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(rt_handle *h, cudaError_t e, const char *what)
+{
+    return fail(h, RT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RT_CUDA(h, call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+double courant(const rt_handle *h) { return h->opt.cfl * h->g.dx / (3.0 * h->cr); }
+
+int status_to_code(rt_handle *h, unsigned st)
+{
+    if (st & kStatusNonFinite) return fail(h, RT_ENONFINITE, "non-finite value in the state");
+    if (st & kStatusSubcycle) return fail(h, RT_ESUBCYCLE, "a cell exceeded max_subcycles thermochemistry attempts");
+    if (st & kStatusQueue) return fail(h, RT_EQUEUE, "thermochemistry work queue overflow");
+    return RT_OK;
+}
+
+void prof_collect(rt_handle *h);
+
+int sync_and_check(rt_handle *h)
+{
+    RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    unsigned st = 0;
+    RT_CUDA(h, cudaMemcpy(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return status_to_code(h, st);
+}
+
+void free_all(rt_handle *h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (cudaEvent_t e : h->pending) cudaEventDestroy(e);
+    h->pending.clear();
+    void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
+                    h->hll, h->subcycles, h->q.cell, h->q.t_left, h->q.dt_tc, h->q.attempts,
+                    h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
+                    h->budget, h->status, h->src_cell, h->src_L};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->status_host) cudaFreeHost(h->status_host);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+}
+
+template <typename T>
+int dalloc(rt_handle *h, T **p, size_t n)
+{
+    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return fail(h, RT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return RT_OK;
+}
+
+ThermoParams thermo_params(const rt_handle *h, double dt)
+{
+    ThermoParams p{};
+    p.nc = h->g.nc;
+    p.dt = dt;
+    p.cr = h->cr;
+    p.X = h->opt.X;
+    double Y = 1.0 - h->opt.X;
+    p.he_ratio = (Y > 0.0) ? Y / (4.0 * h->opt.X) : 0.0;
+    // K = (gamma - 1) m_H / (rho k_B) with rho = n_H m_H / X
+    p.kfac = (5.0 / 3.0 - 1.0) * h->opt.X / 1.380649e-16;
+    p.a_exp = h->opt.a_exp;
+    p.isothermal = h->opt.isothermal ? 1 : 0;
+    p.helium = (Y > 0.0) ? 1 : 0;
+    p.case_b = h->opt.otsa ? 1 : 0;
+    p.max_sub = h->opt.max_subcycles;
+    p.pass1_attempts = 6;
+    p.gc = h->gc;
+    return p;
+}
+
+// Profiling: a fresh start/stop event pair per phase launch; elapsed times
+// are folded in at the next synchronising call.
+void prof_pair(rt_handle *h, int phase, cudaEvent_t *a, cudaEvent_t *b)
+{
+    cudaEventCreate(a);
+    cudaEventCreate(b);
+    h->pending.push_back(*a);
+    h->pending.push_back(*b);
+    h->pending_phase.push_back(phase);
+}
+
+void prof_collect(rt_handle *h)
+{
+    for (size_t k = 0; k < h->pending_phase.size(); ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->pending[2 * k], h->pending[2 * k + 1]) == cudaSuccess) {
+            h->prof_ms[h->pending_phase[k]] += ms;
+            h->prof_n[h->pending_phase[k]] += 1;
+        }
+        cudaEventDestroy(h->pending[2 * k]);
+        cudaEventDestroy(h->pending[2 * k + 1]);
+    }
+    h->pending.clear();
+    h->pending_phase.clear();
+}
+
+// Enqueue one RT step on h->stream (no host synchronisation).
+int enqueue_step(rt_handle *h, double dt, bool capturing = false)
+{
+    const bool prof = h->prof && !capturing;
+    cudaEvent_t a, b;
+    const long long nc = h->g.nc;
+    const double V = h->g.dx * h->g.dx * h->g.dx;
+    cudaError_t e;
+    if (h->nsrc > 0) {
+        if (prof) { prof_pair(h, 0, &a, &b); cudaEventRecord(a, h->stream); }
+        e = launch_inject(h->nsrc, h->G, nc, h->src_cell, h->src_L, dt / V, h->N[h->cur], h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "inject");
+        if (prof) cudaEventRecord(b, h->stream);
+    }
+    int nxt = 1 - h->cur;
+    if (prof) { prof_pair(h, 1, &a, &b); cudaEventRecord(a, h->stream); }
+    e = launch_transport(h->g, h->G, h->opt.flux, h->cr, dt, h->N[h->cur], h->F[h->cur], h->N[nxt],
+                         h->F[nxt], h->hll, h->part, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "transport");
+    if (prof) cudaEventRecord(b, h->stream);
+    h->cur = nxt;
+    ThermoParams tp = thermo_params(h, dt);
+    cudaEvent_t tev[4];
+    if (prof) {
+        prof_pair(h, 2, &tev[0], &tev[1]);
+        prof_pair(h, 3, &tev[2], &tev[3]);
+    }
+    e = launch_thermo(tp, h->G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[h->cur], h->F[h->cur],
+                      h->subcycles, h->q, h->status, h->n_sm, h->stream, prof ? tev : nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "thermo");
+    if (prof) { prof_pair(h, 4, &a, &b); cudaEventRecord(a, h->stream); }
+    e = launch_reduce_N(h->G, nc, h->N[h->cur], h->part, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
+    if (prof) cudaEventRecord(b, h->stream);
+    double emitted[kMaxG] = {0};
+    for (int g = 0; g < h->G; ++g) emitted[g] = h->src_Lsum_host[g] * dt;
+    if (prof) { prof_pair(h, 5, &a, &b); cudaEventRecord(a, h->stream); }
+    e = launch_finalize_mode(h->G, 0, h->part, V, emitted, h->budget, h->q, h->status, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "finalize");
+    if (prof) cudaEventRecord(b, h->stream);
+    e = cudaMemcpyAsync(h->status_host, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status copy");
+    return RT_OK;
+}
+
+int check_dt(rt_handle *h, double *dt)
+{
+    if (!h->state_set) return fail(h, RT_EINVAL, "rt_set_state has not been called");
+    double dc = courant(h);
+    if (!(*dt > 0.0)) *dt = dc;
+    if (!std::isfinite(*dt)) return fail(h, RT_EINVAL, "dt is not finite");
+    if (*dt > dc * (1.0 + 1e-12)) return fail(h, RT_EDT, "dt above the Courant limit CFL dx/(3 c_r)");
+    // the pinned mirror of the sticky status (stale by at most the steps in flight)
+    unsigned st = *(volatile unsigned *)h->status_host;
+    if (st) return status_to_code(h, st);
+    return RT_OK;
+}
+
+void invalidate_graph(rt_handle *h)
+{
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void rt_default_options(rt_options *o)
+{
+    if (!o) return;
+    o->X = 0.76;
+    o->isothermal = 0;
+    o->otsa = 1;
+    o->flux = RT_GLF;
+    o->cfl = 0.8;
+    o->precision = RT_FP64;
+    o->a_exp = 1.0;
+    o->max_subcycles = 1000000;
+    o->smooth = 0;
+}
+
+int rt_version(void) { return 100; }
+
+int rt_hll_table(int nf, int nmu, double *out)
+{
+    if (nf < 2 || nmu < 2 || !out) return RT_EINVAL;
+    rtgb::hll_table(nf, nmu, out);
+    return RT_OK;
+}
+
+int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c_r, const double *sigN,
+              const double *sigE, const double *egy, rt_handle **out)
+{
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    if (!grid || !opt || !sigN || !sigE || !egy) return RT_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx_cm > 0.0) || !std::isfinite(grid->dx_cm))
+        return RT_EINVAL;
+    long long nc = (long long)grid->nx * grid->ny * grid->nz;
+    if (nc >= (1LL << 31)) return RT_EINVAL;
+    for (int i = 0; i < 6; ++i)
+        if (grid->bc[i] < RT_BC_OUTFLOW || grid->bc[i] > RT_BC_PERIODIC) return RT_EINVAL;
+    for (int d = 0; d < 3; ++d)   // periodic must be set on both faces of an axis
+        if ((grid->bc[2 * d] == RT_BC_PERIODIC) != (grid->bc[2 * d + 1] == RT_BC_PERIODIC)) return RT_EINVAL;
+    if (n_groups < 1 || n_groups > RT_MAX_GROUPS) return RT_EINVAL;
+    if (!(c_r > 0.0) || !std::isfinite(c_r)) return RT_EINVAL;
+    if (!(opt->X > 0.0 && opt->X <= 1.0)) return RT_EINVAL;
+    if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return RT_EINVAL;
+    if (opt->flux != RT_GLF && opt->flux != RT_HLL) return RT_EINVAL;
+    if (opt->otsa != 1 || opt->smooth != 0) return RT_EINVAL;
+    if (opt->precision != RT_FP64) return RT_EINVAL;
+    if (!(opt->a_exp > 0.0) || opt->max_subcycles < 1) return RT_EINVAL;
+    for (int i = 0; i < 3 * n_groups; ++i)
+        if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0) || !std::isfinite(sigN[i]) || !std::isfinite(sigE[i]))
+            return RT_EINVAL;
+    for (int i = 0; i < n_groups; ++i)
+        if (!(egy[i] > 0.0) || !std::isfinite(egy[i])) return RT_EINVAL;
+
+    rt_handle *h = new rt_handle();
+    h->g.nx = grid->nx; h->g.ny = grid->ny; h->g.nz = grid->nz;
+    h->g.nc = nc;
+    h->g.dx = grid->dx_cm;
+    for (int i = 0; i < 6; ++i) h->g.bc[i] = grid->bc[i];
+    h->G = n_groups;
+    h->opt = *opt;
+    h->cr = c_r;
+    for (int i = 0; i < n_groups; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            h->gc.sigN[i][j] = sigN[3 * i + j];
+            h->gc.sigE[i][j] = sigE[3 * i + j];
+        }
+        h->gc.egy[i] = egy[i];
+    }
+    h->src_Lsum_host.assign(n_groups, 0.0);
+    int rc = RT_OK;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaGetDevice"); goto bad; }
+    if ((e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
+        rc = cuda_fail(h, e, "attr"); goto bad;
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        rc = cuda_fail(h, e, "cudaStreamCreate"); goto bad;
+    }
+    h->stream = h->own_stream;
+    transport_init();
+    {
+        const size_t G = (size_t)n_groups;
+        h->part.n_tr_blocks = transport_blocks_per_group(h->g);
+        h->part.n_red_blocks = reduce_blocks_per_group();
+        if ((rc = dalloc(h, &h->nH, nc)) || (rc = dalloc(h, &h->xHII, nc)) || (rc = dalloc(h, &h->xHeII, nc)) ||
+            (rc = dalloc(h, &h->xHeIII, nc)) || (rc = dalloc(h, &h->T, nc)) ||
+            (rc = dalloc(h, &h->N[0], G * nc)) || (rc = dalloc(h, &h->N[1], G * nc)) ||
+            (rc = dalloc(h, &h->F[0], 3 * G * nc)) || (rc = dalloc(h, &h->F[1], 3 * G * nc)) ||
+            (rc = dalloc(h, &h->hll, (size_t)kHllNF * kHllNMU * 2)) || (rc = dalloc(h, &h->subcycles, nc)) ||
+            (rc = dalloc(h, &h->q.cell, nc)) || (rc = dalloc(h, &h->q.t_left, nc)) ||
+            (rc = dalloc(h, &h->q.dt_tc, nc)) || (rc = dalloc(h, &h->q.attempts, nc)) ||
+            (rc = dalloc(h, &h->q.counters, 2)) ||
+            (rc = dalloc(h, &h->part.tr_inbox, G * h->part.n_tr_blocks)) ||
+            (rc = dalloc(h, &h->part.tr_outflow, G * h->part.n_tr_blocks)) ||
+            (rc = dalloc(h, &h->part.th_inbox, G * h->part.n_red_blocks)) ||
+            (rc = dalloc(h, &h->budget, 4 * G)) || (rc = dalloc(h, &h->status, 1)))
+            goto bad;
+        h->q.capacity = nc;
+        if ((e = cudaMallocHost((void **)&h->status_host, sizeof(unsigned))) != cudaSuccess) {
+            rc = fail(h, RT_ENOMEM, "cudaMallocHost"); goto bad;
+        }
+        *h->status_host = 0;
+        std::vector<double> tab((size_t)kHllNF * kHllNMU * 2);
+        rtgb::hll_table(kHllNF, kHllNMU, tab.data());
+        if ((e = cudaMemcpy(h->hll, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            rc = cuda_fail(h, e, "hll copy"); goto bad;
+        }
+        if ((e = cudaMemset(h->q.counters, 0, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMemset(h->status, 0, sizeof(unsigned))) != cudaSuccess ||
+            (e = cudaMemset(h->budget, 0, 4 * G * sizeof(double))) != cudaSuccess ||
+            (e = cudaMemset(h->N[0], 0, G * nc * sizeof(double))) != cudaSuccess ||
+            (e = cudaMemset(h->N[1], 0, G * nc * sizeof(double))) != cudaSuccess ||
+            (e = cudaMemset(h->F[0], 0, 3 * G * nc * sizeof(double))) != cudaSuccess ||
+            (e = cudaMemset(h->F[1], 0, 3 * G * nc * sizeof(double))) != cudaSuccess ||
+            (e = cudaMemset(h->subcycles, 0, nc * sizeof(int32_t))) != cudaSuccess) {
+            rc = cuda_fail(h, e, "cudaMemset"); goto bad;
+        }
+    }
+    *out = h;
+    return RT_OK;
+bad:
+    free_all(h);
+    delete h;
+    return rc;
+}
+
+void rt_destroy(rt_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int rt_set_stream(rt_handle *h, void *stream)
+{
+    if (!h) return RT_EINVAL;
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->own_stream;
+    if (s != h->stream) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        h->stream = s;
+        invalidate_graph(h);
+    }
+    return RT_OK;
+}
+
+int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const double *xHeII, const double *xHeIII,
+                 const double *T, const double *N, const double *F, int device_ptrs)
+{
+    if (!h) return RT_EINVAL;
+    if (!nH || !xHII || !xHeII || !xHeIII || !T || !N || !F) return fail(h, RT_EINVAL, "null state pointer");
+    const long long nc = h->g.nc;
+    const int G = h->G;
+    if (!device_ptrs) {
+        for (long long c = 0; c < nc; ++c) {
+            bool ok = std::isfinite(nH[c]) && nH[c] > 0.0 && std::isfinite(xHII[c]) && xHII[c] >= 1e-6 &&
+                      xHII[c] <= 1.0 && xHeII[c] >= 0.0 && xHeIII[c] >= 0.0 && xHeII[c] + xHeIII[c] <= 1.0 &&
+                      std::isfinite(T[c]) && T[c] > 0.0;
+            if (!ok) return fail(h, RT_EINVAL, "gas state out of range at cell " + std::to_string(c));
+            for (int g = 0; g < G; ++g) {
+                double n = N[(size_t)g * nc + c];
+                double fx = F[((size_t)3 * g) * nc + c], fy = F[((size_t)3 * g + 1) * nc + c],
+                       fz = F[((size_t)3 * g + 2) * nc + c];
+                if (!(std::isfinite(n) && n >= 0.0 && std::isfinite(fx) && std::isfinite(fy) && std::isfinite(fz)))
+                    return fail(h, RT_EINVAL, "photon state not finite / negative at cell " + std::to_string(c));
+                double fm = std::sqrt(fx * fx + fy * fy + fz * fz);
+                if (fm > h->cr * n * (1.0 + 1e-8))
+                    return fail(h, RT_EINVAL, "|F| > c_r N at cell " + std::to_string(c));
+            }
+        }
+    }
+    cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t b = (size_t)nc * sizeof(double);
+    h->cur = 0;
+    RT_CUDA(h, cudaMemcpyAsync(h->nH, nH, b, k, h->stream));
+    RT_CUDA(h, cudaMemcpyAsync(h->xHII, xHII, b, k, h->stream));
+    RT_CUDA(h, cudaMemcpyAsync(h->xHeII, xHeII, b, k, h->stream));
+    RT_CUDA(h, cudaMemcpyAsync(h->xHeIII, xHeIII, b, k, h->stream));
+    RT_CUDA(h, cudaMemcpyAsync(h->T, T, b, k, h->stream));
+    RT_CUDA(h, cudaMemcpyAsync(h->N[0], N, G * b, k, h->stream));
+    RT_CUDA(h, cudaMemcpyAsync(h->F[0], F, 3 * G * b, k, h->stream));
+    RT_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, 2 * sizeof(unsigned long long), h->stream));
+    cudaError_t e = launch_reduce_N(G, nc, h->N[0], h->part, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
+    e = launch_finalize_mode(G, 1, h->part, h->g.dx * h->g.dx * h->g.dx, nullptr, h->budget, h->q, h->status,
+                             h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "finalize");
+    if (!device_ptrs) RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    *h->status_host = 0;
+    h->state_set = true;
+    return RT_OK;
+}
+
+int rt_get_state(rt_handle *h, double *nH, double *xHII, double *xHeII, double *xHeIII, double *T, double *N,
+                 double *F, int device_ptrs)
+{
+    if (!h) return RT_EINVAL;
+    int rc = sync_and_check(h);
+    cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t b = (size_t)h->g.nc * sizeof(double);
+    if (nH) RT_CUDA(h, cudaMemcpyAsync(nH, h->nH, b, k, h->stream));
+    if (xHII) RT_CUDA(h, cudaMemcpyAsync(xHII, h->xHII, b, k, h->stream));
+    if (xHeII) RT_CUDA(h, cudaMemcpyAsync(xHeII, h->xHeII, b, k, h->stream));
+    if (xHeIII) RT_CUDA(h, cudaMemcpyAsync(xHeIII, h->xHeIII, b, k, h->stream));
+    if (T) RT_CUDA(h, cudaMemcpyAsync(T, h->T, b, k, h->stream));
+    if (N) RT_CUDA(h, cudaMemcpyAsync(N, h->N[h->cur], h->G * b, k, h->stream));
+    if (F) RT_CUDA(h, cudaMemcpyAsync(F, h->F[h->cur], 3 * h->G * b, k, h->stream));
+    if (!device_ptrs) RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int rt_set_sources(rt_handle *h, int n, const int32_t *ijk, const double *L)
+{
+    if (!h) return RT_EINVAL;
+    if (n < 0 || (n > 0 && (!ijk || !L))) return fail(h, RT_EINVAL, "bad source arrays");
+    const int G = h->G;
+    std::map<long long, std::vector<double>> merged;
+    std::vector<long long> order;
+    std::vector<double> tot(G, 0.0);
+    for (int s = 0; s < n; ++s) {
+        int i = ijk[3 * s], j = ijk[3 * s + 1], k = ijk[3 * s + 2];
+        if (i < 0 || j < 0 || k < 0 || i >= h->g.nx || j >= h->g.ny || k >= h->g.nz)
+            return fail(h, RT_EINVAL, "source outside the grid");
+        long long c = ((long long)k * h->g.ny + j) * h->g.nx + i;
+        auto it = merged.find(c);
+        if (it == merged.end()) {
+            it = merged.emplace(c, std::vector<double>(G, 0.0)).first;
+            order.push_back(c);
+        }
+        for (int g = 0; g < G; ++g) {
+            double l = L[(size_t)s * G + g];
+            if (!(l >= 0.0) || !std::isfinite(l)) return fail(h, RT_EINVAL, "bad source luminosity");
+            it->second[g] += l;
+            tot[g] += l;
+        }
+    }
+    RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->src_cell) { cudaFree(h->src_cell); h->src_cell = nullptr; }
+    if (h->src_L) { cudaFree(h->src_L); h->src_L = nullptr; }
+    h->nsrc = 0;
+    int m = (int)order.size();
+    if (m > 0) {
+        std::vector<double> Lh((size_t)m * G);
+        for (int s = 0; s < m; ++s)
+            for (int g = 0; g < G; ++g) Lh[(size_t)s * G + g] = merged[order[s]][g];
+        int rc;
+        if ((rc = dalloc(h, &h->src_cell, m)) || (rc = dalloc(h, &h->src_L, (size_t)m * G))) return rc;
+        RT_CUDA(h, cudaMemcpy(h->src_cell, order.data(), m * sizeof(long long), cudaMemcpyHostToDevice));
+        RT_CUDA(h, cudaMemcpy(h->src_L, Lh.data(), Lh.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    h->nsrc = m;
+    h->src_Lsum_host = tot;
+    invalidate_graph(h);
+    return RT_OK;
+}
+
+int rt_courant_dt(const rt_handle *h, double *dt)
+{
+    if (!h || !dt) return RT_EINVAL;
+    *dt = courant(h);
+    return RT_OK;
+}
+
+int rt_step(rt_handle *h, double dt)
+{
+    if (!h) return RT_EINVAL;
+    int rc = check_dt(h, &dt);
+    if (rc) return rc;
+    return enqueue_step(h, dt);
+}
+
+int rt_run(rt_handle *h, double dt, int nsteps)
+{
+    if (!h) return RT_EINVAL;
+    if (nsteps < 0) return fail(h, RT_EINVAL, "nsteps < 0");
+    int rc = check_dt(h, &dt);
+    if (rc) return rc;
+    if (nsteps == 0) return RT_OK;
+    // the graph holds two steps so that the ping-pong buffers line up again
+    if (!h->graph || h->graph_dt != dt || h->graph_cur0 != h->cur) {
+        invalidate_graph(h);
+        cudaGraph_t graph;
+        int cur0 = h->cur;
+        RT_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int r1 = enqueue_step(h, dt, true);
+        int r2 = r1 ? r1 : enqueue_step(h, dt, true);
+        cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+        h->cur = cur0;
+        if (r2) return r2;
+        if (ec != cudaSuccess) return cuda_fail(h, ec, "cudaStreamEndCapture");
+        cudaError_t ei = cudaGraphInstantiate(&h->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) { h->graph = nullptr; return cuda_fail(h, ei, "cudaGraphInstantiate"); }
+        h->graph_dt = dt;
+        h->graph_cur0 = cur0;
+    }
+    int pairs = nsteps / 2;
+    for (int k = 0; k < pairs; ++k) RT_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+    if (nsteps % 2) return enqueue_step(h, dt);
+    return RT_OK;
+}
+
+int rt_get_budget(rt_handle *h, double *out)
+{
+    if (!h || !out) return RT_EINVAL;
+    int rc = sync_and_check(h);
+    RT_CUDA(h, cudaMemcpy(out, h->budget, 4 * h->G * sizeof(double), cudaMemcpyDeviceToHost));
+    return rc;
+}
+
+int rt_get_subcycles(rt_handle *h, int32_t *per_cell, int device_ptr)
+{
+    if (!h || !per_cell) return RT_EINVAL;
+    int rc = sync_and_check(h);
+    RT_CUDA(h, cudaMemcpy(per_cell, h->subcycles, h->g.nc * sizeof(int32_t),
+                          device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return rc;
+}
+
+int rt_set_profiling(rt_handle *h, int enable)
+{
+    if (!h) return RT_EINVAL;
+    RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+    h->prof = enable != 0;
+    for (int k = 0; k < RT_NPHASES; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+    return RT_OK;
+}
+
+int rt_get_profile(rt_handle *h, double *ms, int64_t *launches)
+{
+    if (!h || !ms || !launches) return RT_EINVAL;
+    int rc = sync_and_check(h);
+    for (int k = 0; k < RT_NPHASES; ++k) { ms[k] = h->prof_ms[k]; launches[k] = h->prof_n[k]; }
+    return rc;
+}
+
+int rt_sync(rt_handle *h)
+{
+    if (!h) return RT_EINVAL;
+    return sync_and_check(h);
+}
+
+const char *rt_last_error(const rt_handle *h)
+{
+    if (!h) return kNoHandle;
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal definitions shared by the rtgb translation units (not part of the
+// C-ABI).  Device kernels live in transport.cu, thermo.cu and misc.cu; the
+// C-ABI in rt_api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rt.h"
+
+namespace rtgb {
+
+constexpr int kMaxG = RT_MAX_GROUPS;
+constexpr int kHllNF = 257;   // HLL table: f = k/256
+constexpr int kHllNMU = 257;  // mu = -1 + j/128
+
+// Sticky device status bits.
+enum : unsigned {
+    kStatusSubcycle = 1u,
+    kStatusQueue = 2u,
+    kStatusNonFinite = 4u,
+};
+
+// Constants of the photon groups, passed by value to the kernels.
+struct GroupConsts {
+    double sigN[kMaxG][3];   // cm^2, species HI, HeI, HeII
+    double sigE[kMaxG][3];   // cm^2
+    double egy[kMaxG];       // erg
+};
+
+struct GridDev {
+    int nx, ny, nz;
+    long long nc;            // cells
+    double dx;               // cm
+    int bc[6];
+};
+
+// Parameters of the thermochemistry kernels.
+struct ThermoParams {
+    long long nc;
+    double dt;               // RT step
+    double cr;               // reduced light speed
+    double X;                // hydrogen mass fraction
+    double he_ratio;         // n_He / n_H = Y / (4 X)
+    double kfac;             // (gamma - 1) X / k_B, so K = kfac / n_H
+    double a_exp;
+    int isothermal;
+    int helium;              // Y > 0
+    int case_b;
+    int max_sub;
+    int pass1_attempts;      // attempts before a cell is handed to the queue
+    GroupConsts gc;
+};
+
+// Device work queue of cells whose sub-cycling outlasted the first pass.
+struct Queue {
+    uint32_t *cell;
+    double *t_left;
+    double *dt_tc;
+    int32_t *attempts;
+    unsigned long long *counters;   // [0] = count, [1] = head
+    long long capacity;
+};
+
+// Per-block partial sums of the photon budget.
+struct Partials {
+    double *tr_inbox;     // [G][n_tr_blocks]  sum N after transport
+    double *tr_outflow;   // [G][n_tr_blocks]  net outflow in the step
+    double *th_inbox;     // [G][n_red_blocks] sum N after thermochemistry
+    int n_tr_blocks;      // per group
+    int n_red_blocks;     // per group
+};
+
+// ---- launchers (defined in the .cu files) ----
+// transport: reads N0/F0, writes N1/F1 for all groups.
+cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
+                             const double *N0, const double *F0, double *N1, double *F1,
+                             const double *hll_table, const Partials &p, cudaStream_t s);
+int transport_blocks_per_group(const GridDev &g);
+void transport_init();   // kernel attributes; called once per handle
+
+// ev (optional, 4 events): recorded around the first pass (0, 1) and
+// around the queue drain (2, 3).
+cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, double *xHII,
+                          double *xHeII, double *xHeIII, double *T, double *N, double *F,
+                          int32_t *subcycles, Queue q, unsigned *status, int n_sm,
+                          cudaStream_t s, cudaEvent_t *ev = nullptr);
+
+cudaError_t launch_inject(int nsrc, int G, long long nc, const long long *cells,
+                          const double *Lsum, double dt_over_V, double *N, cudaStream_t s);
+
+cudaError_t launch_reduce_N(int G, long long nc, const double *N, const Partials &p,
+                            cudaStream_t s);
+
+int reduce_blocks_per_group();
+
+// budget[G][4] cumulative: in_box, absorbed, outflow, emitted.  mode 0
+// closes a step (emitted[G] = photons emitted in it, host array baked into
+// the launch); mode 1 re-initialises at set_state.  Also resets the queue.
+cudaError_t launch_finalize_mode(int G, int mode, const Partials &p, double V, const double *emitted,
+                                 double *budget, Queue q, unsigned *status, cudaStream_t s);
+
+void hll_table(int nf, int nmu, double *out);
+void hll_speeds(double f, double mu, double *lmin, double *lmax);
+
+}  // namespace rtgb

@@ -1,0 +1,391 @@
+// Per-cell non-equilibrium thermochemistry (paper Sec. 3.3 and App. A),
+// sub-cycled under the 10% rule (Sec. 3.3.1, App. A task 5), FP64.
+//
+// One thermo_step(h) follows App. A in its order, forward-in-time values
+// wherever already updated, backward otherwise:
+//   1. N_i, F_i semi-implicitly, Eq. (SIE photons) (OTSA: no creation term)
+//   2. T/mu, Eq. (T integration num eq 2), heating Eq. (PHeat2) with the
+//      new N_i, cooling Eq. (rate_cooling) at T(t) (skipped when isothermal)
+//   3. x_HII, Eq. (xhii_update_2), rates at T = (T/mu)' mu(x(t))
+//   4. x_HeI, x_HeII, x_HeIII, Eqs. (xhei_update), (xheii_update),
+//      (xheiii_update), n_e and mu refreshed before each, then the helium
+//      fractions renormalised by lowering the largest one
+// and rejects the sub-step (halving it) when N_i, T/mu, x_HII or n_e move by
+// more than 10%, or the first-order T and x_HII terms exceed 10%; after a
+// sub-step whose largest change is below 5% the next one is doubled.
+//
+// Load balance: a first pass gives every cell (one thread each, coalesced)
+// a fixed number of attempts; cells still sub-cycling are appended to a
+// device queue with their partial state.  A persistent drain kernel then
+// hands queue items to lanes one at a time: each lane runs one attempt per
+// loop iteration and, when its cell completes, fetches the next item, so a
+// warp stays full while cells with very different sub-cycle counts pass
+// through it.  Nothing waits on another thread; the loop ends when the
+// queue is exhausted.
+#include <cuda_runtime.h>
+
+#include "rates.cuh"
+#include "rt_internal.h"
+
+namespace rtgb {
+namespace {
+
+constexpr double kEV = 1.602176634e-12;
+constexpr double kEps0 = 13.60 * kEV, kEps1 = 24.59 * kEV, kEps2 = 54.42 * kEV;
+constexpr double kFloorN = 1e-30;
+constexpr double kXMin = 1e-6;
+constexpr double kNeFloor = 1e-6;
+constexpr double kTFloor = 1.0;
+
+template <int G>
+struct CellState {
+    double x, y2, y3, T;
+    double N[G];
+    double Fs[G];     // accumulated flux scale prod 1/(1 + h D_i)
+};
+
+struct IsoRates {     // rates at the fixed temperature of an isothermal cell
+    HRates h;
+    HeRates he;
+};
+
+__device__ __forceinline__ double mu_of(double X, double x, double y2, double y3)
+{
+    return 1.0 / (X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3));
+}
+
+// One thermo_step over h.  Returns true and fills `o` and `maxrel` when the
+// 10% rule holds.
+template <int G>
+__device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const CellState<G> &s,
+                                        double h, const IsoRates &iso, CellState<G> &o, double &maxrel)
+{
+    const double nHe = nH * p.he_ratio;
+    const double x = s.x, y2 = s.y2, y3 = s.y3;
+    const double nHI = nH * (1.0 - x);
+    const double nHII = nH * x;
+    const double nHeI = nHe * (1.0 - y2 - y3);
+    const double nHeII = nHe * y2;
+    const double nHeIII = nHe * y3;
+    const double ne = nHII + (y2 + 2.0 * y3) * nHe;
+    const double cr = p.cr;
+    double rel_max = 0.0;
+    double gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
+
+    // 1. photons
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        double D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
+        double inv = 1.0 / (1.0 + h * D);
+        double Nn = s.N[i] * inv;
+        double rel = fabs(Nn - s.N[i]) / fmax(s.N[i], kFloorN);
+        if (rel > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+        o.N[i] = Nn;
+        o.Fs[i] = s.Fs[i] * inv;
+        double crN = cr * Nn;
+        gam0 += p.gc.sigN[i][0] * crN;
+        gam1 += p.gc.sigN[i][1] * crN;
+        gam2 += p.gc.sigN[i][2] * crN;
+        if (!p.isothermal) {
+            heat += crN * (nHI * (p.gc.egy[i] * p.gc.sigE[i][0] - kEps0 * p.gc.sigN[i][0]) +
+                           nHeI * (p.gc.egy[i] * p.gc.sigE[i][1] - kEps1 * p.gc.sigN[i][1]) +
+                           nHeII * (p.gc.egy[i] * p.gc.sigE[i][2] - kEps2 * p.gc.sigN[i][2]));
+        }
+    }
+
+    // 2. temperature
+    const double mu = mu_of(p.X, x, y2, y3);
+    double Tmu1 = 0.0;
+    if (!p.isothermal) {
+        TVars tv = tvars(s.T);
+        double L, dL;
+        cooling(tv, p.case_b, p.a_exp, p.helium != 0, ne, nHI, nHII, nHeI, nHeII, nHeIII, L, dL);
+        double lam = heat - L;
+        double dlam = -mu * dL;
+        double K = p.kfac / nH;
+        double Tmu = s.T / mu;
+        double dT = lam * K * h / (1.0 - dlam * K * h);
+        Tmu1 = Tmu + dT;
+        double rel = fabs(dT) / Tmu;
+        if (rel > 0.1) return false;
+        if (fabs(K * lam * h) / Tmu > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+    }
+
+    // 3. hydrogen
+    HRates hr;
+    if (p.isothermal) {
+        hr = iso.h;
+    } else {
+        h_rates(tvars(Tmu1 * mu), p.case_b, hr);
+    }
+    double C = hr.beta * ne + gam0;
+    double Dd = hr.alpha * ne;
+    double dC = nH * hr.beta, dD = nH * hr.alpha;
+    if (!p.isothermal) {
+        double f = ne * Tmu1 * mu * mu * p.X;
+        dC -= f * hr.dbeta;
+        dD -= f * hr.dalpha;
+    }
+    double J = dC - (C + Dd) - x * (dC + dD);
+    double xdot = C - x * (C + Dd);
+    double x1 = x + h * xdot / (1.0 - J * h);
+    x1 = fmin(fmax(x1, kXMin), 1.0);
+    {
+        double xden = fmax(x, kXMin);
+        double rel = fabs(x1 - x) / xden;
+        if (rel > 0.1) return false;
+        if (fabs(xdot) * h / xden > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+    }
+
+    // 4. helium
+    double y2n = y2, y3n = y3;
+    if (p.helium) {
+        double yI = 1.0 - y2 - y3;
+        double ne2 = x1 * nH + (y2 + 2.0 * y3) * nHe;
+        HeRates r2;
+        if (p.isothermal) r2 = iso.he;
+        else he_rates(tvars(Tmu1 * mu_of(p.X, x1, y2, y3)), p.case_b, true, r2);
+        double C1 = y2 * r2.alpha_HeII * ne2;
+        double D1 = r2.beta_HeI * ne2 + gam1;
+        double yI1 = (yI + C1 * h) / (1.0 + D1 * h);
+        double C2 = yI1 * (r2.beta_HeI * ne2 + gam1) + y3 * r2.alpha_HeIII * ne2;
+        double D2 = (r2.beta_HeII + r2.alpha_HeII) * ne2 + gam2;
+        y2n = (y2 + C2 * h) / (1.0 + D2 * h);
+        double ne3 = x1 * nH + (y2n + 2.0 * y3) * nHe;
+        HeRates r3;
+        if (p.isothermal) r3 = iso.he;
+        else he_rates(tvars(Tmu1 * mu_of(p.X, x1, y2n, y3)), p.case_b, false, r3);
+        double C3 = y2n * (r3.beta_HeII * ne3 + gam2);
+        double D3 = r3.alpha_HeIII * ne3;
+        y3n = (y3 + C3 * h) / (1.0 + D3 * h);
+        // conservation: lower the largest fraction (HeI largest: no change)
+        if (y2n >= yI1 && y2n >= y3n) y2n = 1.0 - yI1 - y3n;
+        else if (y3n >= yI1 && y3n > y2n) y3n = 1.0 - yI1 - y2n;
+        y2n = fmin(fmax(y2n, 0.0), 1.0);
+        y3n = fmin(fmax(y3n, 0.0), 1.0);
+    }
+    {
+        double ne1 = x1 * nH + (y2n + 2.0 * y3n) * nHe;
+        double rel = fabs(ne1 - ne) / fmax(ne, kNeFloor * nH);
+        if (rel > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+    }
+    double Tf = p.isothermal ? s.T : Tmu1 * mu_of(p.X, x1, y2n, y3n);
+    o.x = x1;
+    o.y2 = y2n;
+    o.y3 = y3n;
+    o.T = fmax(Tf, kTFloor);
+    maxrel = rel_max;
+    return true;
+}
+
+// One attempt of the sub-cycling loop; returns true when the cell is done.
+template <int G>
+__device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, CellState<G> &st,
+                                              double &t_left, double &dt_tc, int &att, const IsoRates &iso)
+{
+    double h = (dt_tc < t_left) ? dt_tc : t_left;
+    ++att;
+    CellState<G> o;
+    double mr = 0.0;
+    if (attempt<G>(p, nH, st, h, iso, o, mr)) {
+        st = o;
+        t_left = (h == t_left) ? 0.0 : t_left - h;
+        dt_tc = (mr < 0.05) ? 2.0 * h : h;
+    } else {
+        dt_tc = 0.5 * h;
+    }
+    return !(t_left > 0.0);
+}
+
+template <int G>
+__device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, const double *xHII,
+                                          const double *xHeII, const double *xHeIII, const double *T,
+                                          const double *N, CellState<G> &st, IsoRates &iso)
+{
+    st.x = xHII[c];
+    st.y2 = xHeII[c];
+    st.y3 = xHeIII[c];
+    st.T = T[c];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        st.N[i] = N[(long long)i * p.nc + c];
+        st.Fs[i] = 1.0;
+    }
+    if (p.isothermal) {
+        TVars tv = tvars(st.T);
+        h_rates(tv, p.case_b, iso.h);
+        if (p.helium) he_rates(tv, p.case_b, true, iso.he);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, double *xHII, double *xHeII,
+                                           double *xHeIII, double *T, double *N, double *F,
+                                           const CellState<G> &st, unsigned *status)
+{
+    xHII[c] = st.x;
+    xHeII[c] = st.y2;
+    xHeIII[c] = st.y3;
+    T[c] = st.T;
+    bool bad = !isfinite(st.x) || !isfinite(st.T);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        N[(long long)i * p.nc + c] = st.N[i];
+        if (st.Fs[i] != 1.0) {
+            long long b = 3LL * i * p.nc + c;
+            F[b] *= st.Fs[i];
+            F[b + p.nc] *= st.Fs[i];
+            F[b + 2 * p.nc] *= st.Fs[i];
+        }
+        bad |= !isfinite(st.N[i]);
+    }
+    if (bad) atomicOr(status, kStatusNonFinite);
+}
+
+template <int G>
+__global__ void __launch_bounds__(128)
+thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
+             double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
+{
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = c < p.nc;
+    bool push = false;
+    double t_left = p.dt, dt_tc = p.dt;
+    int att = 0;
+    if (valid) {
+        CellState<G> st;
+        IsoRates iso;
+        load_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, st, iso);
+        double n = nH[c];
+        bool done = false;
+        const int lim = p.pass1_attempts < p.max_sub ? p.pass1_attempts : p.max_sub;
+        for (int k = 0; k < lim && !done; ++k)
+            done = subcycle_once<G>(p, n, st, t_left, dt_tc, att, iso);
+        if (!done && att >= p.max_sub) {
+            atomicOr(status, kStatusSubcycle);
+            done = true;
+        }
+        store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+        if (done) subcycles[c] = att;
+        else push = true;
+    }
+    // warp-aggregated append of unfinished cells
+    unsigned m = __ballot_sync(0xffffffffu, push);
+    if (m) {
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&q.counters[0], (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (push) {
+            unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+            if (slot < (unsigned long long)q.capacity) {
+                q.cell[slot] = (uint32_t)c;
+                q.t_left[slot] = t_left;
+                q.dt_tc[slot] = dt_tc;
+                q.attempts[slot] = att;
+            } else {
+                atomicOr(status, kStatusQueue);
+            }
+        }
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(128)
+thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
+             double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
+{
+    unsigned long long count = q.counters[0];
+    if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
+    if (count == 0) return;
+    CellState<G> st;
+    IsoRates iso;
+    double t_left = 0.0, dt_tc = 0.0, n = 0.0;
+    int att = 0;
+    long long c = -1;
+    bool have = false;
+    unsigned long long it = atomicAdd(&q.counters[1], 1ULL);
+    if (it < count) {
+        c = q.cell[it];
+        t_left = q.t_left[it];
+        dt_tc = q.dt_tc[it];
+        att = q.attempts[it];
+        n = nH[c];
+        load_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, st, iso);
+        have = true;
+    }
+    while (have) {
+        bool done = subcycle_once<G>(p, n, st, t_left, dt_tc, att, iso);
+        if (!done && att >= p.max_sub) {
+            atomicOr(status, kStatusSubcycle);
+            done = true;
+        }
+        if (done) {
+            store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+            subcycles[c] = att;
+            it = atomicAdd(&q.counters[1], 1ULL);
+            if (it < count) {
+                c = q.cell[it];
+                t_left = q.t_left[it];
+                dt_tc = q.dt_tc[it];
+                att = q.attempts[it];
+                n = nH[c];
+                load_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, st, iso);
+            } else {
+                have = false;
+            }
+        }
+    }
+}
+
+template <int G>
+cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, double *xHeII,
+                     double *xHeIII, double *T, double *N, double *F, int32_t *sub, Queue q,
+                     unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
+{
+    const int B = 128;
+    long long nb = (tp.nc + B - 1) / B;
+    if (ev) cudaEventRecord(ev[0], s);
+    thermo_pass1<G><<<(unsigned)nb, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G>, B, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    long long grid = (long long)per_sm * n_sm;
+    long long need = (tp.nc + B - 1) / B;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
+    thermo_drain<G><<<(unsigned)grid, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    if (ev) cudaEventRecord(ev[3], s);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
+                          double *xHeIII, double *T, double *N, double *F, int32_t *subcycles, Queue q,
+                          unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
+{
+    switch (G) {
+    case 1: return launch_g<1>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 2: return launch_g<2>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 3: return launch_g<3>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 4: return launch_g<4>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 5: return launch_g<5>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 6: return launch_g<6>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 7: return launch_g<7>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    case 8: return launch_g<8>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rtgb

@@ -1,0 +1,419 @@
+// Photon transport kernel (paper Sec. 3.2): explicit first-order Godunov
+// update of U = (N, F) for every photon group,
+//     U^{n+1} = U^n + dt/dx * sum_d (Flux_{d, l-1/2} - Flux_{d, l+1/2}),
+// unsplit over the six faces (all from U^n), with the M1 closure
+// P = c^2 N D(f, n) (Sec. 2, Eqs. (edd2), (eddTens), (Udir)) and the GLF
+// (Eq. (glf)) or HLL (Eq. (hll)) intercell flux.
+//
+// Data layout: N[g][z][y][x], F[g][3][z][y][x], x fastest.  One CTA owns a
+// 32 x 8 (x, y) tile of one group and marches along z over a chunk of
+// planes.  Each thread keeps its own column's cells z-1, z, z+1 in
+// registers, so the closure is evaluated once per cell and every z face
+// flux once; the in-plane neighbours (and the one-cell halo ring of the
+// tile, recomputed by the ring threads) go through shared memory, where
+// every x and y face flux is also evaluated once.  Reads and writes of the
+// planes are coalesced 256-byte rows.  Per-block photon sums (in the box
+// after transport, net outflow through boundary faces) go to a partials
+// array reduced later in a fixed order, so the budget is reproducible.
+#include <cuda_runtime.h>
+
+#include "rt_internal.h"
+
+namespace rtgb {
+namespace {
+
+constexpr int TBX = 32;
+constexpr int TBY = 8;
+constexpr int TZC = 16;   // planes per CTA
+constexpr int SW = TBX + 2;
+constexpr int SH = TBY + 2;
+
+struct CellQ {
+    double N, Fx, Fy, Fz;            // U
+    double Pxx, Pxy, Pxz, Pyy, Pyz, Pzz;   // c^2 N D
+    double lmin[3], lmax[3];         // HLL wave speeds (already times c)
+};
+
+__device__ __forceinline__ void hll_lookup(const double *__restrict__ tab, double f, double mu,
+                                           double &lo, double &hi)
+{
+    double fx = f * (double)(kHllNF - 1);
+    int k = (int)floor(fx);
+    k = k < 0 ? 0 : (k > kHllNF - 2 ? kHllNF - 2 : k);
+    double wf = fx - (double)k;
+    double mx = (mu + 1.0) * 0.5 * (double)(kHllNMU - 1);
+    int j = (int)floor(mx);
+    j = j < 0 ? 0 : (j > kHllNMU - 2 ? kHllNMU - 2 : j);
+    double wm = mx - (double)j;
+    const double2 *t = reinterpret_cast<const double2 *>(tab);
+    double2 a = __ldg(&t[k * kHllNMU + j]);
+    double2 b = __ldg(&t[k * kHllNMU + j + 1]);
+    double2 c = __ldg(&t[(k + 1) * kHllNMU + j]);
+    double2 d = __ldg(&t[(k + 1) * kHllNMU + j + 1]);
+    double lo0 = a.x + wm * (b.x - a.x), lo1 = c.x + wm * (d.x - c.x);
+    double hi0 = a.y + wm * (b.y - a.y), hi1 = c.y + wm * (d.y - c.y);
+    lo = lo0 + wf * (lo1 - lo0);
+    hi = hi0 + wf * (hi1 - hi0);
+}
+
+// M1 closure of one cell.  f := 0 for N <= 0 or F = 0; f clamped to 1.
+template <int FLUX>
+__device__ __forceinline__ void closure(double N, double Fx, double Fy, double Fz, double c,
+                                        const double *__restrict__ tab, CellQ &q)
+{
+    q.N = N; q.Fx = Fx; q.Fy = Fy; q.Fz = Fz;
+    double F2 = Fx * Fx + Fy * Fy + Fz * Fz;
+    double f = 0.0, nx = 0.0, ny = 0.0, nz = 0.0;
+    if (N > 0.0 && F2 > 0.0) {
+        double inv = rsqrt(F2);
+        f = fmin((F2 * inv) / (c * N), 1.0);
+        nx = Fx * inv; ny = Fy * inv; nz = Fz * inv;
+    }
+    double f2 = f * f;
+    double chi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
+    double cN = c * c * N;
+    double ca = cN * 0.5 * (1.0 - chi);
+    double cb = cN * 0.5 * (3.0 * chi - 1.0);
+    q.Pxx = ca + cb * nx * nx;
+    q.Pyy = ca + cb * ny * ny;
+    q.Pzz = ca + cb * nz * nz;
+    q.Pxy = cb * nx * ny;
+    q.Pxz = cb * nx * nz;
+    q.Pyz = cb * ny * nz;
+    if (FLUX == RT_HLL) {
+        double lo, hi;
+        hll_lookup(tab, f, nx, lo, hi); q.lmin[0] = lo * c; q.lmax[0] = hi * c;
+        hll_lookup(tab, f, ny, lo, hi); q.lmin[1] = lo * c; q.lmax[1] = hi * c;
+        hll_lookup(tab, f, nz, lo, hi); q.lmin[2] = lo * c; q.lmax[2] = hi * c;
+    }
+}
+
+// Intercell flux along direction D from left cell L to right cell R.
+template <int FLUX, int D>
+__device__ __forceinline__ void face_flux(const CellQ &L, const CellQ &R, double c, double out[4])
+{
+    double fl[4], fr[4], ul[4], ur[4];
+    ul[0] = L.N; ul[1] = L.Fx; ul[2] = L.Fy; ul[3] = L.Fz;
+    ur[0] = R.N; ur[1] = R.Fx; ur[2] = R.Fy; ur[3] = R.Fz;
+    if (D == 0) {
+        fl[0] = L.Fx; fl[1] = L.Pxx; fl[2] = L.Pxy; fl[3] = L.Pxz;
+        fr[0] = R.Fx; fr[1] = R.Pxx; fr[2] = R.Pxy; fr[3] = R.Pxz;
+    } else if (D == 1) {
+        fl[0] = L.Fy; fl[1] = L.Pxy; fl[2] = L.Pyy; fl[3] = L.Pyz;
+        fr[0] = R.Fy; fr[1] = R.Pxy; fr[2] = R.Pyy; fr[3] = R.Pyz;
+    } else {
+        fl[0] = L.Fz; fl[1] = L.Pxz; fl[2] = L.Pyz; fl[3] = L.Pzz;
+        fr[0] = R.Fz; fr[1] = R.Pxz; fr[2] = R.Pyz; fr[3] = R.Pzz;
+    }
+    if (FLUX == RT_HLL) {
+        double lp = fmax(0.0, fmax(L.lmax[D], R.lmax[D]));
+        double lm = fmin(0.0, fmin(L.lmin[D], R.lmin[D]));
+        double den = lp - lm;
+        if (den > 0.0) {
+            double inv = 1.0 / den;
+            double pm = lp * lm;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[k] = (lp * fl[k] - lm * fr[k] + pm * (ur[k] - ul[k])) * inv;
+        } else {
+            // both speeds vanish only for f = 1 beams parallel to the face
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[k] = 0.5 * (fl[k] + fr[k]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = 0.5 * (fl[k] + fr[k]) - 0.5 * c * (ur[k] - ul[k]);
+    }
+}
+
+// Load U at (x, y, z) where at most one coordinate may sit one cell outside
+// the box: that position is the boundary ghost (outflow: copy; reflect:
+// copy with the normal flux negated; periodic: wrap).
+__device__ __forceinline__ void load_U(const GridDev &g, const double *__restrict__ N,
+                                       const double *__restrict__ F, int x, int y, int z,
+                                       double &n, double &fx, double &fy, double &fz)
+{
+    int flip = -1;
+    if (x < 0) {
+        if (g.bc[0] == RT_BC_PERIODIC) x = g.nx - 1; else { x = 0; if (g.bc[0] == RT_BC_REFLECT) flip = 0; }
+    } else if (x >= g.nx) {
+        if (g.bc[1] == RT_BC_PERIODIC) x = 0; else { x = g.nx - 1; if (g.bc[1] == RT_BC_REFLECT) flip = 0; }
+    }
+    if (y < 0) {
+        if (g.bc[2] == RT_BC_PERIODIC) y = g.ny - 1; else { y = 0; if (g.bc[2] == RT_BC_REFLECT) flip = 1; }
+    } else if (y >= g.ny) {
+        if (g.bc[3] == RT_BC_PERIODIC) y = 0; else { y = g.ny - 1; if (g.bc[3] == RT_BC_REFLECT) flip = 1; }
+    }
+    if (z < 0) {
+        if (g.bc[4] == RT_BC_PERIODIC) z = g.nz - 1; else { z = 0; if (g.bc[4] == RT_BC_REFLECT) flip = 2; }
+    } else if (z >= g.nz) {
+        if (g.bc[5] == RT_BC_PERIODIC) z = 0; else { z = g.nz - 1; if (g.bc[5] == RT_BC_REFLECT) flip = 2; }
+    }
+    long long i = ((long long)z * g.ny + y) * g.nx + x;
+    n = __ldg(&N[i]);
+    fx = __ldg(&F[i]);
+    fy = __ldg(&F[g.nc + i]);
+    fz = __ldg(&F[2 * g.nc + i]);
+    if (flip == 0) fx = -fx;
+    if (flip == 1) fy = -fy;
+    if (flip == 2) fz = -fz;
+}
+
+// Shared-memory plane of closure quantities needed by the x and y faces.
+struct PlaneSmem {
+    double N[SH][SW], Fx[SH][SW], Fy[SH][SW], Fz[SH][SW];
+    double Pxx[SH][SW], Pxy[SH][SW], Pxz[SH][SW], Pyy[SH][SW], Pyz[SH][SW];
+    double lminx[SH][SW], lmaxx[SH][SW], lminy[SH][SW], lmaxy[SH][SW];
+    double fxs[4][TBY][TBX + 1];     // x faces 0..32 of each row
+    double fys[4][TBY + 1][TBX];     // y faces 0..8 of each column
+    double red[2][TBX * TBY / 32];
+};
+
+template <int FLUX>
+__device__ __forceinline__ void put_plane(PlaneSmem &s, int r, int c, const CellQ &q)
+{
+    s.N[r][c] = q.N; s.Fx[r][c] = q.Fx; s.Fy[r][c] = q.Fy; s.Fz[r][c] = q.Fz;
+    s.Pxx[r][c] = q.Pxx; s.Pxy[r][c] = q.Pxy; s.Pxz[r][c] = q.Pxz; s.Pyy[r][c] = q.Pyy; s.Pyz[r][c] = q.Pyz;
+    if (FLUX == RT_HLL) {
+        s.lminx[r][c] = q.lmin[0]; s.lmaxx[r][c] = q.lmax[0];
+        s.lminy[r][c] = q.lmin[1]; s.lmaxy[r][c] = q.lmax[1];
+    }
+}
+
+template <int FLUX>
+__device__ __forceinline__ void get_plane(const PlaneSmem &s, int r, int c, CellQ &q)
+{
+    q.N = s.N[r][c]; q.Fx = s.Fx[r][c]; q.Fy = s.Fy[r][c]; q.Fz = s.Fz[r][c];
+    q.Pxx = s.Pxx[r][c]; q.Pxy = s.Pxy[r][c]; q.Pxz = s.Pxz[r][c]; q.Pyy = s.Pyy[r][c]; q.Pyz = s.Pyz[r][c];
+    q.Pzz = 0.0;
+    if (FLUX == RT_HLL) {
+        q.lmin[0] = s.lminx[r][c]; q.lmax[0] = s.lmaxx[r][c];
+        q.lmin[1] = s.lminy[r][c]; q.lmax[1] = s.lmaxy[r][c];
+        q.lmin[2] = 0.0; q.lmax[2] = 0.0;
+    }
+}
+
+template <int FLUX>
+__global__ void __launch_bounds__(TBX * TBY)
+transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double *__restrict__ N0all,
+                 const double *__restrict__ F0all, double *__restrict__ N1all,
+                 double *__restrict__ F1all, const double *__restrict__ tab,
+                 double *__restrict__ part_inbox, double *__restrict__ part_out, int tiles_x,
+                 int tiles_y, int nblk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PlaneSmem &s = *reinterpret_cast<PlaneSmem *>(smem_raw);
+
+    const int grp = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int tile_x = tile % tiles_x;
+    const int tile_y = (tile / tiles_x) % tiles_y;
+    const int zc = tile / (tiles_x * tiles_y);
+    const int x0 = tile_x * TBX, y0 = tile_y * TBY;
+    const int z0 = zc * TZC;
+    const int z1 = min(z0 + TZC, g.nz);
+    const double *N0 = N0all + (long long)grp * g.nc;
+    const double *F0 = F0all + 3LL * grp * g.nc;
+    double *N1 = N1all + (long long)grp * g.nc;
+    double *F1 = F1all + 3LL * grp * g.nc;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TBX + tx;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = (x < g.nx) && (y < g.ny);
+    // ghost-only position of this thread's smem slot (ragged tile edge)
+    const bool ghost_slot = !active && ((x == g.nx && y < g.ny) || (x < g.nx && y == g.ny));
+    const bool bc_x_lo = g.bc[0] != RT_BC_PERIODIC, bc_x_hi = g.bc[1] != RT_BC_PERIODIC;
+    const bool bc_y_lo = g.bc[2] != RT_BC_PERIODIC, bc_y_hi = g.bc[3] != RT_BC_PERIODIC;
+    const bool bc_z_lo = g.bc[4] != RT_BC_PERIODIC, bc_z_hi = g.bc[5] != RT_BC_PERIODIC;
+
+    // halo ring slot of this thread (80 slots: left/right columns, bottom/top rows)
+    int hr = -1, hc = -1, hx = 0, hy = 0;
+    bool hvalid = false;
+    if (tid < 2 * TBY) {
+        int r = tid % TBY, side = tid / TBY;
+        hr = r + 1; hc = side ? TBX + 1 : 0;
+        hx = side ? x0 + TBX : x0 - 1; hy = y0 + r;
+        hvalid = hy < g.ny && hx <= g.nx;
+    } else if (tid < 2 * TBY + 2 * TBX) {
+        int t = tid - 2 * TBY;
+        int cc = t % TBX, side = t / TBX;
+        hr = side ? TBY + 1 : 0; hc = cc + 1;
+        hx = x0 + cc; hy = side ? y0 + TBY : y0 - 1;
+        hvalid = hx < g.nx && hy <= g.ny;
+    }
+
+    CellQ cur, nxt;
+    double flo[4] = {0, 0, 0, 0}, fhi[4] = {0, 0, 0, 0};
+    double inbox = 0.0, outflow = 0.0;
+    if (active) {
+        double n, fx, fy, fz;
+        load_U(g, N0, F0, x, y, z0 - 1, n, fx, fy, fz);
+        CellQ prev;
+        closure<FLUX>(n, fx, fy, fz, c, tab, prev);
+        load_U(g, N0, F0, x, y, z0, n, fx, fy, fz);
+        closure<FLUX>(n, fx, fy, fz, c, tab, cur);
+        face_flux<FLUX, 2>(prev, cur, c, flo);
+    }
+
+    for (int z = z0; z < z1; ++z) {
+        if (active) {
+            double n, fx, fy, fz;
+            load_U(g, N0, F0, x, y, z + 1, n, fx, fy, fz);
+            closure<FLUX>(n, fx, fy, fz, c, tab, nxt);
+            face_flux<FLUX, 2>(cur, nxt, c, fhi);
+            put_plane<FLUX>(s, ty + 1, tx + 1, cur);
+        } else if (ghost_slot) {
+            double n, fx, fy, fz;
+            CellQ q;
+            load_U(g, N0, F0, x, y, z, n, fx, fy, fz);
+            closure<FLUX>(n, fx, fy, fz, c, tab, q);
+            put_plane<FLUX>(s, ty + 1, tx + 1, q);
+        }
+        if (hvalid) {
+            double n, fx, fy, fz;
+            CellQ q;
+            load_U(g, N0, F0, hx, hy, z, n, fx, fy, fz);
+            closure<FLUX>(n, fx, fy, fz, c, tab, q);
+            put_plane<FLUX>(s, hr, hc, q);
+        }
+        __syncthreads();
+
+        // x faces: face f of row ty lies between smem columns f and f+1, at
+        // global x position x0 + f - 1/2; thread tx owns face tx, the last
+        // thread also face TBX
+        if (y < g.ny) {
+            const int nf = (tx == TBX - 1) ? 2 : 1;
+            for (int q = 0; q < nf; ++q) {
+                const int ff = tx + q;   // q = 1 only for the last thread: face TBX
+                const int gxf = x0 + ff;
+                if (gxf <= g.nx) {
+                    CellQ L, R;
+                    get_plane<FLUX>(s, ty + 1, ff, L);
+                    get_plane<FLUX>(s, ty + 1, ff + 1, R);
+                    double fl[4];
+                    face_flux<FLUX, 0>(L, R, c, fl);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) s.fxs[k][ty][ff] = fl[k];
+                    if (gxf == 0 && bc_x_lo) outflow -= fl[0];
+                    if (gxf == g.nx && bc_x_hi) outflow += fl[0];
+                }
+            }
+        }
+        // y faces: face f of column tx lies between smem rows f and f+1
+        if (x < g.nx) {
+            int gyf = y0 + ty;
+            if (gyf <= g.ny) {
+                CellQ L, R;
+                get_plane<FLUX>(s, ty, tx + 1, L);
+                get_plane<FLUX>(s, ty + 1, tx + 1, R);
+                double fl[4];
+                face_flux<FLUX, 1>(L, R, c, fl);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) s.fys[k][ty][tx] = fl[k];
+                if (gyf == 0 && bc_y_lo) outflow -= fl[0];
+                if (gyf == g.ny && bc_y_hi) outflow += fl[0];
+            }
+            if (ty == TBY - 1) {
+                int gyt = y0 + TBY;
+                if (gyt <= g.ny) {
+                    CellQ L, R;
+                    get_plane<FLUX>(s, TBY, tx + 1, L);
+                    get_plane<FLUX>(s, TBY + 1, tx + 1, R);
+                    double fl[4];
+                    face_flux<FLUX, 1>(L, R, c, fl);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) s.fys[k][TBY][tx] = fl[k];
+                    if (gyt == g.ny && bc_y_hi) outflow += fl[0];
+                }
+            }
+        }
+        __syncthreads();
+
+        if (active) {
+            double u[4] = {cur.N, cur.Fx, cur.Fy, cur.Fz};
+            double nw[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double acc = (s.fxs[k][ty][tx] - s.fxs[k][ty][tx + 1]) +
+                             (s.fys[k][ty][tx] - s.fys[k][ty + 1][tx]) + (flo[k] - fhi[k]);
+                nw[k] = u[k] + dtdx * acc;
+            }
+            // realisability |F| <= c N (acts only at rounding level for CFL <= 1)
+            if (nw[0] < 0.0) { nw[0] = 0.0; nw[1] = nw[2] = nw[3] = 0.0; }
+            double F2 = nw[1] * nw[1] + nw[2] * nw[2] + nw[3] * nw[3];
+            double cn = c * nw[0];
+            if (F2 > cn * cn) {
+                double sc = (F2 > 0.0) ? cn * rsqrt(F2) : 0.0;
+                nw[1] *= sc; nw[2] *= sc; nw[3] *= sc;
+            }
+            long long i = ((long long)z * g.ny + y) * g.nx + x;
+            N1[i] = nw[0];
+            F1[i] = nw[1];
+            F1[g.nc + i] = nw[2];
+            F1[2 * g.nc + i] = nw[3];
+            inbox += nw[0];
+            if (z == 0 && bc_z_lo) outflow -= flo[0];
+            if (z == g.nz - 1 && bc_z_hi) outflow += fhi[0];
+            cur = nxt;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) flo[k] = fhi[k];
+        }
+        __syncthreads();
+    }
+
+    // fixed-order block reduction of the two budget sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        inbox += __shfl_down_sync(0xffffffffu, inbox, o);
+        outflow += __shfl_down_sync(0xffffffffu, outflow, o);
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) { s.red[0][warp] = inbox; s.red[1][warp] = outflow; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < TBX * TBY / 32; ++w) { a += s.red[0][w]; b += s.red[1][w]; }
+        part_inbox[(long long)grp * nblk + tile] = a;
+        part_out[(long long)grp * nblk + tile] = b * area_dt;
+    }
+}
+
+}  // namespace
+
+int transport_blocks_per_group(const GridDev &g)
+{
+    int tx = (g.nx + TBX - 1) / TBX;
+    int ty = (g.ny + TBY - 1) / TBY;
+    int tz = (g.nz + TZC - 1) / TZC;
+    return tx * ty * tz;
+}
+
+void transport_init()
+{
+    int smem = (int)sizeof(PlaneSmem);
+    cudaFuncSetAttribute(transport_kernel<RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(transport_kernel<RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
+                             const double *N0, const double *F0, double *N1, double *F1,
+                             const double *hll_table, const Partials &p, cudaStream_t st)
+{
+    int tiles_x = (g.nx + TBX - 1) / TBX;
+    int tiles_y = (g.ny + TBY - 1) / TBY;
+    int nblk = transport_blocks_per_group(g);
+    dim3 grid(nblk, G);
+    dim3 block(TBX, TBY);
+    size_t smem = sizeof(PlaneSmem);
+    double dtdx = dt / g.dx;
+    double area_dt = g.dx * g.dx * dt;
+    if (flux == RT_HLL)
+        transport_kernel<RT_HLL><<<grid, block, smem, st>>>(g, cr, dtdx, area_dt, N0, F0, N1, F1, hll_table,
+                                                            p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+    else
+        transport_kernel<RT_GLF><<<grid, block, smem, st>>>(g, cr, dtdx, area_dt, N0, F0, N1, F1, hll_table,
+                                                            p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+    return cudaGetLastError();
+}
+
+}  // namespace rtgb

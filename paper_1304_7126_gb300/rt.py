@@ -1,0 +1,236 @@
+"""Thin ctypes binding of the rtgb C-ABI (include/rt.h).
+
+Argument marshalling only: every step of the RT path runs in the CUDA
+library ``librtgb.so``.  The functions keep the C names (``rt_create``,
+``rt_step`` ...); :class:`RT` wraps a handle for convenience.  Arrays may be
+numpy float64 arrays (host) or CUDA torch tensors (device pointers); there
+is no CPU fallback: a missing library raises at import of the handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+RT_OK, RT_EINVAL, RT_EDT, RT_ESUBCYCLE, RT_EQUEUE, RT_ECUDA, RT_ENOMEM, RT_ENONFINITE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+RT_BC_OUTFLOW, RT_BC_REFLECT, RT_BC_PERIODIC = 0, 1, 2
+RT_GLF, RT_HLL = 0, 1
+RT_FP64, RT_MIXED = 0, 1
+RT_MAX_GROUPS = 8
+
+ERROR_NAMES = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_EDT", -3: "RT_ESUBCYCLE", -4: "RT_EQUEUE",
+               -5: "RT_ECUDA", -6: "RT_ENOMEM", -7: "RT_ENONFINITE"}
+
+
+class rt_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx_cm", C.c_double),
+                ("bc", C.c_int * 6)]
+
+
+class rt_options(C.Structure):
+    _fields_ = [("X", C.c_double), ("isothermal", C.c_int), ("otsa", C.c_int), ("flux", C.c_int),
+                ("cfl", C.c_double), ("precision", C.c_int), ("a_exp", C.c_double),
+                ("max_subcycles", C.c_int), ("smooth", C.c_int)]
+
+
+class RTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(build: bool = True):
+    """Load librtgb.so (building it with nvcc first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("librtgb.so is not built (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.c_void_p, C.c_void_p
+    L.rt_default_options.argtypes = [C.POINTER(rt_options)]
+    L.rt_default_options.restype = None
+    L.rt_create.argtypes = [C.POINTER(rt_grid), C.c_int, C.POINTER(rt_options), C.c_double, dp, dp, dp,
+                            C.POINTER(vp)]
+    L.rt_destroy.argtypes = [vp]
+    L.rt_destroy.restype = None
+    L.rt_set_stream.argtypes = [vp, vp]
+    L.rt_set_state.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+    L.rt_get_state.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+    L.rt_set_sources.argtypes = [vp, C.c_int, ip, dp]
+    L.rt_courant_dt.argtypes = [vp, C.POINTER(C.c_double)]
+    L.rt_step.argtypes = [vp, C.c_double]
+    L.rt_run.argtypes = [vp, C.c_double, C.c_int]
+    L.rt_get_budget.argtypes = [vp, dp]
+    L.rt_get_subcycles.argtypes = [vp, ip, C.c_int]
+    L.rt_sync.argtypes = [vp]
+    L.rt_last_error.argtypes = [vp]
+    L.rt_last_error.restype = C.c_char_p
+    L.rt_hll_table.argtypes = [C.c_int, C.c_int, dp]
+    L.rt_version.argtypes = []
+    L.rt_set_profiling.argtypes = [vp, C.c_int]
+    L.rt_get_profile.argtypes = [vp, dp, dp]
+    for name in ("rt_create", "rt_set_stream", "rt_set_state", "rt_get_state", "rt_set_sources",
+                 "rt_courant_dt", "rt_step", "rt_run", "rt_get_budget", "rt_get_subcycles", "rt_sync",
+                 "rt_hll_table", "rt_version", "rt_set_profiling", "rt_get_profile"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def _is_dev(a):
+    return a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def rt_hll_table(nf: int = 257, nmu: int = 257) -> np.ndarray:
+    out = np.zeros((nf, nmu, 2))
+    rc = load().rt_hll_table(nf, nmu, _ptr(out))
+    if rc:
+        raise RTError(rc, "rt_hll_table")
+    return out
+
+
+def default_options(**kw) -> rt_options:
+    o = rt_options()
+    load().rt_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class RT:
+    """One rtgb handle: a uniform grid, its photon groups and options."""
+
+    def __init__(self, shape, dx, G, cr, sigN, sigE, egy, bc=(0,) * 6, **opts):
+        L = load()
+        nz, ny, nx = shape
+        self.shape = (nz, ny, nx)
+        self.G = int(G)
+        g = rt_grid()
+        g.nx, g.ny, g.nz = nx, ny, nz
+        g.dx_cm = float(dx)
+        for i in range(6):
+            g.bc[i] = int(bc[i])
+        o = default_options(**opts)
+        sn = np.ascontiguousarray(sigN, dtype=np.float64).reshape(G, 3)
+        se = np.ascontiguousarray(sigE, dtype=np.float64).reshape(G, 3)
+        eg = np.ascontiguousarray(egy, dtype=np.float64).reshape(G)
+        h = C.c_void_p()
+        rc = L.rt_create(C.byref(g), self.G, C.byref(o), float(cr), _ptr(sn), _ptr(se), _ptr(eg), C.byref(h))
+        if rc:
+            raise RTError(rc, "rt_create")
+        self.h = h
+        self.L = L
+
+    @property
+    def ncells(self):
+        nz, ny, nx = self.shape
+        return nz * ny * nx
+
+    def _check(self, rc, what):
+        if rc:
+            raise RTError(rc, "%s: %s" % (what, self.L.rt_last_error(self.h).decode()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        self._check(self.L.rt_set_stream(self.h, stream_ptr), "rt_set_stream")
+
+    def set_state(self, s: dict):
+        keys = ("nH", "xHII", "xHeII", "xHeIII", "T", "N", "F")
+        dev = _is_dev(s["N"])
+        args = [_ptr(s[k]) for k in keys]
+        self._check(self.L.rt_set_state(self.h, *args, int(dev)), "rt_set_state")
+
+    def get_state(self, out: dict | None = None, device=False) -> dict:
+        nc, G = self.ncells, self.G
+        if out is None:
+            if device:
+                import torch
+                mk = lambda n: torch.empty(n, dtype=torch.float64, device="cuda")  # noqa: E731
+            else:
+                mk = lambda n: np.empty(n)  # noqa: E731
+            out = {"nH": mk(nc), "xHII": mk(nc), "xHeII": mk(nc), "xHeIII": mk(nc), "T": mk(nc),
+                   "N": mk(G * nc), "F": mk(3 * G * nc)}
+        keys = ("nH", "xHII", "xHeII", "xHeIII", "T", "N", "F")
+        dev = any(_is_dev(out.get(k)) for k in keys)
+        self._check(self.L.rt_get_state(self.h, *[_ptr(out.get(k)) for k in keys], int(dev)), "rt_get_state")
+        return out
+
+    def set_sources(self, ijk, L):
+        if ijk is None or len(ijk) == 0:
+            self._check(self.L.rt_set_sources(self.h, 0, None, None), "rt_set_sources")
+            return
+        a = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+        l = np.ascontiguousarray(L, dtype=np.float64).reshape(a.shape[0], self.G)
+        self._check(self.L.rt_set_sources(self.h, a.shape[0], _ptr(a), _ptr(l)), "rt_set_sources")
+
+    def courant_dt(self) -> float:
+        d = C.c_double()
+        self._check(self.L.rt_courant_dt(self.h, C.byref(d)), "rt_courant_dt")
+        return d.value
+
+    def step(self, dt: float = 0.0):
+        self._check(self.L.rt_step(self.h, float(dt)), "rt_step")
+
+    def run(self, dt: float, nsteps: int):
+        self._check(self.L.rt_run(self.h, float(dt), int(nsteps)), "rt_run")
+
+    def budget(self) -> np.ndarray:
+        b = np.zeros((self.G, 4))
+        self._check(self.L.rt_get_budget(self.h, _ptr(b)), "rt_get_budget")
+        return b
+
+    def subcycles(self) -> np.ndarray:
+        s = np.zeros(self.ncells, dtype=np.int32)
+        self._check(self.L.rt_get_subcycles(self.h, _ptr(s), 0), "rt_get_subcycles")
+        return s.reshape(self.shape)
+
+    PHASES = ("inject", "transport", "thermo_pass1", "thermo_drain", "reduce", "finalize")
+
+    def set_profiling(self, on: bool):
+        self._check(self.L.rt_set_profiling(self.h, int(bool(on))), "rt_set_profiling")
+
+    def profile(self) -> dict:
+        ms = np.zeros(6)
+        n = np.zeros(6, dtype=np.int64)
+        self._check(self.L.rt_get_profile(self.h, _ptr(ms), _ptr(n)), "rt_get_profile")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PHASES)}
+
+    def sync(self):
+        self._check(self.L.rt_sync(self.h), "rt_sync")
+
+    @classmethod
+    def from_workload(cls, w, **opts):
+        o = dict(X=w.X, isothermal=int(w.isothermal), otsa=int(w.otsa), flux=w.flux, cfl=w.cfl)
+        o.update(opts)
+        r = cls(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, bc=w.bc, **o)
+        r.set_state(w.state())
+        r.set_sources(w.src_ijk, w.src_L)
+        return r

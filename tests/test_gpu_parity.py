@@ -1,0 +1,214 @@
+"""Parity of the CUDA RT step (through the C-ABI) with the FP64 oracle.
+
+Tolerance: 1e-10 relative on N, F, x_HII, x_HeII, x_HeIII and T per field
+(max over cells of |gpu - oracle| / max(|oracle|, 1e-6 max|oracle|)), and
+identical per-cell thermochemistry attempt counts; transport-only cases
+(all cross sections zero) at 1e-12, the flux components there measured
+against their local scale c_r N (a component can be ~0 while |F| is not)."""
+import numpy as np
+import pytest
+
+from parity import compare, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+C_LIGHT = 2.99792458e10
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1304_7126_gb300 import rt
+    rt.load()
+    return rt
+
+
+def _transport_workload(shape, flux, bc, G, seed):
+    from paper_1304_7126_gb300 import workloads as W
+    nz, ny, nx = shape
+    nc = nx * ny * nz
+    rng = np.random.default_rng(seed)
+    w = W.Workload(name="tr", shape=shape, dx=3e20, G=G, cr=C_LIGHT / 100, sigN=np.zeros((G, 3)),
+                   sigE=np.zeros((G, 3)), egy=np.full(G, 3e-11), X=1.0, isothermal=True, otsa=True,
+                   flux=flux, bc=bc, steps=5)
+    w.nH = np.full(nc, 1e-3)
+    w.xHII = np.full(nc, 0.5)
+    w.xHeII = np.zeros(nc)
+    w.xHeIII = np.zeros(nc)
+    w.T = np.full(nc, 1e4)
+    N = 10 ** rng.uniform(-3, 0, size=(G, nc))
+    d = rng.standard_normal((G, 3, nc))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    f = rng.uniform(0, 1, size=(G, 1, nc))
+    F = w.cr * N[:, None, :] * f * d
+    w.src_ijk = np.array([[min(1, nx - 1), min(2, ny - 1), min(3, nz - 1)]], dtype=np.int32)
+    w.src_L = np.full((1, G), 1e55)
+    return w, N.reshape(-1).copy(), F.reshape(-1).copy()
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+@pytest.mark.parametrize("shape,bc", [((37, 21, 37), (0,) * 6), ((13, 9, 40), (1, 0, 2, 2, 0, 1)),
+                                      ((16, 16, 32), (2,) * 6), ((1, 1, 5), (1,) * 6)])
+def test_transport_parity(oracle_mod, R, flux, shape, bc):
+    G = 2
+    w, N, F = _transport_workload(shape, flux, bc, G, 11)
+    sim = R.RT.from_workload(w)
+    s0 = w.state()
+    s0["N"], s0["F"] = N, F
+    sim.set_state(s0)
+    p = oracle_problem(oracle_mod, w)
+    ref = {k: v.copy() for k, v in s0.items()}
+    dt = sim.courant_dt()
+    for step in range(4):
+        sim.step(dt)
+        st, b, _, _ = p.step(ref, dt, w.src_ijk, w.src_L)
+        assert st == 0
+        got = sim.get_state()
+        e = compare(got, ref, ("N", "F"), cr=w.cr, G=G)
+        if not (e["N"] < 1e-12 and e["F"] < 1e-12):
+            d = np.abs(got["N"] - ref["N"]).reshape((G,) + shape)
+            bad = np.argwhere(d > 1e-12 * np.abs(ref["N"]).max())
+            print("worst cells (g, z, y, x):", bad[:20].tolist())
+        assert e["N"] < 1e-12 and e["F"] < 1e-12, (step, e)
+    bud = sim.budget()
+    assert np.allclose(bud[:, 0], b[:, 0], rtol=1e-12)
+
+
+@pytest.mark.parametrize("flux", [1, 0])
+@pytest.mark.parametrize("n,nx,ny", [(16, None, None), (18, 37, 11)])
+def test_full_step_parity_cosmo(oracle_mod, R, flux, n, nx, ny):
+    """H+He, evolving T, 3 groups, sources at the densest cells."""
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.small_cosmo(n, seed=3, nsrc=4, flux=flux, nx=nx, ny=ny)
+    sim = R.RT.from_workload(w)
+    p = oracle_problem(oracle_mod, w, nthreads=4)
+    ref = w.state()
+    dt = sim.courant_dt()
+    for step in range(8):
+        sim.step(dt)
+        st, b, sub_o, mg = p.step(ref, dt, w.src_ijk, w.src_L)
+        assert st == 0
+        sub_g = sim.subcycles()
+        differ = sub_g != sub_o
+        # a schedule may only differ where a 10%/5% decision was a rounding tie
+        assert np.all(mg[differ] < 1e-9), (step, int(differ.sum()))
+        got = sim.get_state()
+        if not differ.any():
+            e = compare(got, ref)
+            assert max(e.values()) < 1e-10, (step, e)
+    assert sub_o.max() > 1
+
+
+def test_stromgren_parity_and_front(oracle_mod, R):
+    """The 32^3 isothermal Stromgren workload: parity for the first 40 steps,
+    then the full 500 Myr on the GPU (CUDA graph) against the analytic front."""
+    import analytic as A
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.stromgren32(32)
+    sim = R.RT.from_workload(w)
+    p = oracle_problem(oracle_mod, w, nthreads=8)
+    ref = w.state()
+    dt = sim.courant_dt()
+    for step in range(40):
+        sim.step(dt)
+        st, _, sub_o, mg = p.step(ref, dt, w.src_ijk, w.src_L)
+    got = sim.get_state()
+    assert np.array_equal(sim.subcycles(), sub_o)
+    e = compare(got, ref, ("N", "F", "xHII"))
+    assert max(e.values()) < 1e-10, e
+    r, _ = oracle_mod.rates(1e4)
+    rS = A.stromgren_radius(w.extra["L_full"], 1e-3, r["alpha_HII"])
+    tr = A.t_rec(1e-3, r["alpha_HII"])
+    done = 40
+    for t_myr in (30.0, 100.0, 200.0, 500.0):
+        k = int(round(t_myr * A.MYR / dt))
+        sim.run(dt, k - done)
+        done = k
+        x = sim.get_state()["xHII"].reshape(w.shape)
+        rn = A.ifront_radius(x, w.dx)
+        assert abs(rn / A.front_radius(k * dt, rS, tr) - 1.0) <= 0.10, (t_myr, rn / rS)
+    assert 0.95 <= rn / rS <= 1.10
+
+
+def test_ledger_and_determinism(R):
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.small_cosmo(20, seed=4, nsrc=3)
+    outs = []
+    for _ in range(2):
+        sim = R.RT.from_workload(w)
+        b0 = sim.budget()
+        in0 = b0[:, 0].copy()
+        assert np.all(b0[:, 1:] == 0)
+        dt = sim.courant_dt()
+        sim.run(dt, 7)
+        sim.step(dt)
+        b = sim.budget()
+        resid = b[:, 3] - (b[:, 0] - in0) - b[:, 1] - b[:, 2]
+        assert np.all(np.abs(resid) <= 1e-12 * b[:, 3])
+        outs.append((sim.get_state(), b, sim.subcycles()))
+        sim.close()
+    for k in outs[0][0]:
+        assert np.array_equal(outs[0][0][k], outs[1][0][k]), k
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_graph_matches_steps(R):
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.small_cosmo(16, seed=6, nsrc=2)
+    a = R.RT.from_workload(w)
+    b = R.RT.from_workload(w)
+    dt = a.courant_dt()
+    for _ in range(5):
+        a.step(dt)
+    b.run(dt, 5)
+    sa, sb = a.get_state(), b.get_state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a.budget(), b.budget())
+
+
+def test_state_roundtrip_device_pointers(R):
+    import torch
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.small_cosmo(12, seed=1, nsrc=1)
+    sim = R.RT.from_workload(w)
+    sim.step()
+    host = sim.get_state()
+    dev = sim.get_state(device=True)
+    for k in host:
+        assert np.array_equal(host[k], dev[k].cpu().numpy()), k
+    sim2 = R.RT.from_workload(w)
+    sim2.set_state(dev)
+    back = sim2.get_state()
+    for k in host:
+        assert np.array_equal(host[k], back[k]), k
+
+
+def test_error_paths(R):
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.small_cosmo(8, seed=2, nsrc=1)
+    sim = R.RT.from_workload(w)
+    dt = sim.courant_dt()
+    with pytest.raises(R.RTError) as ei:
+        sim.step(dt * 1.01)
+    assert ei.value.code == R.RT_EDT
+    s = w.state()
+    s["xHII"][3] = 2.0
+    with pytest.raises(R.RTError) as ei:
+        sim.set_state(s)
+    assert ei.value.code == R.RT_EINVAL
+    with pytest.raises(R.RTError) as ei:
+        sim.set_sources([[99, 0, 0]], [[1.0] * w.G])
+    assert ei.value.code == R.RT_EINVAL
+    # a one-attempt cap is exceeded by the sub-cycling source cells: the
+    # kernel stops those cells and reports RT_ESUBCYCLE; no hang
+    capped = R.RT.from_workload(w, max_subcycles=1)
+    capped.step(dt)
+    with pytest.raises(R.RTError) as ei:
+        capped.sync()
+    assert ei.value.code == R.RT_ESUBCYCLE
+    with pytest.raises(R.RTError):
+        capped.step(dt)          # sticky until set_state
+    capped.set_state(w.state())
+    capped.sync()
