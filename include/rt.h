@@ -106,7 +106,8 @@ int rt_set_stream(rt_handle *h, void *stream);
 
 /* Set the full state (all pointers required).  nH > 0; x_HII in
  * [1e-6, 1]; x_HeII, x_HeIII >= 0 with sum <= 1; T > 0; N >= 0;
- * |F| <= c_r N (1 + 1e-8).  Validated on the host for host pointers;
+ * |F| <= c_r (N (1 + 1e-8) + 1e-290) (the slack covers sub-normal
+ * photon densities left by strong absorption).  Validated on the host for host pointers;
  * device pointers are copied without validation.  Resets the budget. */
 int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const double *xHeII,
                  const double *xHeIII, const double *T, const double *N, const double *F,

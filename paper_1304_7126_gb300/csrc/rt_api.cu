@@ -407,7 +407,7 @@ int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const doubl
                 if (!(std::isfinite(n) && n >= 0.0 && std::isfinite(fx) && std::isfinite(fy) && std::isfinite(fz)))
                     return fail(h, RT_EINVAL, "photon state not finite / negative at cell " + std::to_string(c));
                 double fm = std::sqrt(fx * fx + fy * fy + fz * fz);
-                if (fm > h->cr * n * (1.0 + 1e-8))
+                if (fm > h->cr * (n * (1.0 + 1e-8) + 1e-290))
                     return fail(h, RT_EINVAL, "|F| > c_r N at cell " + std::to_string(c));
             }
         }
