@@ -170,6 +170,34 @@ int rt_set_profiling(rt_handle *h, int enable);
  * enabled, ms [RT_NPHASES], launches [RT_NPHASES].  Synchronises. */
 int rt_get_profile(rt_handle *h, double *ms, int64_t *launches);
 
+/* Allocation-free thermochemistry (no counterpart in the paper): the
+ * sub-cycled thermochemistry of one RT step (what rt_step does after the
+ * transport) applied in place to caller-owned device arrays, for callers
+ * that cannot allocate device memory at call time, such as code running
+ * under another framework that has reserved all device memory for its own
+ * pool, or a loop with a fixed memory footprint that must not call into
+ * the CUDA allocator.  No handle is needed and nothing is allocated: the
+ * work queue lives in a fixed device array of the library, sized for at
+ * most 262144 cells (6.3 MB held on every GPU that loads the library until
+ * the process exits).  ncells above that returns RT_EINVAL, as do the
+ * option values rt_create rejects.
+ * Arguments: ncells cells in any order (one value per cell), the options,
+ * c_r and group constants as for rt_create (host pointers), dt > 0; nH,
+ * xHII, xHeII, xHeIII, T [ncells], N [G][ncells], F [G][3][ncells] and
+ * subcycles [ncells] (attempts per cell, written) are device pointers on
+ * the current device, updated in place on `stream` (a cudaStream_t, NULL =
+ * legacy default stream).  The call waits for the stream and returns
+ * RT_OK or the device status (RT_ESUBCYCLE, RT_EQUEUE, RT_ENONFINITE);
+ * RT_ECUDA if a CUDA call fails.
+ * The first call on each device looks up the array's device address with
+ * that device current (the device must be current when calling); make that
+ * first call before any stream capture.  Every call uses the same array and
+ * clears its counters first; calls that overlap on the GPU race on it. */
+int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_options *opt, double c_r,
+                           const double *sigN, const double *sigE, const double *egy, double dt,
+                           const double *nH, double *xHII, double *xHeII, double *xHeIII,
+                           double *T, double *N, double *F, int32_t *subcycles, void *stream);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 int rt_version(void);
 

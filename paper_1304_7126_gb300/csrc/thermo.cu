@@ -24,6 +24,8 @@
 // queue is exhausted.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "rates.cuh"
 #include "rt_internal.h"
 
@@ -389,3 +391,119 @@ cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, doubl
 }
 
 }  // namespace rtgb
+
+// ---------------------------------------------------------------------------
+// Allocation-free thermochemistry entry point (rt_thermo_step_noalloc).
+//
+// For callers that cannot allocate device memory at call time: the work
+// queue lives in a fixed file-scope device array instead of memory owned by
+// an rt_handle.  Every GPU that loads the library holds this array until
+// the process exits.  All calls share it, and its contents persist from the
+// previous call, so the queue counters and the status word are cleared at
+// the start of every call; calls whose kernels overlap on the GPU race on
+// it and must not be issued.
+namespace rtgb {
+namespace {
+
+constexpr long long kNoAllocMaxCells = 1LL << 18;   // 262144 cells
+// layout: [0,16) queue counters, [16,20) status, queue arrays from byte 256
+constexpr size_t kNoAllocHeader = 256;
+constexpr size_t kNoAllocBytes =
+    kNoAllocHeader + (size_t)kNoAllocMaxCells * (sizeof(uint32_t) + sizeof(int32_t) + 2 * sizeof(double));
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_addr[kMaxDevices] = {};
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_thermo_scratch[kNoAllocBytes];
+
+namespace {
+
+// Device address of g_thermo_scratch on the current device, looked up once
+// per device.  In host code the symbol names a host-side shadow, so only
+// this address may be handed to kernels.
+cudaError_t noalloc_scratch(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_thermo_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+}  // namespace rtgb
+
+extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_options *opt, double c_r,
+                                      const double *sigN, const double *sigE, const double *egy, double dt,
+                                      const double *nH, double *xHII, double *xHeII, double *xHeIII, double *T,
+                                      double *N, double *F, int32_t *subcycles, void *stream)
+{
+    using namespace rtgb;
+    if (ncells < 1 || ncells > kNoAllocMaxCells) return RT_EINVAL;
+    if (n_groups < 1 || n_groups > RT_MAX_GROUPS || !opt || !sigN || !sigE || !egy) return RT_EINVAL;
+    if (!nH || !xHII || !xHeII || !xHeIII || !T || !N || !F || !subcycles) return RT_EINVAL;
+    if (!(c_r > 0.0) || !(dt > 0.0) || !(opt->X > 0.0 && opt->X <= 1.0)) return RT_EINVAL;
+    if (opt->otsa != 1 || opt->smooth != 0 || opt->precision != RT_FP64 || opt->max_subcycles < 1 ||
+        !(opt->a_exp > 0.0))
+        return RT_EINVAL;
+    for (int i = 0; i < 3 * n_groups; ++i)
+        if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0)) return RT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, n_sm = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RT_ECUDA;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RT_ECUDA;
+    unsigned char *base = nullptr;
+    if (noalloc_scratch(dev, &base) != cudaSuccess) return RT_ECUDA;
+
+    ThermoParams tp{};
+    tp.nc = ncells;
+    tp.dt = dt;
+    tp.cr = c_r;
+    tp.X = opt->X;
+    const double Y = 1.0 - opt->X;
+    tp.he_ratio = (Y > 0.0) ? Y / (4.0 * opt->X) : 0.0;
+    tp.kfac = (5.0 / 3.0 - 1.0) * opt->X / 1.380649e-16;
+    tp.a_exp = opt->a_exp;
+    tp.isothermal = opt->isothermal ? 1 : 0;
+    tp.helium = (Y > 0.0) ? 1 : 0;
+    tp.case_b = 1;
+    tp.max_sub = opt->max_subcycles;
+    tp.pass1_attempts = 6;
+    for (int i = 0; i < n_groups; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            tp.gc.sigN[i][j] = sigN[3 * i + j];
+            tp.gc.sigE[i][j] = sigE[3 * i + j];
+        }
+        tp.gc.egy[i] = egy[i];
+    }
+    Queue q{};
+    q.counters = reinterpret_cast<unsigned long long *>(base);
+    unsigned *status = reinterpret_cast<unsigned *>(base + 16);
+    const size_t K = (size_t)kNoAllocMaxCells;
+    q.cell = reinterpret_cast<uint32_t *>(base + kNoAllocHeader);
+    q.attempts = reinterpret_cast<int32_t *>(base + kNoAllocHeader + 4 * K);
+    q.t_left = reinterpret_cast<double *>(base + kNoAllocHeader + 8 * K);
+    q.dt_tc = reinterpret_cast<double *>(base + kNoAllocHeader + 16 * K);
+    q.capacity = ncells;
+
+    if (cudaMemsetAsync(base, 0, kNoAllocHeader, s) != cudaSuccess) return RT_ECUDA;
+    if (launch_thermo(tp, n_groups, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s) !=
+        cudaSuccess)
+        return RT_ECUDA;
+    unsigned st = 0;
+    if (cudaMemcpyAsync(&st, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RT_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RT_ECUDA;
+    if (st & kStatusNonFinite) return RT_ENONFINITE;
+    if (st & kStatusSubcycle) return RT_ESUBCYCLE;
+    if (st & kStatusQueue) return RT_EQUEUE;
+    return RT_OK;
+}

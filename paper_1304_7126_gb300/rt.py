@@ -76,6 +76,9 @@ def load(build: bool = True):
     L.rt_last_error.restype = C.c_char_p
     L.rt_hll_table.argtypes = [C.c_int, C.c_int, dp]
     L.rt_version.argtypes = []
+    L.rt_thermo_step_noalloc.argtypes = [C.c_longlong, C.c_int, C.POINTER(rt_options), C.c_double, dp, dp,
+                                         dp, C.c_double, dp, dp, dp, dp, dp, dp, dp, ip, vp]
+    L.rt_thermo_step_noalloc.restype = C.c_int
     L.rt_set_profiling.argtypes = [vp, C.c_int]
     L.rt_get_profile.argtypes = [vp, dp, dp]
     for name in ("rt_create", "rt_set_stream", "rt_set_state", "rt_get_state", "rt_set_sources",
@@ -105,6 +108,19 @@ def rt_hll_table(nf: int = 257, nmu: int = 257) -> np.ndarray:
     if rc:
         raise RTError(rc, "rt_hll_table")
     return out
+
+
+def rt_thermo_step_noalloc(ncells, G, opt, cr, sigN, sigE, egy, dt, state: dict, subcycles,
+                           stream=None) -> int:
+    """Allocation-free thermochemistry on caller-owned device arrays (torch
+    CUDA tensors, updated in place); returns the C status code."""
+    sn = np.ascontiguousarray(sigN, dtype=np.float64).reshape(G, 3)
+    se = np.ascontiguousarray(sigE, dtype=np.float64).reshape(G, 3)
+    eg = np.ascontiguousarray(egy, dtype=np.float64).reshape(G)
+    keys = ("nH", "xHII", "xHeII", "xHeIII", "T", "N", "F")
+    return load().rt_thermo_step_noalloc(int(ncells), int(G), C.byref(opt), float(cr), _ptr(sn), _ptr(se),
+                                         _ptr(eg), float(dt), *[_ptr(state[k]) for k in keys],
+                                         _ptr(subcycles), stream)
 
 
 def default_options(**kw) -> rt_options:
