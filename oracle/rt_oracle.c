@@ -412,9 +412,14 @@ static double transport_group(const oracle_cfg *cfg, double dt, double *N, doubl
         double fy = U0[4 * q + 2] + dt / dx * acc[4 * q + 2];
         double fz = U0[4 * q + 3] + dt / dx * acc[4 * q + 3];
         if (Nn < 0.0) { Nn = 0.0; fx = fy = fz = 0.0; }
-        double Fm = sqrt(fx * fx + fy * fy + fz * fz);
-        if (Fm > c * Nn) {
-            double s = (Fm > 0.0) ? c * Nn / Fm : 0.0;
+        /* |F| of a tiny state is taken on values scaled by 2^600 (exact),
+         * since squares below ~1e-154 lose digits */
+        double mx = fmax(fmax(fabs(fx), fabs(fy)), fmax(fabs(fz), c * Nn));
+        double sc = (mx < 1e-140) ? ldexp(1.0, 600) : 1.0;
+        double Fm = sqrt((fx * sc) * (fx * sc) + (fy * sc) * (fy * sc) + (fz * sc) * (fz * sc));
+        double cNs = c * Nn * sc;
+        if (Fm > cNs) {
+            double s = (Fm > 0.0) ? cNs / Fm : 0.0;
             fx *= s; fy *= s; fz *= s;
         }
         N[q] = Nn;

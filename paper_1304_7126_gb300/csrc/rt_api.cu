@@ -406,7 +406,12 @@ int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const doubl
                        fz = F[((size_t)3 * g + 2) * nc + c];
                 if (!(std::isfinite(n) && n >= 0.0 && std::isfinite(fx) && std::isfinite(fy) && std::isfinite(fz)))
                     return fail(h, RT_EINVAL, "photon state not finite / negative at cell " + std::to_string(c));
-                double fm = std::sqrt(fx * fx + fy * fy + fz * fz);
+                double mx = std::max(std::max(std::fabs(fx), std::fabs(fy)), std::fabs(fz));
+                double fm = 0.0;
+                if (mx > 0.0) {
+                    double a = fx / mx, b = fy / mx, d = fz / mx;
+                    fm = mx * std::sqrt(a * a + b * b + d * d);
+                }
                 if (fm > h->cr * (n * (1.0 + 1e-8) + 1e-290))
                     return fail(h, RT_EINVAL, "|F| > c_r N at cell " + std::to_string(c));
             }

@@ -340,10 +340,15 @@ transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double 
             }
             // realisability |F| <= c N (acts only at rounding level for CFL <= 1)
             if (nw[0] < 0.0) { nw[0] = 0.0; nw[1] = nw[2] = nw[3] = 0.0; }
-            double F2 = nw[1] * nw[1] + nw[2] * nw[2] + nw[3] * nw[3];
+            // squares of values below ~1e-154 lose digits: compare tiny
+            // states scaled by 2^600 (exact), the factor is scale-free
             double cn = c * nw[0];
-            if (F2 > cn * cn) {
-                double sc = (F2 > 0.0) ? cn * rsqrt(F2) : 0.0;
+            double m = fmax(fmax(fabs(nw[1]), fabs(nw[2])), fmax(fabs(nw[3]), cn));
+            double s = (m < 1e-140) ? 0x1p600 : 1.0;
+            double f1 = nw[1] * s, f2 = nw[2] * s, f3 = nw[3] * s, cs = cn * s;
+            double F2 = f1 * f1 + f2 * f2 + f3 * f3;
+            if (F2 > cs * cs) {
+                double sc = (F2 > 0.0) ? cs * rsqrt(F2) : 0.0;
                 nw[1] *= sc; nw[2] *= sc; nw[3] *= sc;
             }
             long long i = ((long long)z * g.ny + y) * g.nx + x;
