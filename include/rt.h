@@ -178,7 +178,7 @@ int rt_get_profile(rt_handle *h, double *ms, int64_t *launches);
  * pool, or a loop with a fixed memory footprint that must not call into
  * the CUDA allocator.  No handle is needed and nothing is allocated: the
  * work queue lives in a fixed device array of the library, sized for at
- * most 262144 cells (6.3 MB held on every GPU that loads the library until
+ * most 262144 cells (12.6 MB held on every GPU that loads the library until
  * the process exits).  ncells above that returns RT_EINVAL, as do the
  * option values rt_create rejects.
  * Arguments: ncells cells in any order (one value per cell), the options,

@@ -4,157 +4,229 @@
 // 1992; bremsstrahlung; Compton: Haiman et al. 1996; dielectronic: Black
 // 1981), each with its analytic temperature derivative, in FP64.
 //
-// Transcendentals are shared: ln T, sqrt T and 1/T once per temperature;
-// each Boltzmann factor exp(-T0/T) serves both the collisional ionisation
-// rate and its cooling rate; every Hui & Gnedin form
-// A lam^p / (1 + (lam/l0)^r)^s is one log1p and two exp.
+// Evaluation is split in two stages so that the same arithmetic can be done
+// by one thread or spread over the lanes of a warp:
+//   1. transcendentals of one temperature (struct Transc): ln T, sqrt T,
+//      1/T, and twelve exponentials exp(a ln T + b/T + c) - the Boltzmann
+//      factors exp(-T0/T), the power laws, and w = (lam/l0)^r of the four
+//      Hui & Gnedin fits A lam^p / (1 + w)^s - then log1p(w) and
+//      exp(p ln lam - s log1p(w)) of those four fits;
+//   2. assembly of the rates and derivatives from Transc (plain arithmetic).
+// transc_serial computes stage 1 in one thread; transc_warp lets lane k of a
+// warp evaluate exponential k, so a warp pays for three exponential levels
+// instead of twenty transcendental calls.  Both use identical expressions,
+// so they give identical bits.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace rtgb {
 
-struct TVars {
-    double T, invT, lnT, sqrtT, u;   // u = 1 / (1 + sqrt(T / 1e5))
+// exp arguments: exp(fma(a, ln T, fma(b, 1/T, c)))
+enum {
+    E_BETA_HI = 0,   // exp(-157809.1/T): beta_HI, zeta_HI
+    E_BETA_HEI,      // exp(-285335.4/T): beta_HeI, zeta_HeI
+    E_BETA_HEII,     // exp(-631515/T):   beta_HeII, zeta_HeII
+    E_PSI_HI,        // exp(-118348/T)
+    E_PSI_HEII,      // T^-0.397 exp(-473638/T)
+    E_OMEGA1,        // T^-1.5 exp(-470000/T)
+    E_OMEGA2,        // exp(-94000/T)
+    E_ALPHA_HEII,    // (570670/T)^p
+    E_W0,            // w of the Hui & Gnedin fits HG_*
+    NEXP = E_W0 + 4
+};
+enum { HG_ALPHA_HII = 0, HG_ALPHA_HEIII, HG_ETA_HII, HG_ETA_HEIII, NHG };
+
+struct ExpArg {
+    double a, b, c;
+};
+struct HGPar {
+    double A, lnT1, p, r, s;   // A lam^p / (1 + w)^s, lam = T1/T, w = (lam/l0)^r
+};
+struct RateTable {           // one per recombination case (A, B)
+    ExpArg ea[NEXP];
+    HGPar hg[NHG];
+    double A_aHeII, p_aHeII;  // alpha_HeII = A (570670/T)^p
 };
 
-__device__ __forceinline__ TVars tvars(double T)
+struct Transc {
+    double lnT, sqrtT, invT, u;   // u = 1 / (1 + sqrt(T / 1e5))
+    double e[NEXP];
+    double l[NHG];                 // log1p(w)
+    double v[NHG];                 // exp(p ln lam - s log1p(w))
+};
+
+// Rate tables: exp(a ln T + b/T + c) arguments and the Hui &
+// Gnedin parameters, case A then case B; the logarithms are of the fits'
+// temperature constants and pivots.
+static __constant__ RateTable c_rate_tab[2] = {
+    { // case A
+        {{0.0, -157809.1, 0.0}, {0.0, -285335.4, 0.0}, {0.0, -631515.0, 0.0}, {0.0, -118348.0, 0.0}, {-0.397, -473638.0, 0.0}, {-1.5, -470000.0, 0.0}, {0.0, -94000.0, 0.0}, {-0.654, 0.0, 8.668486417830579}, {-0.47, 0.0, 6.2568105714688285}, {-0.47, 0.0, 6.908582567206}, {-0.502, 0.0, 6.664858835981581}, {-0.502, 0.0, 7.361006797385964}},
+        {{1.269e-13, 12.662275226919286, 1.503, 0.47, 1.923}, {2.538e-13, 14.049024154019651, 1.503, 0.47, 1.923}, {1.778e-29, 12.662275226919286, 1.965, 0.502, 2.697}, {1.4224e-28, 14.049024154019651, 1.965, 0.502, 2.697}},
+        3e-14, 0.654 },
+    { // case B
+        {{0.0, -157809.1, 0.0}, {0.0, -285335.4, 0.0}, {0.0, -631515.0, 0.0}, {0.0, -118348.0, 0.0}, {-0.397, -473638.0, 0.0}, {-1.5, -470000.0, 0.0}, {0.0, -94000.0, 0.0}, {-0.75, 0.0, 9.940924791090113}, {-0.407, 0.0, 4.743307143753357}, {-0.407, 0.0, 5.307713957083206}, {-0.376, 0.0, 4.456105724024312}, {-0.376, 0.0, 4.977523320614049}},
+        {{2.753e-14, 12.662275226919286, 1.5, 0.407, 2.242}, {5.506e-14, 14.049024154019651, 1.5, 0.407, 2.242}, {3.435e-30, 12.662275226919286, 1.97, 0.376, 3.72}, {2.748e-29, 14.049024154019651, 1.97, 0.376, 3.72}},
+        1.26e-14, 0.75 }
+};
+
+__device__ __forceinline__ void transc_level0(double T, Transc &t)
 {
-    TVars v;
-    v.T = T;
-    v.invT = 1.0 / T;
-    v.lnT = log(T);
-    v.sqrtT = sqrt(T);
-    v.u = 1.0 / (1.0 + v.sqrtT * 0.003162277660168379);
-    return v;
+    t.lnT = log(T);
+    t.sqrtT = sqrt(T);
+    t.invT = 1.0 / T;
+    t.u = 1.0 / (1.0 + t.sqrtT * 0.003162277660168379);
 }
 
-// A sqrt(T) u exp(-T0/T), given e = exp(-T0/T)
-__device__ __forceinline__ void cen_fit(double A, double T0, double e, const TVars &t, double &v, double &dv)
+__device__ __forceinline__ double exp_arg(const ExpArg &q, const Transc &t)
+{
+    return fma(q.a, t.lnT, fma(q.b, t.invT, q.c));
+}
+
+__device__ __forceinline__ double hg_arg(const HGPar &h, double lnT, double l)
+{
+    return h.p * (h.lnT1 - lnT) - h.s * l;
+}
+
+// Stage 1 in one thread.  need: bit k of the exponentials E_*, bit NEXP + j
+// of the Hui & Gnedin fits j.
+__device__ __forceinline__ void transc_serial(double T, int case_b, unsigned need, Transc &t)
+{
+    const RateTable &R = c_rate_tab[case_b];
+    transc_level0(T, t);
+#pragma unroll
+    for (int k = 0; k < NEXP; ++k)
+        if (need & (1u << k)) t.e[k] = exp(exp_arg(R.ea[k], t));
+#pragma unroll
+    for (int j = 0; j < NHG; ++j) {
+        if (need & (1u << (NEXP + j))) {
+            t.l[j] = log1p(t.e[E_W0 + j]);
+            t.v[j] = exp(hg_arg(R.hg[j], t.lnT, t.l[j]));
+        }
+    }
+}
+
+// Stage 1 spread over a full warp (all 32 lanes must call it with the same
+// T); every lane ends with the complete, identical Transc.
+__device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
+{
+    const RateTable &R = c_rate_tab[case_b];
+    const int lane = threadIdx.x & 31;
+    transc_level0(T, t);
+    const int k = lane < NEXP ? lane : 0;
+    double ek = exp(exp_arg(R.ea[k], t));
+    const int j = lane & 3;
+    double wj = __shfl_sync(0xffffffffu, ek, E_W0 + j);
+    double lj = log1p(wj);
+    double vj = exp(hg_arg(R.hg[j], t.lnT, lj));
+#pragma unroll
+    for (int q = 0; q < NEXP; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
+#pragma unroll
+    for (int q = 0; q < NHG; ++q) {
+        t.l[q] = __shfl_sync(0xffffffffu, lj, q);
+        t.v[q] = __shfl_sync(0xffffffffu, vj, q);
+    }
+}
+
+// d ln v / dT of a Hui & Gnedin fit: -(1/T) (p - s r w / (1 + w))
+__device__ __forceinline__ double hg_dlog(const HGPar &h, const Transc &t, int j)
+{
+    double w = t.e[E_W0 + j];
+    return -t.invT * (h.p - h.s * h.r * w / (1.0 + w));
+}
+
+// bits of Transc needed by each consumer
+constexpr unsigned kNeedH = (1u << E_BETA_HI) | (1u << E_W0) | (1u << (NEXP + HG_ALPHA_HII));
+constexpr unsigned kNeedHe = (1u << E_BETA_HEI) | (1u << E_BETA_HEII) | (1u << E_ALPHA_HEII) |
+                             (1u << (E_W0 + HG_ALPHA_HEIII)) | (1u << (NEXP + HG_ALPHA_HEIII));
+constexpr unsigned kNeedHe3 = (1u << E_BETA_HEII) | (1u << (E_W0 + HG_ALPHA_HEIII)) |
+                              (1u << (NEXP + HG_ALPHA_HEIII));
+constexpr unsigned kNeedCoolH = (1u << E_BETA_HI) | (1u << E_PSI_HI) | (1u << (E_W0 + HG_ETA_HII)) |
+                                (1u << (NEXP + HG_ETA_HII));
+constexpr unsigned kNeedCoolHe = (1u << E_BETA_HEI) | (1u << E_BETA_HEII) | (1u << E_PSI_HEII) |
+                                 (1u << E_OMEGA1) | (1u << E_OMEGA2) | (1u << E_ALPHA_HEII) |
+                                 (1u << (E_W0 + HG_ETA_HEIII)) | (1u << (NEXP + HG_ETA_HEIII));
+
+struct HRates {       // rates needed by the x_HII update
+    double beta, dbeta, alpha, dalpha;
+};
+struct HeRates {
+    double beta_HeI, beta_HeII, alpha_HeII, alpha_HeIII;
+};
+
+// Cen (1992) form A sqrt(T) u exp(-T0/T)
+__device__ __forceinline__ void cen_fit(double A, double T0, double e, const Transc &t, double &v, double &dv)
 {
     v = A * t.sqrtT * t.u * e;
     dv = v * (0.5 * t.u * t.invT + T0 * t.invT * t.invT);
 }
 
-// A lam^p / (1 + (lam/l0)^r)^s, lam = T1 / T; lnT1 = ln T1, lnl0 = ln l0
-__device__ __forceinline__ void hg_fit(double A, double lnT1, double p, double lnl0, double r, double s,
-                                       const TVars &t, double &v, double &dv)
+__device__ __forceinline__ void h_rates_from(const Transc &t, int case_b, HRates &r)
 {
-    double lnlam = lnT1 - t.lnT;
-    double w = exp(r * (lnlam - lnl0));
-    double l1w = log1p(w);
-    v = A * exp(p * lnlam - s * l1w);
-    dv = -v * t.invT * (p - s * r * w / (1.0 + w));
+    const RateTable &R = c_rate_tab[case_b];
+    cen_fit(5.85e-11, 157809.1, t.e[E_BETA_HI], t, r.beta, r.dbeta);
+    r.alpha = R.hg[HG_ALPHA_HII].A * t.v[HG_ALPHA_HII];
+    r.dalpha = r.alpha * hg_dlog(R.hg[HG_ALPHA_HII], t, HG_ALPHA_HII);
 }
 
-// A lam^p, lam = T1 / T
-__device__ __forceinline__ void pow_fit(double A, double lnT1, double p, const TVars &t, double &v, double &dv)
+__device__ __forceinline__ void he_rates_from(const Transc &t, int case_b, HeRates &r)
 {
-    v = A * exp(p * (lnT1 - t.lnT));
-    dv = -v * p * t.invT;
-}
-
-// ln of the fit temperatures and pivots
-#define RTGB_LN_315614 12.662275226919286     // HI
-#define RTGB_LN_570670 13.254566388120152     // HeI
-#define RTGB_LN_1263030 14.049024154019651    // HeII
-#define RTGB_LN_2_74 1.007957920399979
-#define RTGB_LN_0_522 -0.6500876910994983
-#define RTGB_LN_2_25 0.8109302162163288
-#define RTGB_LN_0_541 -0.6143360001356555
-
-struct HRates {       // rates needed by the x_HII update
-    double beta, dbeta, alpha, dalpha;
-};
-
-__device__ __forceinline__ void h_rates(const TVars &t, int case_b, HRates &r)
-{
-    cen_fit(5.85e-11, 157809.1, exp(-157809.1 * t.invT), t, r.beta, r.dbeta);
-    if (case_b)
-        hg_fit(2.753e-14, RTGB_LN_315614, 1.5, RTGB_LN_2_74, 0.407, 2.242, t, r.alpha, r.dalpha);
-    else
-        hg_fit(1.269e-13, RTGB_LN_315614, 1.503, RTGB_LN_0_522, 0.47, 1.923, t, r.alpha, r.dalpha);
-}
-
-struct HeRates {
-    double beta_HeI, beta_HeII, alpha_HeII, alpha_HeIII;
-};
-
-__device__ __forceinline__ void he_rates(const TVars &t, int case_b, bool need_hei, HeRates &r)
-{
+    const RateTable &R = c_rate_tab[case_b];
     double d;
-    if (need_hei) {
-        cen_fit(2.38e-11, 285335.4, exp(-285335.4 * t.invT), t, r.beta_HeI, d);
-        if (case_b) pow_fit(1.26e-14, RTGB_LN_570670, 0.75, t, r.alpha_HeII, d);
-        else pow_fit(3e-14, RTGB_LN_570670, 0.654, t, r.alpha_HeII, d);
-    }
-    cen_fit(5.68e-12, 631515.0, exp(-631515.0 * t.invT), t, r.beta_HeII, d);
-    if (case_b)
-        hg_fit(5.506e-14, RTGB_LN_1263030, 1.5, RTGB_LN_2_74, 0.407, 2.242, t, r.alpha_HeIII, d);
-    else
-        hg_fit(2.538e-13, RTGB_LN_1263030, 1.503, RTGB_LN_0_522, 0.47, 1.923, t, r.alpha_HeIII, d);
+    cen_fit(2.38e-11, 285335.4, t.e[E_BETA_HEI], t, r.beta_HeI, d);
+    cen_fit(5.68e-12, 631515.0, t.e[E_BETA_HEII], t, r.beta_HeII, d);
+    r.alpha_HeII = R.A_aHeII * t.e[E_ALPHA_HEII];
+    r.alpha_HeIII = R.hg[HG_ALPHA_HEIII].A * t.v[HG_ALPHA_HEIII];
 }
 
 // Primordial cooling magnitude L (Eq. (rate_cooling), positive = cooling)
-// and dL/dT, for the given absorber/ion densities and electron density.
-__device__ __forceinline__ void cooling(const TVars &t, int case_b, double a_exp, bool helium, double ne,
-                                        double nHI, double nHII, double nHeI, double nHeII, double nHeIII,
-                                        double &L, double &dL)
+// and dL/dT for the given densities and electron density.
+__device__ __forceinline__ void cooling_from(const Transc &t, int case_b, double a_exp, bool helium, double T,
+                                             double ne, double nHI, double nHII, double nHeI, double nHeII,
+                                             double nHeIII, double &L, double &dL)
 {
+    const RateTable &R = c_rate_tab[case_b];
     const double kB = 1.380649e-16;
     double v, dv;
-    double e1 = exp(-157809.1 * t.invT);
-    double e4 = exp(-118348.0 * t.invT);
-    // zeta_HI + psi_HI on n_e n_HI
-    cen_fit(1.27e-21, 157809.1, e1, t, v, dv);
-    double psi = 7.5e-19 * t.u * e4;
+    cen_fit(1.27e-21, 157809.1, t.e[E_BETA_HI], t, v, dv);
+    double psi = 7.5e-19 * t.u * t.e[E_PSI_HI];
     double dpsi = psi * (-0.5 * (1.0 - t.u) * t.invT + 118348.0 * t.invT * t.invT);
     double Ls = (v + psi) * nHI;
     double dLs = (dv + dpsi) * nHI;
-    // recombination cooling eta_HII T-form
-    double eta, deta;
-    if (case_b) hg_fit(3.435e-30, RTGB_LN_315614, 1.97, RTGB_LN_2_25, 0.376, 3.72, t, eta, deta);
-    else hg_fit(1.778e-29, RTGB_LN_315614, 1.965, RTGB_LN_0_541, 0.502, 2.697, t, eta, deta);
-    Ls += t.T * eta * nHII;
-    dLs += (eta + t.T * deta) * nHII;
-    // bremsstrahlung
+    double eta = R.hg[HG_ETA_HII].A * t.v[HG_ETA_HII];
+    double deta = eta * hg_dlog(R.hg[HG_ETA_HII], t, HG_ETA_HII);
+    Ls += T * eta * nHII;
+    dLs += (eta + T * deta) * nHII;
     double th = 1.42e-27 * t.sqrtT;
     double dth = 0.5 * th * t.invT;
     Ls += th * (nHII + nHeII + 4.0 * nHeIII);
     dLs += dth * (nHII + nHeII + 4.0 * nHeIII);
     if (helium) {
-        double e2 = exp(-285335.4 * t.invT);
-        double e3 = exp(-631515.0 * t.invT);
-        cen_fit(9.38e-22, 285335.4, e2, t, v, dv);
+        cen_fit(9.38e-22, 285335.4, t.e[E_BETA_HEI], t, v, dv);
         Ls += v * nHeI;
         dLs += dv * nHeI;
-        // HeII: zeta + psi + eta + omega
         double zs, dzs;
-        cen_fit(4.95e-22, 631515.0, e3, t, zs, dzs);
-        double p2 = 5.54e-17 * t.u * exp(-0.397 * t.lnT - 473638.0 * t.invT);
+        cen_fit(4.95e-22, 631515.0, t.e[E_BETA_HEII], t, zs, dzs);
+        double p2 = 5.54e-17 * t.u * t.e[E_PSI_HEII];
         double dp2 = p2 * (-0.397 * t.invT - 0.5 * (1.0 - t.u) * t.invT + 473638.0 * t.invT * t.invT);
-        double a2, da2;
-        if (case_b) pow_fit(1.26e-14, RTGB_LN_570670, 0.75, t, a2, da2);
-        else pow_fit(3e-14, RTGB_LN_570670, 0.654, t, a2, da2);
-        double et2 = kB * t.T * a2;
-        double det2 = kB * (a2 + t.T * da2);
-        double e7 = exp(-94000.0 * t.invT);
-        double base = 1.24e-13 * exp(-1.5 * t.lnT - 470000.0 * t.invT);
+        double a2 = R.A_aHeII * t.e[E_ALPHA_HEII];
+        double da2 = -a2 * R.p_aHeII * t.invT;
+        double et2 = kB * T * a2;
+        double det2 = kB * (a2 + T * da2);
+        double base = 1.24e-13 * t.e[E_OMEGA1];
+        double e7 = t.e[E_OMEGA2];
         double om = base * (1.0 + 0.3 * e7);
         double dom = om * (-1.5 * t.invT + 470000.0 * t.invT * t.invT) + base * 0.3 * e7 * 94000.0 * t.invT * t.invT;
         Ls += (zs + p2 + et2 + om) * nHeII;
         dLs += (dzs + dp2 + det2 + dom) * nHeII;
-        // HeIII recombination cooling
-        double e3h, de3h;
-        if (case_b) hg_fit(8.0 * 3.435e-30, RTGB_LN_1263030, 1.97, RTGB_LN_2_25, 0.376, 3.72, t, e3h, de3h);
-        else hg_fit(8.0 * 1.778e-29, RTGB_LN_1263030, 1.965, RTGB_LN_0_541, 0.502, 2.697, t, e3h, de3h);
-        Ls += t.T * e3h * nHeIII;
-        dLs += (e3h + t.T * de3h) * nHeIII;
+        double e3h = R.hg[HG_ETA_HEIII].A * t.v[HG_ETA_HEIII];
+        double de3h = e3h * hg_dlog(R.hg[HG_ETA_HEIII], t, HG_ETA_HEIII);
+        Ls += T * e3h * nHeIII;
+        dLs += (e3h + T * de3h) * nHeIII;
     }
-    // Compton (signed) on n_e
     double Tg = 2.727 / a_exp;
     double Tg4 = Tg * Tg * Tg * Tg;
-    double vp = 1.017e-37 * Tg4 * (t.T - Tg);
+    double vp = 1.017e-37 * Tg4 * (T - Tg);
     L = ne * (Ls + vp);
     dL = ne * (dLs + 1.017e-37 * Tg4);
 }

@@ -108,8 +108,8 @@ void free_all(rt_handle *h)
     for (cudaEvent_t e : h->pending) cudaEventDestroy(e);
     h->pending.clear();
     void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
-                    h->hll, h->subcycles, h->q.cell, h->q.t_left, h->q.dt_tc, h->q.attempts,
-                    h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
+                    h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
+                    h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
                     h->budget, h->status, h->src_cell, h->src_L};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -329,9 +329,11 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
             (rc = dalloc(h, &h->N[0], G * nc)) || (rc = dalloc(h, &h->N[1], G * nc)) ||
             (rc = dalloc(h, &h->F[0], 3 * G * nc)) || (rc = dalloc(h, &h->F[1], 3 * G * nc)) ||
             (rc = dalloc(h, &h->hll, (size_t)kHllNF * kHllNMU * 2)) || (rc = dalloc(h, &h->subcycles, nc)) ||
-            (rc = dalloc(h, &h->q.cell, nc)) || (rc = dalloc(h, &h->q.t_left, nc)) ||
-            (rc = dalloc(h, &h->q.dt_tc, nc)) || (rc = dalloc(h, &h->q.attempts, nc)) ||
-            (rc = dalloc(h, &h->q.counters, 2)) ||
+            (rc = dalloc(h, &h->q.a.cell, nc)) || (rc = dalloc(h, &h->q.a.t_left, nc)) ||
+            (rc = dalloc(h, &h->q.a.dt_tc, nc)) || (rc = dalloc(h, &h->q.a.attempts, nc)) ||
+            (rc = dalloc(h, &h->q.b.cell, nc)) || (rc = dalloc(h, &h->q.b.t_left, nc)) ||
+            (rc = dalloc(h, &h->q.b.dt_tc, nc)) || (rc = dalloc(h, &h->q.b.attempts, nc)) ||
+            (rc = dalloc(h, &h->q.counters, 4)) ||
             (rc = dalloc(h, &h->part.tr_inbox, G * h->part.n_tr_blocks)) ||
             (rc = dalloc(h, &h->part.tr_outflow, G * h->part.n_tr_blocks)) ||
             (rc = dalloc(h, &h->part.th_inbox, G * h->part.n_red_blocks)) ||
@@ -347,7 +349,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
         if ((e = cudaMemcpy(h->hll, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
             rc = cuda_fail(h, e, "hll copy"); goto bad;
         }
-        if ((e = cudaMemset(h->q.counters, 0, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+        if ((e = cudaMemset(h->q.counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMemset(h->status, 0, sizeof(unsigned))) != cudaSuccess ||
             (e = cudaMemset(h->budget, 0, 4 * G * sizeof(double))) != cudaSuccess ||
             (e = cudaMemset(h->N[0], 0, G * nc * sizeof(double))) != cudaSuccess ||
@@ -428,7 +430,7 @@ int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const doubl
     RT_CUDA(h, cudaMemcpyAsync(h->N[0], N, G * b, k, h->stream));
     RT_CUDA(h, cudaMemcpyAsync(h->F[0], F, 3 * G * b, k, h->stream));
     RT_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-    RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, 2 * sizeof(unsigned long long), h->stream));
+    RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, 4 * sizeof(unsigned long long), h->stream));
     cudaError_t e = launch_reduce_N(G, nc, h->N[0], h->part, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
     e = launch_finalize_mode(G, 1, h->part, h->g.dx * h->g.dx * h->g.dx, nullptr, h->budget, h->q, h->status,

@@ -55,14 +55,18 @@ struct ThermoParams {
     GroupConsts gc;
 };
 
-// Device work queue of cells whose sub-cycling outlasted the first pass.
-struct Queue {
+// Device work queues of cells whose sub-cycling outlasted the first pass
+// (a) and the lane-per-cell drain (b).
+struct QueueArrays {
     uint32_t *cell;
     double *t_left;
     double *dt_tc;
     int32_t *attempts;
-    unsigned long long *counters;   // [0] = count, [1] = head
-    long long capacity;
+};
+struct Queue {
+    QueueArrays a, b;
+    unsigned long long *counters;   // [0] a.count, [1] a.head, [2] b.count, [3] b.head
+    long long capacity;             // items per queue
 };
 
 // Per-block partial sums of the photon budget.
@@ -83,7 +87,7 @@ int transport_blocks_per_group(const GridDev &g);
 void transport_init();   // kernel attributes; called once per handle
 
 // ev (optional, 4 events): recorded around the first pass (0, 1) and
-// around the queue drain (2, 3).
+// around the queue drains (2, 3).
 cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, double *xHII,
                           double *xHeII, double *xHeIII, double *T, double *N, double *F,
                           int32_t *subcycles, Queue q, unsigned *status, int n_sm,

@@ -12,16 +12,26 @@
 //      fractions renormalised by lowering the largest one
 // and rejects the sub-step (halving it) when N_i, T/mu, x_HII or n_e move by
 // more than 10%, or the first-order T and x_HII terms exceed 10%; after a
-// sub-step whose largest change is below 5% the next one is doubled.
+// sub-step whose largest change is below 5% the next one is doubled.  The
+// cooling rate and its derivative depend only on the state at t, so a
+// rejected sub-step keeps them for the retry.
 //
-// Load balance: a first pass gives every cell (one thread each, coalesced)
-// a fixed number of attempts; cells still sub-cycling are appended to a
-// device queue with their partial state.  A persistent drain kernel then
-// hands queue items to lanes one at a time: each lane runs one attempt per
-// loop iteration and, when its cell completes, fetches the next item, so a
-// warp stays full while cells with very different sub-cycle counts pass
-// through it.  Nothing waits on another thread; the loop ends when the
-// queue is exhausted.
+// Load balance, three kernels per RT step:
+//   thermo_pass1  one thread per cell (coalesced), up to 6 attempts; cells
+//                 still sub-cycling go to queue A with their partial state;
+//   thermo_drain  persistent; every lane takes queue-A items one at a time,
+//                 one attempt per loop iteration, and fetches the next item
+//                 as soon as its cell completes; a cell that needs more than
+//                 kDrainBudget attempts here moves to queue B;
+//   thermo_hard   persistent; one warp per queue-B cell.  On GB300 a lone
+//                 FP64 dependent chain is slow (64 cycles per FMA, ~1000 per
+//                 exp), so the lanes of the warp evaluate the cell's
+//                 twenty-odd transcendentals of each temperature in parallel
+//                 (rates.cuh, transc_warp) while the scalar update runs
+//                 redundantly in all lanes.  The arithmetic is identical to
+//                 the one-thread path, so results do not depend on which
+//                 kernel finished a cell.
+// Nothing waits on another thread; each kernel ends when its queue is empty.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,6 +40,8 @@
 #include "rt_internal.h"
 
 namespace rtgb {
+
+
 namespace {
 
 constexpr double kEV = 1.602176634e-12;
@@ -38,6 +50,8 @@ constexpr double kFloorN = 1e-30;
 constexpr double kXMin = 1e-6;
 constexpr double kNeFloor = 1e-6;
 constexpr double kTFloor = 1.0;
+constexpr int kPass1Block = 128;
+constexpr int kDrainBudget = 192;   // attempts a cell may spend in thermo_drain
 
 template <int G>
 struct CellState {
@@ -51,16 +65,28 @@ struct IsoRates {     // rates at the fixed temperature of an isothermal cell
     HeRates he;
 };
 
+struct CoolCache {    // cooling L and dL/dT of the current state at t
+    double L, dL;
+    bool valid;
+};
+
 __device__ __forceinline__ double mu_of(double X, double x, double y2, double y3)
 {
     return 1.0 / (X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3));
 }
 
+template <bool WARP>
+__device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, Transc &t)
+{
+    if (WARP) transc_warp(T, case_b, t);
+    else transc_serial(T, case_b, need, t);
+}
+
 // One thermo_step over h.  Returns true and fills `o` and `maxrel` when the
 // 10% rule holds.
-template <int G>
-__device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const CellState<G> &s,
-                                        double h, const IsoRates &iso, CellState<G> &o, double &maxrel)
+template <int G, bool WARP>
+__device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const CellState<G> &s, double h,
+                                        const IsoRates &iso, CoolCache &cc, CellState<G> &o, double &maxrel)
 {
     const double nHe = nH * p.he_ratio;
     const double x = s.x, y2 = s.y2, y3 = s.y3;
@@ -100,11 +126,15 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
     const double mu = mu_of(p.X, x, y2, y3);
     double Tmu1 = 0.0;
     if (!p.isothermal) {
-        TVars tv = tvars(s.T);
-        double L, dL;
-        cooling(tv, p.case_b, p.a_exp, p.helium != 0, ne, nHI, nHII, nHeI, nHeII, nHeIII, L, dL);
-        double lam = heat - L;
-        double dlam = -mu * dL;
+        if (!cc.valid) {
+            Transc t;
+            get_transc<WARP>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
+            cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L,
+                         cc.dL);
+            cc.valid = true;
+        }
+        double lam = heat - cc.L;
+        double dlam = -mu * cc.dL;
         double K = p.kfac / nH;
         double Tmu = s.T / mu;
         double dT = lam * K * h / (1.0 - dlam * K * h);
@@ -120,7 +150,9 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
     if (p.isothermal) {
         hr = iso.h;
     } else {
-        h_rates(tvars(Tmu1 * mu), p.case_b, hr);
+        Transc t;
+        get_transc<WARP>(Tmu1 * mu, p.case_b, kNeedH, t);
+        h_rates_from(t, p.case_b, hr);
     }
     double C = hr.beta * ne + gam0;
     double Dd = hr.alpha * ne;
@@ -148,8 +180,13 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
         double yI = 1.0 - y2 - y3;
         double ne2 = x1 * nH + (y2 + 2.0 * y3) * nHe;
         HeRates r2;
-        if (p.isothermal) r2 = iso.he;
-        else he_rates(tvars(Tmu1 * mu_of(p.X, x1, y2, y3)), p.case_b, true, r2);
+        if (p.isothermal) {
+            r2 = iso.he;
+        } else {
+            Transc t;
+            get_transc<WARP>(Tmu1 * mu_of(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
+            he_rates_from(t, p.case_b, r2);
+        }
         double C1 = y2 * r2.alpha_HeII * ne2;
         double D1 = r2.beta_HeI * ne2 + gam1;
         double yI1 = (yI + C1 * h) / (1.0 + D1 * h);
@@ -158,8 +195,13 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
         y2n = (y2 + C2 * h) / (1.0 + D2 * h);
         double ne3 = x1 * nH + (y2n + 2.0 * y3) * nHe;
         HeRates r3;
-        if (p.isothermal) r3 = iso.he;
-        else he_rates(tvars(Tmu1 * mu_of(p.X, x1, y2n, y3)), p.case_b, false, r3);
+        if (p.isothermal) {
+            r3 = iso.he;
+        } else {
+            Transc t;
+            get_transc<WARP>(Tmu1 * mu_of(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
+            he_rates_from(t, p.case_b, r3);
+        }
         double C3 = y2n * (r3.beta_HeII * ne3 + gam2);
         double D3 = r3.alpha_HeIII * ne3;
         y3n = (y3 + C3 * h) / (1.0 + D3 * h);
@@ -185,16 +227,17 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
 }
 
 // One attempt of the sub-cycling loop; returns true when the cell is done.
-template <int G>
-__device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, CellState<G> &st,
-                                              double &t_left, double &dt_tc, int &att, const IsoRates &iso)
+template <int G, bool WARP>
+__device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, CellState<G> &st, double &t_left,
+                                              double &dt_tc, int &att, const IsoRates &iso, CoolCache &cc)
 {
     double h = (dt_tc < t_left) ? dt_tc : t_left;
     ++att;
     CellState<G> o;
     double mr = 0.0;
-    if (attempt<G>(p, nH, st, h, iso, o, mr)) {
+    if (attempt<G, WARP>(p, nH, st, h, iso, cc, o, mr)) {
         st = o;
+        cc.valid = false;
         t_left = (h == t_left) ? 0.0 : t_left - h;
         dt_tc = (mr < 0.05) ? 2.0 * h : h;
     } else {
@@ -203,10 +246,10 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, 
     return !(t_left > 0.0);
 }
 
-template <int G>
+template <int G, bool WARP>
 __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, const double *xHII,
                                           const double *xHeII, const double *xHeIII, const double *T,
-                                          const double *N, CellState<G> &st, IsoRates &iso)
+                                          const double *N, CellState<G> &st, IsoRates &iso, CoolCache &cc)
 {
     st.x = xHII[c];
     st.y2 = xHeII[c];
@@ -217,10 +260,12 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, co
         st.N[i] = N[(long long)i * p.nc + c];
         st.Fs[i] = 1.0;
     }
+    cc.valid = false;
     if (p.isothermal) {
-        TVars tv = tvars(st.T);
-        h_rates(tv, p.case_b, iso.h);
-        if (p.helium) he_rates(tv, p.case_b, true, iso.he);
+        Transc t;
+        get_transc<WARP>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
+        h_rates_from(t, p.case_b, iso.h);
+        if (p.helium) he_rates_from(t, p.case_b, iso.he);
     }
 }
 
@@ -248,8 +293,21 @@ __device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, d
     if (bad) atomicOr(status, kStatusNonFinite);
 }
 
+__device__ __forceinline__ void push_item(const QueueArrays &a, unsigned long long slot, long long cap, uint32_t c,
+                                          double t_left, double dt_tc, int att, unsigned *status)
+{
+    if (slot < (unsigned long long)cap) {
+        a.cell[slot] = c;
+        a.t_left[slot] = t_left;
+        a.dt_tc[slot] = dt_tc;
+        a.attempts[slot] = att;
+    } else {
+        atomicOr(status, kStatusQueue);
+    }
+}
+
 template <int G>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPass1Block)
 thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
              double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
 {
@@ -261,12 +319,13 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     if (valid) {
         CellState<G> st;
         IsoRates iso;
-        load_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, st, iso);
+        CoolCache cc;
+        load_cell<G, false>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         double n = nH[c];
         bool done = false;
         const int lim = p.pass1_attempts < p.max_sub ? p.pass1_attempts : p.max_sub;
         for (int k = 0; k < lim && !done; ++k)
-            done = subcycle_once<G>(p, n, st, t_left, dt_tc, att, iso);
+            done = subcycle_once<G, false>(p, n, st, t_left, dt_tc, att, iso, cc);
         if (!done && att >= p.max_sub) {
             atomicOr(status, kStatusSubcycle);
             done = true;
@@ -275,7 +334,7 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         if (done) subcycles[c] = att;
         else push = true;
     }
-    // warp-aggregated append of unfinished cells
+    // warp-aggregated append of unfinished cells to queue A
     unsigned m = __ballot_sync(0xffffffffu, push);
     if (m) {
         int lane = threadIdx.x & 31;
@@ -283,17 +342,9 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         unsigned long long base = 0;
         if (lane == leader) base = atomicAdd(&q.counters[0], (unsigned long long)__popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (push) {
-            unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
-            if (slot < (unsigned long long)q.capacity) {
-                q.cell[slot] = (uint32_t)c;
-                q.t_left[slot] = t_left;
-                q.dt_tc[slot] = dt_tc;
-                q.attempts[slot] = att;
-            } else {
-                atomicOr(status, kStatusQueue);
-            }
-        }
+        if (push)
+            push_item(q.a, base + __popc(m & ((1u << lane) - 1u)), q.capacity, (uint32_t)c, t_left, dt_tc, att,
+                      status);
     }
 }
 
@@ -307,22 +358,29 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     if (count == 0) return;
     CellState<G> st;
     IsoRates iso;
+    CoolCache cc;
     double t_left = 0.0, dt_tc = 0.0, n = 0.0;
-    int att = 0;
+    int att = 0, used = 0;
     long long c = -1;
     bool have = false;
-    unsigned long long it = atomicAdd(&q.counters[1], 1ULL);
-    if (it < count) {
-        c = q.cell[it];
-        t_left = q.t_left[it];
-        dt_tc = q.dt_tc[it];
-        att = q.attempts[it];
-        n = nH[c];
-        load_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, st, iso);
-        have = true;
-    }
+    auto fetch = [&]() {
+        unsigned long long it = atomicAdd(&q.counters[1], 1ULL);
+        if (it < count) {
+            c = q.a.cell[it];
+            t_left = q.a.t_left[it];
+            dt_tc = q.a.dt_tc[it];
+            att = q.a.attempts[it];
+            n = nH[c];
+            used = 0;
+            load_cell<G, false>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+            have = true;
+        } else {
+            have = false;
+        }
+    };
+    fetch();
     while (have) {
-        bool done = subcycle_once<G>(p, n, st, t_left, dt_tc, att, iso);
+        bool done = subcycle_once<G, false>(p, n, st, t_left, dt_tc, att, iso, cc);
         if (!done && att >= p.max_sub) {
             atomicOr(status, kStatusSubcycle);
             done = true;
@@ -330,27 +388,62 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         if (done) {
             store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
             subcycles[c] = att;
-            it = atomicAdd(&q.counters[1], 1ULL);
-            if (it < count) {
-                c = q.cell[it];
-                t_left = q.t_left[it];
-                dt_tc = q.dt_tc[it];
-                att = q.attempts[it];
-                n = nH[c];
-                load_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, st, iso);
-            } else {
-                have = false;
-            }
+            fetch();
+        } else if (++used >= kDrainBudget) {
+            // long sub-cycler: hand it to the warp-per-cell kernel
+            store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+            unsigned long long slot = atomicAdd(&q.counters[2], 1ULL);
+            push_item(q.b, slot, q.capacity, (uint32_t)c, t_left, dt_tc, att, status);
+            fetch();
         }
     }
 }
 
 template <int G>
-cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, double *xHeII,
-                     double *xHeIII, double *T, double *N, double *F, int32_t *sub, Queue q,
-                     unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
+__global__ void __launch_bounds__(128)
+thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
+            double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
 {
-    const int B = 128;
+    unsigned long long count = q.counters[2];
+    if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
+    if (count == 0) return;
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(&q.counters[3], 1ULL);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= count) break;
+        const long long c = q.b.cell[it];
+        double t_left = q.b.t_left[it];
+        double dt_tc = q.b.dt_tc[it];
+        int att = q.b.attempts[it];
+        const double n = nH[c];
+        CellState<G> st;
+        IsoRates iso;
+        CoolCache cc;
+        load_cell<G, true>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+        bool done = false;
+        while (!done) {
+            done = subcycle_once<G, true>(p, n, st, t_left, dt_tc, att, iso, cc);
+            if (!done && att >= p.max_sub) {
+                if (lane == 0) atomicOr(status, kStatusSubcycle);
+                done = true;
+            }
+        }
+        if (lane == 0) {
+            store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+            subcycles[c] = att;
+        }
+        __syncwarp();
+    }
+}
+
+template <int G>
+cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, double *xHeII, double *xHeIII,
+                     double *T, double *N, double *F, int32_t *sub, Queue q, unsigned *status, int n_sm,
+                     cudaStream_t s, cudaEvent_t *ev)
+{
+    const int B = kPass1Block;
     long long nb = (tp.nc + B - 1) / B;
     if (ev) cudaEventRecord(ev[0], s);
     thermo_pass1<G><<<(unsigned)nb, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
@@ -358,15 +451,23 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     if (e != cudaSuccess) return e;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G>, B, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G>, 128, 0);
         if (per_sm < 1) per_sm = 1;
     }
     long long grid = (long long)per_sm * n_sm;
-    long long need = (tp.nc + B - 1) / B;
+    long long need = (tp.nc + 127) / 128;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
-    thermo_drain<G><<<(unsigned)grid, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_drain<G><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // one warp per long sub-cycler: two 4-warp blocks per SM
+    long long hgrid = 2LL * n_sm;
+    long long hneed = (tp.nc + 3) / 4;
+    if (hgrid > hneed) hgrid = hneed;
+    if (hgrid < 1) hgrid = 1;
+    thermo_hard<G><<<(unsigned)hgrid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
@@ -406,10 +507,12 @@ namespace rtgb {
 namespace {
 
 constexpr long long kNoAllocMaxCells = 1LL << 18;   // 262144 cells
-// layout: [0,16) queue counters, [16,20) status, queue arrays from byte 256
+// layout: [0,32) queue counters, [32,36) status; from byte 256 the two
+// queues, each cell / attempts / t_left / dt_tc arrays of kNoAllocMaxCells
 constexpr size_t kNoAllocHeader = 256;
-constexpr size_t kNoAllocBytes =
-    kNoAllocHeader + (size_t)kNoAllocMaxCells * (sizeof(uint32_t) + sizeof(int32_t) + 2 * sizeof(double));
+constexpr size_t kNoAllocQueueBytes =
+    (size_t)kNoAllocMaxCells * (sizeof(uint32_t) + sizeof(int32_t) + 2 * sizeof(double));
+constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * kNoAllocQueueBytes;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
@@ -487,12 +590,16 @@ extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_o
     }
     Queue q{};
     q.counters = reinterpret_cast<unsigned long long *>(base);
-    unsigned *status = reinterpret_cast<unsigned *>(base + 16);
+    unsigned *status = reinterpret_cast<unsigned *>(base + 32);
     const size_t K = (size_t)kNoAllocMaxCells;
-    q.cell = reinterpret_cast<uint32_t *>(base + kNoAllocHeader);
-    q.attempts = reinterpret_cast<int32_t *>(base + kNoAllocHeader + 4 * K);
-    q.t_left = reinterpret_cast<double *>(base + kNoAllocHeader + 8 * K);
-    q.dt_tc = reinterpret_cast<double *>(base + kNoAllocHeader + 16 * K);
+    QueueArrays *qa[2] = {&q.a, &q.b};
+    for (int k = 0; k < 2; ++k) {
+        unsigned char *qb = base + kNoAllocHeader + k * kNoAllocQueueBytes;
+        qa[k]->cell = reinterpret_cast<uint32_t *>(qb);
+        qa[k]->attempts = reinterpret_cast<int32_t *>(qb + 4 * K);
+        qa[k]->t_left = reinterpret_cast<double *>(qb + 8 * K);
+        qa[k]->dt_tc = reinterpret_cast<double *>(qb + 16 * K);
+    }
     q.capacity = ncells;
 
     if (cudaMemsetAsync(base, 0, kNoAllocHeader, s) != cudaSuccess) return RT_ECUDA;
