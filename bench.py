@@ -205,6 +205,7 @@ def main():
     ap.add_argument("--workload", default="cosmo128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip timing the RT_MIXED variant")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -325,6 +326,38 @@ def main():
         e2e = {"value": units / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "how": "per step: rt_set_state from pinned host buffers, rt_step, rt_get_state to pinned host"}
 
+    # ---- the mixed-precision variant (FP32 transport, FP32 rates, FP64 stiff updates) ----
+    variants = {}
+    if not args.no_mixed:
+        simm = R.RT.from_workload(w, precision=R.RT_MIXED)
+        simm.set_stream(stream.cuda_stream)
+        simm.run(dt, max(args.warmup, 3))
+        simm.sync()
+        simm.set_state(dev_init)
+        simm.sync()
+        barrier()
+        ev0.record(stream)
+        simm.run(dt, args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        simm.sync()
+        tm = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        simm.set_state(dev_init)
+        simm.set_profiling(True)
+        for _ in range(args.steps):
+            simm.step(dt)
+        pm = simm.profile()
+        simm.set_profiling(False)
+        tr_ms = pm["transport"][0] / max(pm["transport"][1], 1)
+        alg32 = 32.0 * cg
+        ach32 = alg32 / (tr_ms / 1e3) / 1e9
+        variants["mixed"] = {
+            "value": units / tm, "ms_per_step": 1e3 * tm / args.steps, "speedup_vs_fp64": t / tm,
+            "phases_ms_per_launch": {k: round(v[0] / v[1], 5) if v[1] else None for k, v in pm.items()},
+            "transport_roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": ach32 / hbm_peak, "algorithmic_bytes_per_launch": alg32}}
+        simm.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -337,6 +370,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clocks, "phases": phases,
+                "variants": variants,
                 "thermo_attempts": {"per_step": attempts / args.steps, "max_per_cell": att_max,
                                     "queued_cells_per_step": queued / args.steps,
                                     "queued_attempts_per_step": queued_att / args.steps}}

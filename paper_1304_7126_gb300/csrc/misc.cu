@@ -11,14 +11,26 @@ namespace {
 constexpr int RB = 256;       // reduction block
 constexpr int RBLK = 296;     // reduction blocks per group (2 per SM)
 
-// N_i += L_i dt / V in each source cell (sources pre-merged per cell).
+// N_i += L_i dt / V in each source cell (sources pre-merged per cell); the
+// add is done in FP64 and rounded to the state type.
+template <typename P>
 __global__ void inject_kernel(int nsrc, int G, long long nc, const long long *__restrict__ cells,
-                              const double *__restrict__ Lsum, double dt_over_V, double *N)
+                              const double *__restrict__ Lsum, double dt_over_V, P *N)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsrc) return;
     long long c = cells[s];
-    for (int g = 0; g < G; ++g) N[(long long)g * nc + c] += Lsum[(long long)s * G + g] * dt_over_V;
+    for (int g = 0; g < G; ++g) {
+        P &n = N[(long long)g * nc + c];
+        n = (P)((double)n + Lsum[(long long)s * G + g] * dt_over_V);
+    }
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(long long n, const A *__restrict__ in, B *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh)
@@ -37,15 +49,15 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 // Per-block partial sums of N over the cells of one group; the partition
 // of cells into blocks is fixed, so the result is reproducible.
-__global__ void __launch_bounds__(RB) reduce_N_kernel(long long nc, const double *__restrict__ N,
-                                                      double *part)
+template <typename P>
+__global__ void __launch_bounds__(RB) reduce_N_kernel(long long nc, const P *__restrict__ N, double *part)
 {
     __shared__ double sh[RB / 32];
     const int g = blockIdx.y;
-    const double *Ng = N + (long long)g * nc;
+    const P *Ng = N + (long long)g * nc;
     double acc = 0.0;
     for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < nc; i += (long long)gridDim.x * RB)
-        acc += Ng[i];
+        acc += (double)Ng[i];
     double t = block_sum(acc, sh);
     if (threadIdx.x == 0) part[(long long)g * gridDim.x + blockIdx.x] = t;
 }
@@ -107,14 +119,43 @@ cudaError_t launch_inject(int nsrc, int G, long long nc, const long long *cells,
                           double dt_over_V, double *N, cudaStream_t s)
 {
     if (nsrc <= 0) return cudaSuccess;
-    inject_kernel<<<(nsrc + 127) / 128, 128, 0, s>>>(nsrc, G, nc, cells, Lsum, dt_over_V, N);
+    inject_kernel<double><<<(nsrc + 127) / 128, 128, 0, s>>>(nsrc, G, nc, cells, Lsum, dt_over_V, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_f32(int nsrc, int G, long long nc, const long long *cells, const double *Lsum,
+                              double dt_over_V, float *N, cudaStream_t s)
+{
+    if (nsrc <= 0) return cudaSuccess;
+    inject_kernel<float><<<(nsrc + 127) / 128, 128, 0, s>>>(nsrc, G, nc, cells, Lsum, dt_over_V, N);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_N(int G, long long nc, const double *N, const Partials &p, cudaStream_t s)
 {
     dim3 grid(p.n_red_blocks, G);
-    reduce_N_kernel<<<grid, RB, 0, s>>>(nc, N, p.th_inbox);
+    reduce_N_kernel<double><<<grid, RB, 0, s>>>(nc, N, p.th_inbox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_N_f32(int G, long long nc, const float *N, const Partials &p, cudaStream_t s)
+{
+    dim3 grid(p.n_red_blocks, G);
+    reduce_N_kernel<float><<<grid, RB, 0, s>>>(nc, N, p.th_inbox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_d2f(long long n, const double *in, float *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    convert_kernel<double, float><<<1216, 256, 0, s>>>(n, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f2d(long long n, const float *in, double *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    convert_kernel<float, double><<<1216, 256, 0, s>>>(n, in, out);
     return cudaGetLastError();
 }
 

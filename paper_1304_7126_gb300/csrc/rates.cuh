@@ -128,6 +128,70 @@ __device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
     }
 }
 
+// FP32 transcendentals (the mixed-precision thermochemistry): the same
+// arguments evaluated in single precision, stored widened into Transc so the
+// assembly below is shared.  Relative accuracy ~1e-7.
+__device__ __forceinline__ void transc_level0_f(double T, Transc &t, float &lnT, float &invT)
+{
+    float Tf = (float)T;
+    lnT = logf(Tf);
+    float sq = sqrtf(Tf);
+    invT = 1.0f / Tf;
+    t.lnT = lnT;
+    t.sqrtT = sq;
+    t.invT = invT;
+    t.u = 1.0f / (1.0f + sq * 0.0031622776f);
+}
+
+__device__ __forceinline__ float exp_arg_f(const ExpArg &q, float lnT, float invT)
+{
+    return fmaf((float)q.a, lnT, fmaf((float)q.b, invT, (float)q.c));
+}
+
+__device__ __forceinline__ float hg_arg_f(const HGPar &h, float lnT, float l)
+{
+    return (float)h.p * ((float)h.lnT1 - lnT) - (float)h.s * l;
+}
+
+__device__ __forceinline__ void transc_serial_f(double T, int case_b, unsigned need, Transc &t)
+{
+    const RateTable &R = c_rate_tab[case_b];
+    float lnT, invT;
+    transc_level0_f(T, t, lnT, invT);
+#pragma unroll
+    for (int k = 0; k < NEXP; ++k)
+        if (need & (1u << k)) t.e[k] = expf(exp_arg_f(R.ea[k], lnT, invT));
+#pragma unroll
+    for (int j = 0; j < NHG; ++j) {
+        if (need & (1u << (NEXP + j))) {
+            float l = log1pf((float)t.e[E_W0 + j]);
+            t.l[j] = l;
+            t.v[j] = expf(hg_arg_f(R.hg[j], lnT, l));
+        }
+    }
+}
+
+__device__ __forceinline__ void transc_warp_f(double T, int case_b, Transc &t)
+{
+    const RateTable &R = c_rate_tab[case_b];
+    const int lane = threadIdx.x & 31;
+    float lnT, invT;
+    transc_level0_f(T, t, lnT, invT);
+    const int k = lane < NEXP ? lane : 0;
+    float ek = expf(exp_arg_f(R.ea[k], lnT, invT));
+    const int j = lane & 3;
+    float wj = __shfl_sync(0xffffffffu, ek, E_W0 + j);
+    float lj = log1pf(wj);
+    float vj = expf(hg_arg_f(R.hg[j], lnT, lj));
+#pragma unroll
+    for (int q = 0; q < NEXP; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
+#pragma unroll
+    for (int q = 0; q < NHG; ++q) {
+        t.l[q] = __shfl_sync(0xffffffffu, lj, q);
+        t.v[q] = __shfl_sync(0xffffffffu, vj, q);
+    }
+}
+
 // d ln v / dT of a Hui & Gnedin fit: -(1/T) (p - s r w / (1 + w))
 __device__ __forceinline__ double hg_dlog(const HGPar &h, const Transc &t, int j)
 {

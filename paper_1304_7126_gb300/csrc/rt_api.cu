@@ -28,10 +28,14 @@ struct rt_handle {
     cudaStream_t stream = nullptr;
 
     double *nH = nullptr, *xHII = nullptr, *xHeII = nullptr, *xHeIII = nullptr, *T = nullptr;
-    double *N[2] = {nullptr, nullptr};
+    double *N[2] = {nullptr, nullptr};   // RT_FP64 photon state
     double *F[2] = {nullptr, nullptr};
+    float *Nf[2] = {nullptr, nullptr};   // RT_MIXED photon state
+    float *Ff[2] = {nullptr, nullptr};
+    bool mixed = false;
     int cur = 0;
     double *hll = nullptr;
+    float *hllf = nullptr;
     int32_t *subcycles = nullptr;
     Queue q{};
     Partials part{};
@@ -108,7 +112,7 @@ void free_all(rt_handle *h)
     for (cudaEvent_t e : h->pending) cudaEventDestroy(e);
     h->pending.clear();
     void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
-                    h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
+                    h->Nf[0], h->Nf[1], h->Ff[0], h->Ff[1], h->hllf, h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
                     h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
                     h->budget, h->status, h->src_cell, h->src_L};
     for (void *p : ptrs)
@@ -182,14 +186,19 @@ int enqueue_step(rt_handle *h, double dt, bool capturing = false)
     cudaError_t e;
     if (h->nsrc > 0) {
         if (prof) { prof_pair(h, 0, &a, &b); cudaEventRecord(a, h->stream); }
-        e = launch_inject(h->nsrc, h->G, nc, h->src_cell, h->src_L, dt / V, h->N[h->cur], h->stream);
+        if (h->mixed) e = launch_inject_f32(h->nsrc, h->G, nc, h->src_cell, h->src_L, dt / V, h->Nf[h->cur], h->stream);
+        else e = launch_inject(h->nsrc, h->G, nc, h->src_cell, h->src_L, dt / V, h->N[h->cur], h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "inject");
         if (prof) cudaEventRecord(b, h->stream);
     }
     int nxt = 1 - h->cur;
     if (prof) { prof_pair(h, 1, &a, &b); cudaEventRecord(a, h->stream); }
-    e = launch_transport(h->g, h->G, h->opt.flux, h->cr, dt, h->N[h->cur], h->F[h->cur], h->N[nxt],
-                         h->F[nxt], h->hll, h->part, h->stream);
+    if (h->mixed)
+        e = launch_transport_f32(h->g, h->G, h->opt.flux, h->cr, dt, h->Nf[h->cur], h->Ff[h->cur], h->Nf[nxt],
+                                 h->Ff[nxt], h->hllf, h->part, h->stream);
+    else
+        e = launch_transport(h->g, h->G, h->opt.flux, h->cr, dt, h->N[h->cur], h->F[h->cur], h->N[nxt],
+                             h->F[nxt], h->hll, h->part, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "transport");
     if (prof) cudaEventRecord(b, h->stream);
     h->cur = nxt;
@@ -199,11 +208,17 @@ int enqueue_step(rt_handle *h, double dt, bool capturing = false)
         prof_pair(h, 2, &tev[0], &tev[1]);
         prof_pair(h, 3, &tev[2], &tev[3]);
     }
-    e = launch_thermo(tp, h->G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[h->cur], h->F[h->cur],
-                      h->subcycles, h->q, h->status, h->n_sm, h->stream, prof ? tev : nullptr);
+    if (h->mixed)
+        e = launch_thermo_mixed(tp, h->G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->Nf[h->cur],
+                                h->Ff[h->cur], h->subcycles, h->q, h->status, h->n_sm, h->stream,
+                                prof ? tev : nullptr);
+    else
+        e = launch_thermo(tp, h->G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[h->cur], h->F[h->cur],
+                          h->subcycles, h->q, h->status, h->n_sm, h->stream, prof ? tev : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "thermo");
     if (prof) { prof_pair(h, 4, &a, &b); cudaEventRecord(a, h->stream); }
-    e = launch_reduce_N(h->G, nc, h->N[h->cur], h->part, h->stream);
+    e = h->mixed ? launch_reduce_N_f32(h->G, nc, h->Nf[h->cur], h->part, h->stream)
+                 : launch_reduce_N(h->G, nc, h->N[h->cur], h->part, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
     if (prof) cudaEventRecord(b, h->stream);
     double emitted[kMaxG] = {0};
@@ -285,7 +300,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return RT_EINVAL;
     if (opt->flux != RT_GLF && opt->flux != RT_HLL) return RT_EINVAL;
     if (opt->otsa != 1 || opt->smooth != 0) return RT_EINVAL;
-    if (opt->precision != RT_FP64) return RT_EINVAL;
+    if (opt->precision != RT_FP64 && opt->precision != RT_MIXED) return RT_EINVAL;
     if (!(opt->a_exp > 0.0) || opt->max_subcycles < 1) return RT_EINVAL;
     for (int i = 0; i < 3 * n_groups; ++i)
         if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0) || !std::isfinite(sigN[i]) || !std::isfinite(sigE[i]))
@@ -300,6 +315,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     for (int i = 0; i < 6; ++i) h->g.bc[i] = grid->bc[i];
     h->G = n_groups;
     h->opt = *opt;
+    h->mixed = opt->precision == RT_MIXED;
     h->cr = c_r;
     for (int i = 0; i < n_groups; ++i) {
         for (int j = 0; j < 3; ++j) {
@@ -326,8 +342,6 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
         h->part.n_red_blocks = reduce_blocks_per_group();
         if ((rc = dalloc(h, &h->nH, nc)) || (rc = dalloc(h, &h->xHII, nc)) || (rc = dalloc(h, &h->xHeII, nc)) ||
             (rc = dalloc(h, &h->xHeIII, nc)) || (rc = dalloc(h, &h->T, nc)) ||
-            (rc = dalloc(h, &h->N[0], G * nc)) || (rc = dalloc(h, &h->N[1], G * nc)) ||
-            (rc = dalloc(h, &h->F[0], 3 * G * nc)) || (rc = dalloc(h, &h->F[1], 3 * G * nc)) ||
             (rc = dalloc(h, &h->hll, (size_t)kHllNF * kHllNMU * 2)) || (rc = dalloc(h, &h->subcycles, nc)) ||
             (rc = dalloc(h, &h->q.a.cell, nc)) || (rc = dalloc(h, &h->q.a.t_left, nc)) ||
             (rc = dalloc(h, &h->q.a.dt_tc, nc)) || (rc = dalloc(h, &h->q.a.attempts, nc)) ||
@@ -339,6 +353,17 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
             (rc = dalloc(h, &h->part.th_inbox, G * h->part.n_red_blocks)) ||
             (rc = dalloc(h, &h->budget, 4 * G)) || (rc = dalloc(h, &h->status, 1)))
             goto bad;
+        for (int k = 0; k < 2; ++k) {
+            if (h->mixed) {
+                if ((rc = dalloc(h, &h->Nf[k], G * nc)) || (rc = dalloc(h, &h->Ff[k], 3 * G * nc))) goto bad;
+                cudaMemset(h->Nf[k], 0, G * nc * sizeof(float));
+                cudaMemset(h->Ff[k], 0, 3 * G * nc * sizeof(float));
+            } else {
+                if ((rc = dalloc(h, &h->N[k], G * nc)) || (rc = dalloc(h, &h->F[k], 3 * G * nc))) goto bad;
+                cudaMemset(h->N[k], 0, G * nc * sizeof(double));
+                cudaMemset(h->F[k], 0, 3 * G * nc * sizeof(double));
+            }
+        }
         h->q.capacity = nc;
         if ((e = cudaMallocHost((void **)&h->status_host, sizeof(unsigned))) != cudaSuccess) {
             rc = fail(h, RT_ENOMEM, "cudaMallocHost"); goto bad;
@@ -349,13 +374,17 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
         if ((e = cudaMemcpy(h->hll, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
             rc = cuda_fail(h, e, "hll copy"); goto bad;
         }
+        if (h->mixed) {
+            std::vector<float> tabf(tab.begin(), tab.end());
+            if ((rc = dalloc(h, &h->hllf, tabf.size()))) goto bad;
+            if ((e = cudaMemcpy(h->hllf, tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+                rc = cuda_fail(h, e, "hll copy"); goto bad;
+            }
+        }
         if ((e = cudaMemset(h->q.counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMemset(h->status, 0, sizeof(unsigned))) != cudaSuccess ||
             (e = cudaMemset(h->budget, 0, 4 * G * sizeof(double))) != cudaSuccess ||
-            (e = cudaMemset(h->N[0], 0, G * nc * sizeof(double))) != cudaSuccess ||
-            (e = cudaMemset(h->N[1], 0, G * nc * sizeof(double))) != cudaSuccess ||
-            (e = cudaMemset(h->F[0], 0, 3 * G * nc * sizeof(double))) != cudaSuccess ||
-            (e = cudaMemset(h->F[1], 0, 3 * G * nc * sizeof(double))) != cudaSuccess ||
             (e = cudaMemset(h->subcycles, 0, nc * sizeof(int32_t))) != cudaSuccess) {
             rc = cuda_fail(h, e, "cudaMemset"); goto bad;
         }
@@ -427,11 +456,25 @@ int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const doubl
     RT_CUDA(h, cudaMemcpyAsync(h->xHeII, xHeII, b, k, h->stream));
     RT_CUDA(h, cudaMemcpyAsync(h->xHeIII, xHeIII, b, k, h->stream));
     RT_CUDA(h, cudaMemcpyAsync(h->T, T, b, k, h->stream));
-    RT_CUDA(h, cudaMemcpyAsync(h->N[0], N, G * b, k, h->stream));
-    RT_CUDA(h, cudaMemcpyAsync(h->F[0], F, 3 * G * b, k, h->stream));
+    if (!h->mixed) {
+        RT_CUDA(h, cudaMemcpyAsync(h->N[0], N, G * b, k, h->stream));
+        RT_CUDA(h, cudaMemcpyAsync(h->F[0], F, 3 * G * b, k, h->stream));
+    } else if (device_ptrs) {
+        cudaError_t ec = launch_convert_d2f((long long)G * nc, N, h->Nf[0], h->stream);
+        if (ec == cudaSuccess) ec = launch_convert_d2f(3LL * G * nc, F, h->Ff[0], h->stream);
+        if (ec != cudaSuccess) return cuda_fail(h, ec, "convert");
+    } else {
+        std::vector<float> nf(N, N + (size_t)G * nc), ff(F, F + (size_t)3 * G * nc);
+        RT_CUDA(h, cudaMemcpyAsync(h->Nf[0], nf.data(), nf.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                   h->stream));
+        RT_CUDA(h, cudaMemcpyAsync(h->Ff[0], ff.data(), ff.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                   h->stream));
+        RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     RT_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, 4 * sizeof(unsigned long long), h->stream));
-    cudaError_t e = launch_reduce_N(G, nc, h->N[0], h->part, h->stream);
+    cudaError_t e = h->mixed ? launch_reduce_N_f32(G, nc, h->Nf[0], h->part, h->stream)
+                             : launch_reduce_N(G, nc, h->N[0], h->part, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
     e = launch_finalize_mode(G, 1, h->part, h->g.dx * h->g.dx * h->g.dx, nullptr, h->budget, h->q, h->status,
                              h->stream);
@@ -454,8 +497,33 @@ int rt_get_state(rt_handle *h, double *nH, double *xHII, double *xHeII, double *
     if (xHeII) RT_CUDA(h, cudaMemcpyAsync(xHeII, h->xHeII, b, k, h->stream));
     if (xHeIII) RT_CUDA(h, cudaMemcpyAsync(xHeIII, h->xHeIII, b, k, h->stream));
     if (T) RT_CUDA(h, cudaMemcpyAsync(T, h->T, b, k, h->stream));
-    if (N) RT_CUDA(h, cudaMemcpyAsync(N, h->N[h->cur], h->G * b, k, h->stream));
-    if (F) RT_CUDA(h, cudaMemcpyAsync(F, h->F[h->cur], 3 * h->G * b, k, h->stream));
+    if (!h->mixed) {
+        if (N) RT_CUDA(h, cudaMemcpyAsync(N, h->N[h->cur], h->G * b, k, h->stream));
+        if (F) RT_CUDA(h, cudaMemcpyAsync(F, h->F[h->cur], 3 * h->G * b, k, h->stream));
+    } else if (device_ptrs) {
+        const long long n1 = (long long)h->G * h->g.nc;
+        cudaError_t ec = cudaSuccess;
+        if (N) ec = launch_convert_f2d(n1, h->Nf[h->cur], N, h->stream);
+        if (F && ec == cudaSuccess) ec = launch_convert_f2d(3 * n1, h->Ff[h->cur], F, h->stream);
+        if (ec != cudaSuccess) return cuda_fail(h, ec, "convert");
+    } else {
+        const size_t n1 = (size_t)h->G * h->g.nc;
+        std::vector<float> tmp;
+        if (N) {
+            tmp.resize(n1);
+            RT_CUDA(h, cudaMemcpyAsync(tmp.data(), h->Nf[h->cur], n1 * sizeof(float), cudaMemcpyDeviceToHost,
+                                       h->stream));
+            RT_CUDA(h, cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < n1; ++i) N[i] = tmp[i];
+        }
+        if (F) {
+            tmp.resize(3 * n1);
+            RT_CUDA(h, cudaMemcpyAsync(tmp.data(), h->Ff[h->cur], 3 * n1 * sizeof(float), cudaMemcpyDeviceToHost,
+                                       h->stream));
+            RT_CUDA(h, cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < 3 * n1; ++i) F[i] = tmp[i];
+        }
+    }
     if (!device_ptrs) RT_CUDA(h, cudaStreamSynchronize(h->stream));
     return rc;
 }

@@ -83,6 +83,10 @@ struct Partials {
 cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
                              const double *N0, const double *F0, double *N1, double *F1,
                              const double *hll_table, const Partials &p, cudaStream_t s);
+// FP32 state (RT_MIXED): same scheme, compensated update.
+cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, double dt, const float *N0,
+                                 const float *F0, float *N1, float *F1, const float *hll_table,
+                                 const Partials &p, cudaStream_t s);
 int transport_blocks_per_group(const GridDev &g);
 void transport_init();   // kernel attributes; called once per handle
 
@@ -93,11 +97,22 @@ cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, doubl
                           int32_t *subcycles, Queue q, unsigned *status, int n_sm,
                           cudaStream_t s, cudaEvent_t *ev = nullptr);
 
+// RT_MIXED: FP32 photon state, FP32 rate transcendentals, FP64 stiff updates.
+cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, const double *nH, double *xHII,
+                                double *xHeII, double *xHeIII, double *T, float *N, float *F,
+                                int32_t *subcycles, Queue q, unsigned *status, int n_sm,
+                                cudaStream_t s, cudaEvent_t *ev = nullptr);
+
 cudaError_t launch_inject(int nsrc, int G, long long nc, const long long *cells,
                           const double *Lsum, double dt_over_V, double *N, cudaStream_t s);
 
 cudaError_t launch_reduce_N(int G, long long nc, const double *N, const Partials &p,
                             cudaStream_t s);
+cudaError_t launch_inject_f32(int nsrc, int G, long long nc, const long long *cells, const double *Lsum,
+                              double dt_over_V, float *N, cudaStream_t s);
+cudaError_t launch_reduce_N_f32(int G, long long nc, const float *N, const Partials &p, cudaStream_t s);
+cudaError_t launch_convert_d2f(long long n, const double *in, float *out, cudaStream_t s);
+cudaError_t launch_convert_f2d(long long n, const float *in, double *out, cudaStream_t s);
 
 int reduce_blocks_per_group();
 

@@ -75,16 +75,22 @@ __device__ __forceinline__ double mu_of(double X, double x, double y2, double y3
     return 1.0 / (X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3));
 }
 
-template <bool WARP>
+template <bool WARP, bool MIX>
 __device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, Transc &t)
 {
-    if (WARP) transc_warp(T, case_b, t);
-    else transc_serial(T, case_b, need, t);
+    if (MIX) {
+        if (WARP) transc_warp_f(T, case_b, t);
+        else transc_serial_f(T, case_b, need, t);
+    } else {
+        if (WARP) transc_warp(T, case_b, t);
+        else transc_serial(T, case_b, need, t);
+    }
 }
 
 // One thermo_step over h.  Returns true and fills `o` and `maxrel` when the
-// 10% rule holds.
-template <int G, bool WARP>
+// 10% rule holds.  MIX (the RT_MIXED path): rates from FP32 transcendentals
+// and the photon update in FP32; T/mu, x_HII, helium and 1 - x stay FP64.
+template <int G, bool WARP, bool MIX>
 __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const CellState<G> &s, double h,
                                         const IsoRates &iso, CoolCache &cc, CellState<G> &o, double &maxrel)
 {
@@ -103,14 +109,28 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
     // 1. photons
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        double D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
-        double inv = 1.0 / (1.0 + h * D);
-        double Nn = s.N[i] * inv;
-        double rel = fabs(Nn - s.N[i]) / fmax(s.N[i], kFloorN);
-        if (rel > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
+        double Nn;
+        if (MIX) {
+            float D = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
+                                   (float)p.gc.sigN[i][2] * (float)nHeII);
+            float inv = 1.0f / (1.0f + (float)h * D);
+            float N0 = (float)s.N[i];
+            float Nf = N0 * inv;
+            float rel = fabsf(Nf - N0) / fmaxf(N0, (float)kFloorN);
+            if (rel > 0.1f) return false;
+            rel_max = fmax(rel_max, (double)rel);
+            Nn = Nf;
+            o.Fs[i] = (float)s.Fs[i] * inv;
+        } else {
+            double D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
+            double inv = 1.0 / (1.0 + h * D);
+            Nn = s.N[i] * inv;
+            double rel = fabs(Nn - s.N[i]) / fmax(s.N[i], kFloorN);
+            if (rel > 0.1) return false;
+            rel_max = fmax(rel_max, rel);
+            o.Fs[i] = s.Fs[i] * inv;
+        }
         o.N[i] = Nn;
-        o.Fs[i] = s.Fs[i] * inv;
         double crN = cr * Nn;
         gam0 += p.gc.sigN[i][0] * crN;
         gam1 += p.gc.sigN[i][1] * crN;
@@ -128,7 +148,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
     if (!p.isothermal) {
         if (!cc.valid) {
             Transc t;
-            get_transc<WARP>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
+            get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
             cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L,
                          cc.dL);
             cc.valid = true;
@@ -151,7 +171,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
         hr = iso.h;
     } else {
         Transc t;
-        get_transc<WARP>(Tmu1 * mu, p.case_b, kNeedH, t);
+        get_transc<WARP, MIX>(Tmu1 * mu, p.case_b, kNeedH, t);
         h_rates_from(t, p.case_b, hr);
     }
     double C = hr.beta * ne + gam0;
@@ -184,7 +204,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
             r2 = iso.he;
         } else {
             Transc t;
-            get_transc<WARP>(Tmu1 * mu_of(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
+            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
             he_rates_from(t, p.case_b, r2);
         }
         double C1 = y2 * r2.alpha_HeII * ne2;
@@ -199,7 +219,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
             r3 = iso.he;
         } else {
             Transc t;
-            get_transc<WARP>(Tmu1 * mu_of(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
+            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
             he_rates_from(t, p.case_b, r3);
         }
         double C3 = y2n * (r3.beta_HeII * ne3 + gam2);
@@ -227,7 +247,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const 
 }
 
 // One attempt of the sub-cycling loop; returns true when the cell is done.
-template <int G, bool WARP>
+template <int G, bool WARP, bool MIX>
 __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, CellState<G> &st, double &t_left,
                                               double &dt_tc, int &att, const IsoRates &iso, CoolCache &cc)
 {
@@ -235,7 +255,7 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, 
     ++att;
     CellState<G> o;
     double mr = 0.0;
-    if (attempt<G, WARP>(p, nH, st, h, iso, cc, o, mr)) {
+    if (attempt<G, WARP, MIX>(p, nH, st, h, iso, cc, o, mr)) {
         st = o;
         cc.valid = false;
         t_left = (h == t_left) ? 0.0 : t_left - h;
@@ -246,10 +266,10 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, 
     return !(t_left > 0.0);
 }
 
-template <int G, bool WARP>
+template <int G, bool WARP, typename P>
 __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, const double *xHII,
                                           const double *xHeII, const double *xHeIII, const double *T,
-                                          const double *N, CellState<G> &st, IsoRates &iso, CoolCache &cc)
+                                          const P *N, CellState<G> &st, IsoRates &iso, CoolCache &cc)
 {
     st.x = xHII[c];
     st.y2 = xHeII[c];
@@ -257,22 +277,22 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, co
     st.T = T[c];
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        st.N[i] = N[(long long)i * p.nc + c];
+        st.N[i] = (double)N[(long long)i * p.nc + c];
         st.Fs[i] = 1.0;
     }
     cc.valid = false;
     if (p.isothermal) {
         Transc t;
-        get_transc<WARP>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
+        get_transc<WARP, sizeof(P) == sizeof(float)>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
         h_rates_from(t, p.case_b, iso.h);
         if (p.helium) he_rates_from(t, p.case_b, iso.he);
     }
 }
 
-template <int G>
+template <int G, typename P>
 __device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, double *xHII, double *xHeII,
-                                           double *xHeIII, double *T, double *N, double *F,
-                                           const CellState<G> &st, unsigned *status)
+                                           double *xHeIII, double *T, P *N, P *F, const CellState<G> &st,
+                                           unsigned *status)
 {
     xHII[c] = st.x;
     xHeII[c] = st.y2;
@@ -281,12 +301,13 @@ __device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, d
     bool bad = !isfinite(st.x) || !isfinite(st.T);
 #pragma unroll
     for (int i = 0; i < G; ++i) {
-        N[(long long)i * p.nc + c] = st.N[i];
+        N[(long long)i * p.nc + c] = (P)st.N[i];
         if (st.Fs[i] != 1.0) {
             long long b = 3LL * i * p.nc + c;
-            F[b] *= st.Fs[i];
-            F[b + p.nc] *= st.Fs[i];
-            F[b + 2 * p.nc] *= st.Fs[i];
+            const P f = (P)st.Fs[i];
+            F[b] *= f;
+            F[b + p.nc] *= f;
+            F[b + 2 * p.nc] *= f;
         }
         bad |= !isfinite(st.N[i]);
     }
@@ -306,10 +327,10 @@ __device__ __forceinline__ void push_item(const QueueArrays &a, unsigned long lo
     }
 }
 
-template <int G>
+template <int G, typename P>
 __global__ void __launch_bounds__(kPass1Block)
 thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
-             double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
+             double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
 {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = c < p.nc;
@@ -320,17 +341,17 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         CellState<G> st;
         IsoRates iso;
         CoolCache cc;
-        load_cell<G, false>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+        load_cell<G, false, P>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         double n = nH[c];
         bool done = false;
         const int lim = p.pass1_attempts < p.max_sub ? p.pass1_attempts : p.max_sub;
         for (int k = 0; k < lim && !done; ++k)
-            done = subcycle_once<G, false>(p, n, st, t_left, dt_tc, att, iso, cc);
+            done = subcycle_once<G, false, sizeof(P) == sizeof(float)>(p, n, st, t_left, dt_tc, att, iso, cc);
         if (!done && att >= p.max_sub) {
             atomicOr(status, kStatusSubcycle);
             done = true;
         }
-        store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+        store_cell<G, P>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
         if (done) subcycles[c] = att;
         else push = true;
     }
@@ -348,10 +369,10 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     }
 }
 
-template <int G>
+template <int G, typename P>
 __global__ void __launch_bounds__(128)
 thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
-             double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
+             double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
 {
     unsigned long long count = q.counters[0];
     if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
@@ -372,7 +393,7 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             att = q.a.attempts[it];
             n = nH[c];
             used = 0;
-            load_cell<G, false>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+            load_cell<G, false, P>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
             have = true;
         } else {
             have = false;
@@ -380,18 +401,18 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     };
     fetch();
     while (have) {
-        bool done = subcycle_once<G, false>(p, n, st, t_left, dt_tc, att, iso, cc);
+        bool done = subcycle_once<G, false, sizeof(P) == sizeof(float)>(p, n, st, t_left, dt_tc, att, iso, cc);
         if (!done && att >= p.max_sub) {
             atomicOr(status, kStatusSubcycle);
             done = true;
         }
         if (done) {
-            store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+            store_cell<G, P>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
             subcycles[c] = att;
             fetch();
         } else if (++used >= kDrainBudget) {
             // long sub-cycler: hand it to the warp-per-cell kernel
-            store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+            store_cell<G, P>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
             unsigned long long slot = atomicAdd(&q.counters[2], 1ULL);
             push_item(q.b, slot, q.capacity, (uint32_t)c, t_left, dt_tc, att, status);
             fetch();
@@ -399,10 +420,10 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     }
 }
 
-template <int G>
+template <int G, typename P>
 __global__ void __launch_bounds__(128)
 thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
-            double *T, double *N, double *F, int32_t *subcycles, Queue q, unsigned *status)
+            double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
 {
     unsigned long long count = q.counters[2];
     if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
@@ -421,37 +442,37 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
         CellState<G> st;
         IsoRates iso;
         CoolCache cc;
-        load_cell<G, true>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+        load_cell<G, true, P>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         bool done = false;
         while (!done) {
-            done = subcycle_once<G, true>(p, n, st, t_left, dt_tc, att, iso, cc);
+            done = subcycle_once<G, true, sizeof(P) == sizeof(float)>(p, n, st, t_left, dt_tc, att, iso, cc);
             if (!done && att >= p.max_sub) {
                 if (lane == 0) atomicOr(status, kStatusSubcycle);
                 done = true;
             }
         }
         if (lane == 0) {
-            store_cell<G>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
+            store_cell<G, P>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
             subcycles[c] = att;
         }
         __syncwarp();
     }
 }
 
-template <int G>
+template <int G, typename P>
 cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, double *xHeII, double *xHeIII,
-                     double *T, double *N, double *F, int32_t *sub, Queue q, unsigned *status, int n_sm,
+                     double *T, P *N, P *F, int32_t *sub, Queue q, unsigned *status, int n_sm,
                      cudaStream_t s, cudaEvent_t *ev)
 {
     const int B = kPass1Block;
     long long nb = (tp.nc + B - 1) / B;
     if (ev) cudaEventRecord(ev[0], s);
-    thermo_pass1<G><<<(unsigned)nb, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_pass1<G, P><<<(unsigned)nb, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G, P>, 128, 0);
         if (per_sm < 1) per_sm = 1;
     }
     long long grid = (long long)per_sm * n_sm;
@@ -459,7 +480,7 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
-    thermo_drain<G><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_drain<G, P><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one warp per long sub-cycler: two 4-warp blocks per SM
@@ -467,28 +488,43 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     long long hneed = (tp.nc + 3) / 4;
     if (hgrid > hneed) hgrid = hneed;
     if (hgrid < 1) hgrid = 1;
-    thermo_hard<G><<<(unsigned)hgrid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_hard<G, P><<<(unsigned)hgrid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+template <typename P>
+static cudaError_t dispatch_g(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
+                              double *xHeIII, double *T, P *N, P *F, int32_t *sub, Queue q, unsigned *status,
+                              int n_sm, cudaStream_t s, cudaEvent_t *ev)
+{
+    switch (G) {
+    case 1: return launch_g<1, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 2: return launch_g<2, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 3: return launch_g<3, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 4: return launch_g<4, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 5: return launch_g<5, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 6: return launch_g<6, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 7: return launch_g<7, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 8: return launch_g<8, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
                           double *xHeIII, double *T, double *N, double *F, int32_t *subcycles, Queue q,
                           unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
 {
-    switch (G) {
-    case 1: return launch_g<1>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 2: return launch_g<2>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 3: return launch_g<3>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 4: return launch_g<4>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 5: return launch_g<5>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 6: return launch_g<6>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 7: return launch_g<7>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    case 8: return launch_g<8>(tp, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
-    default: return cudaErrorInvalidValue;
-    }
+    return dispatch_g<double>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+}
+
+cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
+                                double *xHeIII, double *T, float *N, float *F, int32_t *subcycles, Queue q,
+                                unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
+{
+    return dispatch_g<float>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
 }
 
 }  // namespace rtgb

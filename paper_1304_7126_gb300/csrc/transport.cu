@@ -15,6 +15,12 @@
 // planes are coalesced 256-byte rows.  Per-block photon sums (in the box
 // after transport, net outflow through boundary faces) go to a partials
 // array reduced later in a fixed order, so the budget is reproducible.
+//
+// The kernel is templated on the state type S: double (the FP64 path) or
+// float (the mixed path, RT_MIXED: state stored and transported in FP32,
+// half the HBM traffic; the six face-flux differences are added to U with
+// error-free TwoSum steps and the accumulated rounding error folded back in
+// once, so an update loses one rounding instead of several).
 #include <cuda_runtime.h>
 
 #include "rt_internal.h"
@@ -28,52 +34,57 @@ constexpr int TZC = 16;   // planes per CTA
 constexpr int SW = TBX + 2;
 constexpr int SH = TBY + 2;
 
+template <typename S>
 struct CellQ {
-    double N, Fx, Fy, Fz;            // U
-    double Pxx, Pxy, Pxz, Pyy, Pyz, Pzz;   // c^2 N D
-    double lmin[3], lmax[3];         // HLL wave speeds (already times c)
+    S N, Fx, Fy, Fz;            // U
+    S Pxx, Pxy, Pxz, Pyy, Pyz, Pzz;   // c^2 N D
+    S lmin[3], lmax[3];         // HLL wave speeds (already times c)
 };
 
-__device__ __forceinline__ void hll_lookup(const double *__restrict__ tab, double f, double mu,
-                                           double &lo, double &hi)
+template <typename S> struct Vec2;
+template <> struct Vec2<double> { using T = double2; };
+template <> struct Vec2<float> { using T = float2; };
+
+template <typename S>
+__device__ __forceinline__ void hll_lookup(const S *__restrict__ tab, S f, S mu, S &lo, S &hi)
 {
-    double fx = f * (double)(kHllNF - 1);
+    S fx = f * (S)(kHllNF - 1);
     int k = (int)floor(fx);
     k = k < 0 ? 0 : (k > kHllNF - 2 ? kHllNF - 2 : k);
-    double wf = fx - (double)k;
-    double mx = (mu + 1.0) * 0.5 * (double)(kHllNMU - 1);
+    S wf = fx - (S)k;
+    S mx = (mu + (S)1) * (S)0.5 * (S)(kHllNMU - 1);
     int j = (int)floor(mx);
     j = j < 0 ? 0 : (j > kHllNMU - 2 ? kHllNMU - 2 : j);
-    double wm = mx - (double)j;
-    const double2 *t = reinterpret_cast<const double2 *>(tab);
-    double2 a = __ldg(&t[k * kHllNMU + j]);
-    double2 b = __ldg(&t[k * kHllNMU + j + 1]);
-    double2 c = __ldg(&t[(k + 1) * kHllNMU + j]);
-    double2 d = __ldg(&t[(k + 1) * kHllNMU + j + 1]);
-    double lo0 = a.x + wm * (b.x - a.x), lo1 = c.x + wm * (d.x - c.x);
-    double hi0 = a.y + wm * (b.y - a.y), hi1 = c.y + wm * (d.y - c.y);
+    S wm = mx - (S)j;
+    using V = typename Vec2<S>::T;
+    const V *t = reinterpret_cast<const V *>(tab);
+    V a = __ldg(&t[k * kHllNMU + j]);
+    V b = __ldg(&t[k * kHllNMU + j + 1]);
+    V c = __ldg(&t[(k + 1) * kHllNMU + j]);
+    V d = __ldg(&t[(k + 1) * kHllNMU + j + 1]);
+    S lo0 = a.x + wm * (b.x - a.x), lo1 = c.x + wm * (d.x - c.x);
+    S hi0 = a.y + wm * (b.y - a.y), hi1 = c.y + wm * (d.y - c.y);
     lo = lo0 + wf * (lo1 - lo0);
     hi = hi0 + wf * (hi1 - hi0);
 }
 
 // M1 closure of one cell.  f := 0 for N <= 0 or F = 0; f clamped to 1.
-template <int FLUX>
-__device__ __forceinline__ void closure(double N, double Fx, double Fy, double Fz, double c,
-                                        const double *__restrict__ tab, CellQ &q)
+template <typename S, int FLUX>
+__device__ __forceinline__ void closure(S N, S Fx, S Fy, S Fz, S c, const S *__restrict__ tab, CellQ<S> &q)
 {
     q.N = N; q.Fx = Fx; q.Fy = Fy; q.Fz = Fz;
-    double F2 = Fx * Fx + Fy * Fy + Fz * Fz;
-    double f = 0.0, nx = 0.0, ny = 0.0, nz = 0.0;
-    if (N > 0.0 && F2 > 0.0) {
-        double inv = rsqrt(F2);
-        f = fmin((F2 * inv) / (c * N), 1.0);
+    S F2 = Fx * Fx + Fy * Fy + Fz * Fz;
+    S f = 0, nx = 0, ny = 0, nz = 0;
+    if (N > (S)0 && F2 > (S)0) {
+        S inv = rsqrt(F2);
+        f = fmin((F2 * inv) / (c * N), (S)1);
         nx = Fx * inv; ny = Fy * inv; nz = Fz * inv;
     }
-    double f2 = f * f;
-    double chi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
-    double cN = c * c * N;
-    double ca = cN * 0.5 * (1.0 - chi);
-    double cb = cN * 0.5 * (3.0 * chi - 1.0);
+    S f2 = f * f;
+    S chi = ((S)3 + (S)4 * f2) / ((S)5 + (S)2 * sqrt((S)4 - (S)3 * f2));
+    S cN = c * c * N;
+    S ca = cN * (S)0.5 * ((S)1 - chi);
+    S cb = cN * (S)0.5 * ((S)3 * chi - (S)1);
     q.Pxx = ca + cb * nx * nx;
     q.Pyy = ca + cb * ny * ny;
     q.Pzz = ca + cb * nz * nz;
@@ -81,18 +92,18 @@ __device__ __forceinline__ void closure(double N, double Fx, double Fy, double F
     q.Pxz = cb * nx * nz;
     q.Pyz = cb * ny * nz;
     if (FLUX == RT_HLL) {
-        double lo, hi;
-        hll_lookup(tab, f, nx, lo, hi); q.lmin[0] = lo * c; q.lmax[0] = hi * c;
-        hll_lookup(tab, f, ny, lo, hi); q.lmin[1] = lo * c; q.lmax[1] = hi * c;
-        hll_lookup(tab, f, nz, lo, hi); q.lmin[2] = lo * c; q.lmax[2] = hi * c;
+        S lo, hi;
+        hll_lookup<S>(tab, f, nx, lo, hi); q.lmin[0] = lo * c; q.lmax[0] = hi * c;
+        hll_lookup<S>(tab, f, ny, lo, hi); q.lmin[1] = lo * c; q.lmax[1] = hi * c;
+        hll_lookup<S>(tab, f, nz, lo, hi); q.lmin[2] = lo * c; q.lmax[2] = hi * c;
     }
 }
 
 // Intercell flux along direction D from left cell L to right cell R.
-template <int FLUX, int D>
-__device__ __forceinline__ void face_flux(const CellQ &L, const CellQ &R, double c, double out[4])
+template <typename S, int FLUX, int D>
+__device__ __forceinline__ void face_flux(const CellQ<S> &L, const CellQ<S> &R, S c, S out[4])
 {
-    double fl[4], fr[4], ul[4], ur[4];
+    S fl[4], fr[4], ul[4], ur[4];
     ul[0] = L.N; ul[1] = L.Fx; ul[2] = L.Fy; ul[3] = L.Fz;
     ur[0] = R.N; ur[1] = R.Fx; ur[2] = R.Fy; ur[3] = R.Fz;
     if (D == 0) {
@@ -106,31 +117,40 @@ __device__ __forceinline__ void face_flux(const CellQ &L, const CellQ &R, double
         fr[0] = R.Fz; fr[1] = R.Pxz; fr[2] = R.Pyz; fr[3] = R.Pzz;
     }
     if (FLUX == RT_HLL) {
-        double lp = fmax(0.0, fmax(L.lmax[D], R.lmax[D]));
-        double lm = fmin(0.0, fmin(L.lmin[D], R.lmin[D]));
-        double den = lp - lm;
-        if (den > 0.0) {
-            double inv = 1.0 / den;
-            double pm = lp * lm;
+        S lp = fmax((S)0, fmax(L.lmax[D], R.lmax[D]));
+        S lm = fmin((S)0, fmin(L.lmin[D], R.lmin[D]));
+        S den = lp - lm;
+        if (den > (S)0) {
+            S inv = (S)1 / den;
+            S pm = lp * lm;
 #pragma unroll
             for (int k = 0; k < 4; ++k) out[k] = (lp * fl[k] - lm * fr[k] + pm * (ur[k] - ul[k])) * inv;
         } else {
             // both speeds vanish only for f = 1 beams parallel to the face
 #pragma unroll
-            for (int k = 0; k < 4; ++k) out[k] = 0.5 * (fl[k] + fr[k]);
+            for (int k = 0; k < 4; ++k) out[k] = (S)0.5 * (fl[k] + fr[k]);
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) out[k] = 0.5 * (fl[k] + fr[k]) - 0.5 * c * (ur[k] - ul[k]);
+        for (int k = 0; k < 4; ++k) out[k] = (S)0.5 * (fl[k] + fr[k]) - (S)0.5 * c * (ur[k] - ul[k]);
     }
+}
+
+// Error-free sum a + b = s + e (Knuth's TwoSum), FP32; the _rn intrinsics
+// keep the compiler from contracting the steps into FMAs.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // Load U at (x, y, z) where at most one coordinate may sit one cell outside
 // the box: that position is the boundary ghost (outflow: copy; reflect:
 // copy with the normal flux negated; periodic: wrap).
-__device__ __forceinline__ void load_U(const GridDev &g, const double *__restrict__ N,
-                                       const double *__restrict__ F, int x, int y, int z,
-                                       double &n, double &fx, double &fy, double &fz)
+template <typename S>
+__device__ __forceinline__ void load_U(const GridDev &g, const S *__restrict__ N, const S *__restrict__ F, int x,
+                                       int y, int z, S &n, S &fx, S &fy, S &fz)
 {
     int flip = -1;
     if (x < 0) {
@@ -159,17 +179,18 @@ __device__ __forceinline__ void load_U(const GridDev &g, const double *__restric
 }
 
 // Shared-memory plane of closure quantities needed by the x and y faces.
+template <typename S>
 struct PlaneSmem {
-    double N[SH][SW], Fx[SH][SW], Fy[SH][SW], Fz[SH][SW];
-    double Pxx[SH][SW], Pxy[SH][SW], Pxz[SH][SW], Pyy[SH][SW], Pyz[SH][SW];
-    double lminx[SH][SW], lmaxx[SH][SW], lminy[SH][SW], lmaxy[SH][SW];
-    double fxs[4][TBY][TBX + 1];     // x faces 0..32 of each row
-    double fys[4][TBY + 1][TBX];     // y faces 0..8 of each column
+    S N[SH][SW], Fx[SH][SW], Fy[SH][SW], Fz[SH][SW];
+    S Pxx[SH][SW], Pxy[SH][SW], Pxz[SH][SW], Pyy[SH][SW], Pyz[SH][SW];
+    S lminx[SH][SW], lmaxx[SH][SW], lminy[SH][SW], lmaxy[SH][SW];
+    S fxs[4][TBY][TBX + 1];     // x faces 0..32 of each row
+    S fys[4][TBY + 1][TBX];     // y faces 0..8 of each column
     double red[2][TBX * TBY / 32];
 };
 
-template <int FLUX>
-__device__ __forceinline__ void put_plane(PlaneSmem &s, int r, int c, const CellQ &q)
+template <typename S, int FLUX>
+__device__ __forceinline__ void put_plane(PlaneSmem<S> &s, int r, int c, const CellQ<S> &q)
 {
     s.N[r][c] = q.N; s.Fx[r][c] = q.Fx; s.Fy[r][c] = q.Fy; s.Fz[r][c] = q.Fz;
     s.Pxx[r][c] = q.Pxx; s.Pxy[r][c] = q.Pxy; s.Pxz[r][c] = q.Pxz; s.Pyy[r][c] = q.Pyy; s.Pyz[r][c] = q.Pyz;
@@ -179,29 +200,28 @@ __device__ __forceinline__ void put_plane(PlaneSmem &s, int r, int c, const Cell
     }
 }
 
-template <int FLUX>
-__device__ __forceinline__ void get_plane(const PlaneSmem &s, int r, int c, CellQ &q)
+template <typename S, int FLUX>
+__device__ __forceinline__ void get_plane(const PlaneSmem<S> &s, int r, int c, CellQ<S> &q)
 {
     q.N = s.N[r][c]; q.Fx = s.Fx[r][c]; q.Fy = s.Fy[r][c]; q.Fz = s.Fz[r][c];
     q.Pxx = s.Pxx[r][c]; q.Pxy = s.Pxy[r][c]; q.Pxz = s.Pxz[r][c]; q.Pyy = s.Pyy[r][c]; q.Pyz = s.Pyz[r][c];
-    q.Pzz = 0.0;
+    q.Pzz = 0;
     if (FLUX == RT_HLL) {
         q.lmin[0] = s.lminx[r][c]; q.lmax[0] = s.lmaxx[r][c];
         q.lmin[1] = s.lminy[r][c]; q.lmax[1] = s.lmaxy[r][c];
-        q.lmin[2] = 0.0; q.lmax[2] = 0.0;
+        q.lmin[2] = 0; q.lmax[2] = 0;
     }
 }
 
-template <int FLUX>
+template <typename S, int FLUX>
 __global__ void __launch_bounds__(TBX * TBY)
-transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double *__restrict__ N0all,
-                 const double *__restrict__ F0all, double *__restrict__ N1all,
-                 double *__restrict__ F1all, const double *__restrict__ tab,
-                 double *__restrict__ part_inbox, double *__restrict__ part_out, int tiles_x,
-                 int tiles_y, int nblk)
+transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
+                 const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
+                 const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
+                 int tiles_x, int tiles_y, int nblk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PlaneSmem &s = *reinterpret_cast<PlaneSmem *>(smem_raw);
+    PlaneSmem<S> &s = *reinterpret_cast<PlaneSmem<S> *>(smem_raw);
 
     const int grp = blockIdx.y;
     const int tile = blockIdx.x;
@@ -211,10 +231,10 @@ transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double 
     const int x0 = tile_x * TBX, y0 = tile_y * TBY;
     const int z0 = zc * TZC;
     const int z1 = min(z0 + TZC, g.nz);
-    const double *N0 = N0all + (long long)grp * g.nc;
-    const double *F0 = F0all + 3LL * grp * g.nc;
-    double *N1 = N1all + (long long)grp * g.nc;
-    double *F1 = F1all + 3LL * grp * g.nc;
+    const S *N0 = N0all + (long long)grp * g.nc;
+    const S *F0 = F0all + 3LL * grp * g.nc;
+    S *N1 = N1all + (long long)grp * g.nc;
+    S *F1 = F1all + 3LL * grp * g.nc;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TBX + tx;
@@ -242,39 +262,39 @@ transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double 
         hvalid = hx < g.nx && hy <= g.ny;
     }
 
-    CellQ cur, nxt;
-    double flo[4] = {0, 0, 0, 0}, fhi[4] = {0, 0, 0, 0};
+    CellQ<S> cur, nxt;
+    S flo[4] = {0, 0, 0, 0}, fhi[4] = {0, 0, 0, 0};
     double inbox = 0.0, outflow = 0.0;
     if (active) {
-        double n, fx, fy, fz;
-        load_U(g, N0, F0, x, y, z0 - 1, n, fx, fy, fz);
-        CellQ prev;
-        closure<FLUX>(n, fx, fy, fz, c, tab, prev);
-        load_U(g, N0, F0, x, y, z0, n, fx, fy, fz);
-        closure<FLUX>(n, fx, fy, fz, c, tab, cur);
-        face_flux<FLUX, 2>(prev, cur, c, flo);
+        S n, fx, fy, fz;
+        load_U<S>(g, N0, F0, x, y, z0 - 1, n, fx, fy, fz);
+        CellQ<S> prev;
+        closure<S, FLUX>(n, fx, fy, fz, c, tab, prev);
+        load_U<S>(g, N0, F0, x, y, z0, n, fx, fy, fz);
+        closure<S, FLUX>(n, fx, fy, fz, c, tab, cur);
+        face_flux<S, FLUX, 2>(prev, cur, c, flo);
     }
 
     for (int z = z0; z < z1; ++z) {
         if (active) {
-            double n, fx, fy, fz;
-            load_U(g, N0, F0, x, y, z + 1, n, fx, fy, fz);
-            closure<FLUX>(n, fx, fy, fz, c, tab, nxt);
-            face_flux<FLUX, 2>(cur, nxt, c, fhi);
-            put_plane<FLUX>(s, ty + 1, tx + 1, cur);
+            S n, fx, fy, fz;
+            load_U<S>(g, N0, F0, x, y, z + 1, n, fx, fy, fz);
+            closure<S, FLUX>(n, fx, fy, fz, c, tab, nxt);
+            face_flux<S, FLUX, 2>(cur, nxt, c, fhi);
+            put_plane<S, FLUX>(s, ty + 1, tx + 1, cur);
         } else if (ghost_slot) {
-            double n, fx, fy, fz;
-            CellQ q;
-            load_U(g, N0, F0, x, y, z, n, fx, fy, fz);
-            closure<FLUX>(n, fx, fy, fz, c, tab, q);
-            put_plane<FLUX>(s, ty + 1, tx + 1, q);
+            S n, fx, fy, fz;
+            CellQ<S> q;
+            load_U<S>(g, N0, F0, x, y, z, n, fx, fy, fz);
+            closure<S, FLUX>(n, fx, fy, fz, c, tab, q);
+            put_plane<S, FLUX>(s, ty + 1, tx + 1, q);
         }
         if (hvalid) {
-            double n, fx, fy, fz;
-            CellQ q;
-            load_U(g, N0, F0, hx, hy, z, n, fx, fy, fz);
-            closure<FLUX>(n, fx, fy, fz, c, tab, q);
-            put_plane<FLUX>(s, hr, hc, q);
+            S n, fx, fy, fz;
+            CellQ<S> q;
+            load_U<S>(g, N0, F0, hx, hy, z, n, fx, fy, fz);
+            closure<S, FLUX>(n, fx, fy, fz, c, tab, q);
+            put_plane<S, FLUX>(s, hr, hc, q);
         }
         __syncthreads();
 
@@ -287,15 +307,15 @@ transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double 
                 const int ff = tx + q;   // q = 1 only for the last thread: face TBX
                 const int gxf = x0 + ff;
                 if (gxf <= g.nx) {
-                    CellQ L, R;
-                    get_plane<FLUX>(s, ty + 1, ff, L);
-                    get_plane<FLUX>(s, ty + 1, ff + 1, R);
-                    double fl[4];
-                    face_flux<FLUX, 0>(L, R, c, fl);
+                    CellQ<S> L, R;
+                    get_plane<S, FLUX>(s, ty + 1, ff, L);
+                    get_plane<S, FLUX>(s, ty + 1, ff + 1, R);
+                    S fl[4];
+                    face_flux<S, FLUX, 0>(L, R, c, fl);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) s.fxs[k][ty][ff] = fl[k];
-                    if (gxf == 0 && bc_x_lo) outflow -= fl[0];
-                    if (gxf == g.nx && bc_x_hi) outflow += fl[0];
+                    if (gxf == 0 && bc_x_lo) outflow -= (double)fl[0];
+                    if (gxf == g.nx && bc_x_hi) outflow += (double)fl[0];
                 }
             }
         }
@@ -303,52 +323,70 @@ transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double 
         if (x < g.nx) {
             int gyf = y0 + ty;
             if (gyf <= g.ny) {
-                CellQ L, R;
-                get_plane<FLUX>(s, ty, tx + 1, L);
-                get_plane<FLUX>(s, ty + 1, tx + 1, R);
-                double fl[4];
-                face_flux<FLUX, 1>(L, R, c, fl);
+                CellQ<S> L, R;
+                get_plane<S, FLUX>(s, ty, tx + 1, L);
+                get_plane<S, FLUX>(s, ty + 1, tx + 1, R);
+                S fl[4];
+                face_flux<S, FLUX, 1>(L, R, c, fl);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) s.fys[k][ty][tx] = fl[k];
-                if (gyf == 0 && bc_y_lo) outflow -= fl[0];
-                if (gyf == g.ny && bc_y_hi) outflow += fl[0];
+                if (gyf == 0 && bc_y_lo) outflow -= (double)fl[0];
+                if (gyf == g.ny && bc_y_hi) outflow += (double)fl[0];
             }
             if (ty == TBY - 1) {
                 int gyt = y0 + TBY;
                 if (gyt <= g.ny) {
-                    CellQ L, R;
-                    get_plane<FLUX>(s, TBY, tx + 1, L);
-                    get_plane<FLUX>(s, TBY + 1, tx + 1, R);
-                    double fl[4];
-                    face_flux<FLUX, 1>(L, R, c, fl);
+                    CellQ<S> L, R;
+                    get_plane<S, FLUX>(s, TBY, tx + 1, L);
+                    get_plane<S, FLUX>(s, TBY + 1, tx + 1, R);
+                    S fl[4];
+                    face_flux<S, FLUX, 1>(L, R, c, fl);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) s.fys[k][TBY][tx] = fl[k];
-                    if (gyt == g.ny && bc_y_hi) outflow += fl[0];
+                    if (gyt == g.ny && bc_y_hi) outflow += (double)fl[0];
                 }
             }
         }
         __syncthreads();
 
         if (active) {
-            double u[4] = {cur.N, cur.Fx, cur.Fy, cur.Fz};
-            double nw[4];
+            S u[4] = {cur.N, cur.Fx, cur.Fy, cur.Fz};
+            S nw[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                double acc = (s.fxs[k][ty][tx] - s.fxs[k][ty][tx + 1]) +
-                             (s.fys[k][ty][tx] - s.fys[k][ty + 1][tx]) + (flo[k] - fhi[k]);
-                nw[k] = u[k] + dtdx * acc;
+                if (sizeof(S) == sizeof(double)) {
+                    S acc = (s.fxs[k][ty][tx] - s.fxs[k][ty][tx + 1]) +
+                            (s.fys[k][ty][tx] - s.fys[k][ty + 1][tx]) + (flo[k] - fhi[k]);
+                    nw[k] = u[k] + dtdx * acc;
+                } else {
+                    // compensated: U + sum of six dt/dx-scaled face fluxes
+                    float d = (float)dtdx;
+                    float t[6] = {__fmul_rn(d, (float)s.fxs[k][ty][tx]), -__fmul_rn(d, (float)s.fxs[k][ty][tx + 1]),
+                                  __fmul_rn(d, (float)s.fys[k][ty][tx]), -__fmul_rn(d, (float)s.fys[k][ty + 1][tx]),
+                                  __fmul_rn(d, (float)flo[k]), -__fmul_rn(d, (float)fhi[k])};
+                    float sum = (float)u[k], err = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        float e;
+                        two_sum(sum, t[q], sum, e);
+                        err = __fadd_rn(err, e);
+                    }
+                    nw[k] = (S)__fadd_rn(sum, err);
+                }
             }
             // realisability |F| <= c N (acts only at rounding level for CFL <= 1)
-            if (nw[0] < 0.0) { nw[0] = 0.0; nw[1] = nw[2] = nw[3] = 0.0; }
-            // squares of values below ~1e-154 lose digits: compare tiny
-            // states scaled by 2^600 (exact), the factor is scale-free
-            double cn = c * nw[0];
-            double m = fmax(fmax(fabs(nw[1]), fabs(nw[2])), fmax(fabs(nw[3]), cn));
-            double s = (m < 1e-140) ? 0x1p600 : 1.0;
-            double f1 = nw[1] * s, f2 = nw[2] * s, f3 = nw[3] * s, cs = cn * s;
-            double F2 = f1 * f1 + f2 * f2 + f3 * f3;
+            if (nw[0] < (S)0) { nw[0] = 0; nw[1] = nw[2] = nw[3] = 0; }
+            // squares of tiny values lose digits: compare tiny states scaled
+            // by a power of two (exact), the factor is scale-free
+            S cn = c * nw[0];
+            S m = fmax(fmax(fabs(nw[1]), fabs(nw[2])), fmax(fabs(nw[3]), cn));
+            const S tiny = sizeof(S) == sizeof(double) ? (S)1e-140 : (S)1e-15;
+            const S big = sizeof(S) == sizeof(double) ? (S)0x1p600 : (S)0x1p60;
+            S sc0 = (m < tiny) ? big : (S)1;
+            S f1 = nw[1] * sc0, f2 = nw[2] * sc0, f3 = nw[3] * sc0, cs = cn * sc0;
+            S F2 = f1 * f1 + f2 * f2 + f3 * f3;
             if (F2 > cs * cs) {
-                double sc = (F2 > 0.0) ? cs * rsqrt(F2) : 0.0;
+                S sc = (F2 > (S)0) ? cs * rsqrt(F2) : (S)0;
                 nw[1] *= sc; nw[2] *= sc; nw[3] *= sc;
             }
             long long i = ((long long)z * g.ny + y) * g.nx + x;
@@ -356,9 +394,9 @@ transport_kernel(GridDev g, double c, double dtdx, double area_dt, const double 
             F1[i] = nw[1];
             F1[g.nc + i] = nw[2];
             F1[2 * g.nc + i] = nw[3];
-            inbox += nw[0];
-            if (z == 0 && bc_z_lo) outflow -= flo[0];
-            if (z == g.nz - 1 && bc_z_hi) outflow += fhi[0];
+            inbox += (double)nw[0];
+            if (z == 0 && bc_z_lo) outflow -= (double)flo[0];
+            if (z == g.nz - 1 && bc_z_hi) outflow += (double)fhi[0];
             cur = nxt;
 #pragma unroll
             for (int k = 0; k < 4; ++k) flo[k] = fhi[k];
@@ -395,30 +433,46 @@ int transport_blocks_per_group(const GridDev &g)
 
 void transport_init()
 {
-    int smem = (int)sizeof(PlaneSmem);
-    cudaFuncSetAttribute(transport_kernel<RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(transport_kernel<RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int s8 = (int)sizeof(PlaneSmem<double>), s4 = (int)sizeof(PlaneSmem<float>);
+    cudaFuncSetAttribute(transport_kernel<double, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
+    cudaFuncSetAttribute(transport_kernel<double, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
+    cudaFuncSetAttribute(transport_kernel<float, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+    cudaFuncSetAttribute(transport_kernel<float, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
 }
 
-cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
-                             const double *N0, const double *F0, double *N1, double *F1,
-                             const double *hll_table, const Partials &p, cudaStream_t st)
+template <typename S>
+static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double dt, const S *N0, const S *F0,
+                            S *N1, S *F1, const S *tab, const Partials &p, cudaStream_t st)
 {
     int tiles_x = (g.nx + TBX - 1) / TBX;
     int tiles_y = (g.ny + TBY - 1) / TBY;
     int nblk = transport_blocks_per_group(g);
     dim3 grid(nblk, G);
     dim3 block(TBX, TBY);
-    size_t smem = sizeof(PlaneSmem);
-    double dtdx = dt / g.dx;
+    size_t smem = sizeof(PlaneSmem<S>);
+    S dtdx = (S)(dt / g.dx);
     double area_dt = g.dx * g.dx * dt;
     if (flux == RT_HLL)
-        transport_kernel<RT_HLL><<<grid, block, smem, st>>>(g, cr, dtdx, area_dt, N0, F0, N1, F1, hll_table,
-                                                            p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+        transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                               p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
     else
-        transport_kernel<RT_GLF><<<grid, block, smem, st>>>(g, cr, dtdx, area_dt, N0, F0, N1, F1, hll_table,
-                                                            p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+        transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                               p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
     return cudaGetLastError();
+}
+
+cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
+                             const double *N0, const double *F0, double *N1, double *F1,
+                             const double *hll_table, const Partials &p, cudaStream_t st)
+{
+    return launch_t<double>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, p, st);
+}
+
+cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, double dt, const float *N0,
+                                 const float *F0, float *N1, float *F1, const float *hll_table,
+                                 const Partials &p, cudaStream_t st)
+{
+    return launch_t<float>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, p, st);
 }
 
 }  // namespace rtgb
