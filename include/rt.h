@@ -53,7 +53,7 @@ extern "C" {
 
 enum { RT_BC_OUTFLOW = 0, RT_BC_REFLECT = 1, RT_BC_PERIODIC = 2 };
 enum { RT_GLF = 0, RT_HLL = 1 };
-enum { RT_FP64 = 0, RT_MIXED = 1 };
+enum { RT_FP64 = 0, RT_MIXED = 1, RT_MIXED32 = 2 };
 
 typedef struct rt_handle rt_handle;
 
@@ -70,8 +70,10 @@ typedef struct {
  * Y = 0).  isothermal: T held fixed.  otsa: on-the-spot approximation
  * (case-B rates, no recombination photons; Sec. 3.3.2) - must be 1.
  * flux: RT_GLF (default) or RT_HLL.  cfl: Courant factor (0.8).
- * precision: RT_FP64 or RT_MIXED (FP32 transport with compensated face
- * sums, FP64 thermochemistry).  a_exp: expansion factor in the Compton
+ * precision: RT_FP64; RT_MIXED (photon state and transport in FP32 with
+ * compensated face sums, thermochemistry in FP64); RT_MIXED32 (as
+ * RT_MIXED, with the rate transcendentals and the photon update of the
+ * thermochemistry in FP32 and the x, T updates in FP64).  a_exp: expansion factor in the Compton
  * term (1).  max_subcycles: thermochemistry attempts allowed per cell and
  * step (1e6).  smooth: must be 0. */
 typedef struct {

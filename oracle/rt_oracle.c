@@ -185,15 +185,17 @@ double oracle_chi(double f)
 }
 
 /* Eddington tensor D (row-major 3x3) of a cell with photon density N and
- * flux F, at light speed c.  READING: f := 0 when N <= 0 or F = 0 (the
- * direction is then irrelevant), and f is clamped to 1 in chi. */
+ * flux F, at light speed c.  READING: f := 0 when F = 0 or when N is below
+ * the photon-density floor FLOOR_N (no photons: the direction is then
+ * irrelevant and the reduced flux of such a cell is not resolved by the
+ * state's precision), and f is clamped to 1 in chi. */
 void oracle_eddington(double c, double N, const double F[3], double D[9],
                       double *f_out, double n_out[3])
 {
     double Fmag = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
     double f = 0.0;
     double n[3] = {0.0, 0.0, 0.0};
-    if (N > 0.0 && Fmag > 0.0) {
+    if (N > FLOOR_N && Fmag > 0.0) {
         f = Fmag / (c * N);
         if (f > 1.0) f = 1.0;
         n[0] = F[0] / Fmag;

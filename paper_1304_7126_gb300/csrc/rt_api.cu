@@ -209,7 +209,7 @@ int enqueue_step(rt_handle *h, double dt, bool capturing = false)
         prof_pair(h, 3, &tev[2], &tev[3]);
     }
     if (h->mixed)
-        e = launch_thermo_mixed(tp, h->G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->Nf[h->cur],
+        e = launch_thermo_mixed(tp, h->G, h->opt.precision == RT_MIXED32, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->Nf[h->cur],
                                 h->Ff[h->cur], h->subcycles, h->q, h->status, h->n_sm, h->stream,
                                 prof ? tev : nullptr);
     else
@@ -300,7 +300,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return RT_EINVAL;
     if (opt->flux != RT_GLF && opt->flux != RT_HLL) return RT_EINVAL;
     if (opt->otsa != 1 || opt->smooth != 0) return RT_EINVAL;
-    if (opt->precision != RT_FP64 && opt->precision != RT_MIXED) return RT_EINVAL;
+    if (opt->precision != RT_FP64 && opt->precision != RT_MIXED && opt->precision != RT_MIXED32) return RT_EINVAL;
     if (!(opt->a_exp > 0.0) || opt->max_subcycles < 1) return RT_EINVAL;
     for (int i = 0; i < 3 * n_groups; ++i)
         if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0) || !std::isfinite(sigN[i]) || !std::isfinite(sigE[i]))
@@ -315,7 +315,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     for (int i = 0; i < 6; ++i) h->g.bc[i] = grid->bc[i];
     h->G = n_groups;
     h->opt = *opt;
-    h->mixed = opt->precision == RT_MIXED;
+    h->mixed = opt->precision == RT_MIXED || opt->precision == RT_MIXED32;
     h->cr = c_r;
     for (int i = 0; i < n_groups; ++i) {
         for (int j = 0; j < 3; ++j) {

@@ -97,8 +97,9 @@ cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, doubl
                           int32_t *subcycles, Queue q, unsigned *status, int n_sm,
                           cudaStream_t s, cudaEvent_t *ev = nullptr);
 
-// RT_MIXED: FP32 photon state, FP32 rate transcendentals, FP64 stiff updates.
-cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, const double *nH, double *xHII,
+// FP32 photon state (RT_MIXED: FP64 thermochemistry; RT_MIXED32, rates32:
+// FP32 rate transcendentals and photon update, FP64 stiff x/T updates).
+cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, bool rates32, const double *nH, double *xHII,
                                 double *xHeII, double *xHeIII, double *T, float *N, float *F,
                                 int32_t *subcycles, Queue q, unsigned *status, int n_sm,
                                 cudaStream_t s, cudaEvent_t *ev = nullptr);

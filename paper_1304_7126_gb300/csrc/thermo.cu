@@ -266,7 +266,7 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, 
     return !(t_left > 0.0);
 }
 
-template <int G, bool WARP, typename P>
+template <int G, bool WARP, typename P, bool R32>
 __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, const double *xHII,
                                           const double *xHeII, const double *xHeIII, const double *T,
                                           const P *N, CellState<G> &st, IsoRates &iso, CoolCache &cc)
@@ -283,7 +283,7 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, co
     cc.valid = false;
     if (p.isothermal) {
         Transc t;
-        get_transc<WARP, sizeof(P) == sizeof(float)>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
+        get_transc<WARP, R32>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
         h_rates_from(t, p.case_b, iso.h);
         if (p.helium) he_rates_from(t, p.case_b, iso.he);
     }
@@ -327,7 +327,7 @@ __device__ __forceinline__ void push_item(const QueueArrays &a, unsigned long lo
     }
 }
 
-template <int G, typename P>
+template <int G, typename P, bool R32>
 __global__ void __launch_bounds__(kPass1Block)
 thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
              double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
@@ -341,12 +341,12 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         CellState<G> st;
         IsoRates iso;
         CoolCache cc;
-        load_cell<G, false, P>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+        load_cell<G, false, P, R32>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         double n = nH[c];
         bool done = false;
         const int lim = p.pass1_attempts < p.max_sub ? p.pass1_attempts : p.max_sub;
         for (int k = 0; k < lim && !done; ++k)
-            done = subcycle_once<G, false, sizeof(P) == sizeof(float)>(p, n, st, t_left, dt_tc, att, iso, cc);
+            done = subcycle_once<G, false, R32>(p, n, st, t_left, dt_tc, att, iso, cc);
         if (!done && att >= p.max_sub) {
             atomicOr(status, kStatusSubcycle);
             done = true;
@@ -369,7 +369,7 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     }
 }
 
-template <int G, typename P>
+template <int G, typename P, bool R32>
 __global__ void __launch_bounds__(128)
 thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
              double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
@@ -393,7 +393,7 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             att = q.a.attempts[it];
             n = nH[c];
             used = 0;
-            load_cell<G, false, P>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+            load_cell<G, false, P, R32>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
             have = true;
         } else {
             have = false;
@@ -401,7 +401,7 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     };
     fetch();
     while (have) {
-        bool done = subcycle_once<G, false, sizeof(P) == sizeof(float)>(p, n, st, t_left, dt_tc, att, iso, cc);
+        bool done = subcycle_once<G, false, R32>(p, n, st, t_left, dt_tc, att, iso, cc);
         if (!done && att >= p.max_sub) {
             atomicOr(status, kStatusSubcycle);
             done = true;
@@ -420,7 +420,7 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     }
 }
 
-template <int G, typename P>
+template <int G, typename P, bool R32>
 __global__ void __launch_bounds__(128)
 thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
             double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
@@ -442,10 +442,10 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
         CellState<G> st;
         IsoRates iso;
         CoolCache cc;
-        load_cell<G, true, P>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
+        load_cell<G, true, P, R32>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         bool done = false;
         while (!done) {
-            done = subcycle_once<G, true, sizeof(P) == sizeof(float)>(p, n, st, t_left, dt_tc, att, iso, cc);
+            done = subcycle_once<G, true, R32>(p, n, st, t_left, dt_tc, att, iso, cc);
             if (!done && att >= p.max_sub) {
                 if (lane == 0) atomicOr(status, kStatusSubcycle);
                 done = true;
@@ -459,7 +459,7 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
     }
 }
 
-template <int G, typename P>
+template <int G, typename P, bool R32>
 cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, double *xHeII, double *xHeIII,
                      double *T, P *N, P *F, int32_t *sub, Queue q, unsigned *status, int n_sm,
                      cudaStream_t s, cudaEvent_t *ev)
@@ -467,12 +467,12 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     const int B = kPass1Block;
     long long nb = (tp.nc + B - 1) / B;
     if (ev) cudaEventRecord(ev[0], s);
-    thermo_pass1<G, P><<<(unsigned)nb, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_pass1<G, P, R32><<<(unsigned)nb, B, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G, P>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_drain<G, P, R32>, 128, 0);
         if (per_sm < 1) per_sm = 1;
     }
     long long grid = (long long)per_sm * n_sm;
@@ -480,7 +480,7 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
-    thermo_drain<G, P><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_drain<G, P, R32><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one warp per long sub-cycler: two 4-warp blocks per SM
@@ -488,27 +488,27 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     long long hneed = (tp.nc + 3) / 4;
     if (hgrid > hneed) hgrid = hneed;
     if (hgrid < 1) hgrid = 1;
-    thermo_hard<G, P><<<(unsigned)hgrid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
+    thermo_hard<G, P, R32><<<(unsigned)hgrid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-template <typename P>
+template <typename P, bool R32>
 static cudaError_t dispatch_g(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
                               double *xHeIII, double *T, P *N, P *F, int32_t *sub, Queue q, unsigned *status,
                               int n_sm, cudaStream_t s, cudaEvent_t *ev)
 {
     switch (G) {
-    case 1: return launch_g<1, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 2: return launch_g<2, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 3: return launch_g<3, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 4: return launch_g<4, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 5: return launch_g<5, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 6: return launch_g<6, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 7: return launch_g<7, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
-    case 8: return launch_g<8, P>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 1: return launch_g<1, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 2: return launch_g<2, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 3: return launch_g<3, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 4: return launch_g<4, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 5: return launch_g<5, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 6: return launch_g<6, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 7: return launch_g<7, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
+    case 8: return launch_g<8, P, R32>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status, n_sm, s, ev);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -517,14 +517,16 @@ cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, doubl
                           double *xHeIII, double *T, double *N, double *F, int32_t *subcycles, Queue q,
                           unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
 {
-    return dispatch_g<double>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    return dispatch_g<double, false>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
 }
 
-cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
-                                double *xHeIII, double *T, float *N, float *F, int32_t *subcycles, Queue q,
-                                unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
+cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, bool rates32, const double *nH, double *xHII,
+                                double *xHeII, double *xHeIII, double *T, float *N, float *F, int32_t *subcycles,
+                                Queue q, unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
 {
-    return dispatch_g<float>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    if (rates32)
+        return dispatch_g<float, true>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
+    return dispatch_g<float, false>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, subcycles, q, status, n_sm, s, ev);
 }
 
 }  // namespace rtgb

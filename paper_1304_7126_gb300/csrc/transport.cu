@@ -68,17 +68,29 @@ __device__ __forceinline__ void hll_lookup(const S *__restrict__ tab, S f, S mu,
     hi = hi0 + wf * (hi1 - hi0);
 }
 
-// M1 closure of one cell.  f := 0 for N <= 0 or F = 0; f clamped to 1.
+// Photon densities below this are no photons: the closure takes f = 0.
+constexpr double kClosureFloorN = 1e-30;
+
+// M1 closure of one cell.  f := 0 for F = 0 or N below kClosureFloorN; f
+// clamped to 1.  In FP32, F is scaled by a power of two (exact) for the
+// direction and |F| so that its square neither underflows for N down to the
+// floor nor overflows.
 template <typename S, int FLUX>
 __device__ __forceinline__ void closure(S N, S Fx, S Fy, S Fz, S c, const S *__restrict__ tab, CellQ<S> &q)
 {
     q.N = N; q.Fx = Fx; q.Fy = Fy; q.Fz = Fz;
-    S F2 = Fx * Fx + Fy * Fy + Fz * Fz;
+    S sc = (S)1;
+    if (sizeof(S) != sizeof(double)) {
+        S m = fmax(fabs(Fx), fmax(fabs(Fy), fabs(Fz)));
+        sc = (m < (S)1e-15) ? (S)0x1p64 : ((m > (S)1e15) ? (S)0x1p-64 : (S)1);
+    }
+    const S gx = Fx * sc, gy = Fy * sc, gz = Fz * sc;
+    S F2 = gx * gx + gy * gy + gz * gz;
     S f = 0, nx = 0, ny = 0, nz = 0;
-    if (N > (S)0 && F2 > (S)0) {
+    if (N > (S)kClosureFloorN && F2 > (S)0) {
         S inv = rsqrt(F2);
-        f = fmin((F2 * inv) / (c * N), (S)1);
-        nx = Fx * inv; ny = Fy * inv; nz = Fz * inv;
+        f = fmin((F2 * inv) / (c * N * sc), (S)1);
+        nx = gx * inv; ny = gy * inv; nz = gz * inv;
     }
     S f2 = f * f;
     S chi = ((S)3 + (S)4 * f2) / ((S)5 + (S)2 * sqrt((S)4 - (S)3 * f2));

@@ -19,7 +19,7 @@ RT_OK, RT_EINVAL, RT_EDT, RT_ESUBCYCLE, RT_EQUEUE, RT_ECUDA, RT_ENOMEM, RT_ENONF
     0, -1, -2, -3, -4, -5, -6, -7
 RT_BC_OUTFLOW, RT_BC_REFLECT, RT_BC_PERIODIC = 0, 1, 2
 RT_GLF, RT_HLL = 0, 1
-RT_FP64, RT_MIXED = 0, 1
+RT_FP64, RT_MIXED, RT_MIXED32 = 0, 1, 2
 RT_MAX_GROUPS = 8
 
 ERROR_NAMES = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_EDT", -3: "RT_ESUBCYCLE", -4: "RT_EQUEUE",

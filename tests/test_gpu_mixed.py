@@ -1,6 +1,7 @@
 """RT_MIXED (FP32 photon state and transport with compensated face sums,
-FP32 rate transcendentals, FP64 stiff x/T updates) against the FP64 oracle
-and the FP64 GPU path.
+FP64 thermochemistry) and RT_MIXED32 (as RT_MIXED with FP32 rate
+transcendentals and photon update, FP64 x/T updates) against the FP64
+oracle and the FP64 GPU path.
 
 Stated accuracy of the mixed form (per field, max over cells):
 ionised fractions 1e-4 absolute, T 1e-3 relative, N 1e-4 relative (floor
@@ -9,12 +10,12 @@ ionised fractions 1e-4 absolute, T 1e-3 relative, N 1e-4 relative (floor
 The 10% rule is a discrete decision: an FP32 perturbation of ~1e-7 can flip
 a decision that sat that close to the threshold, and the cell then follows
 another sub-step schedule, whose result differs by the rule's own
-truncation error (up to a few per cent).  Such flips are rare with GLF
-(none in these runs) and more frequent with HLL.  The tolerances are
-therefore checked over the cells whose attempt counts agreed with the
-reference in every step, excluding their face neighbours (which receive the
-perturbed photons); the excluded fraction must stay below 5%, and the
-box-averaged x_HII, T and the photon budget must agree to 1e-3."""
+truncation error (up to a few per cent).  Such flips are rare (none or one
+per step in these runs).  The tolerances are therefore checked over the
+cells whose attempt counts agreed with the reference in every step,
+excluding their face neighbours (which receive the perturbed photons); the
+excluded fraction must stay below 1%, and the box-averaged x_HII, T and
+the photon budget must agree to 1e-3."""
 import numpy as np
 import pytest
 
@@ -35,7 +36,7 @@ def _dilate(m):
 def _check(got, ref, w, flipped):
     nc = w.ncells
     keep = ~_dilate(flipped.reshape(w.shape)).reshape(-1)
-    assert keep.mean() >= 0.95, ("too many flipped schedules", 1 - keep.mean())
+    assert keep.mean() >= 0.99, ("too many flipped schedules", 1 - keep.mean())
     kG = np.tile(keep, w.G)
     errs = {
         "xHII": float(np.max(np.abs(got["xHII"] - ref["xHII"])[keep], initial=0.0)),
@@ -60,12 +61,13 @@ def R():
     return rt
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed32"])
 @pytest.mark.parametrize("flux", [1, 0])
 @pytest.mark.parametrize("n,nx,ny", [(16, None, None), (18, 37, 11)])
-def test_mixed_vs_oracle(oracle_mod, R, flux, n, nx, ny):
+def test_mixed_vs_oracle(oracle_mod, R, prec, flux, n, nx, ny):
     from paper_1304_7126_gb300 import workloads as W
     w = W.small_cosmo(n, seed=3, nsrc=4, flux=flux, nx=nx, ny=ny)
-    sim = R.RT.from_workload(w, precision=R.RT_MIXED)
+    sim = R.RT.from_workload(w, precision={"mixed": R.RT_MIXED, "mixed32": R.RT_MIXED32}[prec])
     p = oracle_problem(oracle_mod, w, nthreads=4)
     ref = w.state()
     dt = sim.courant_dt()
@@ -76,8 +78,6 @@ def test_mixed_vs_oracle(oracle_mod, R, flux, n, nx, ny):
         assert st == 0
         flipped |= sim.subcycles().reshape(-1) != sub_o.reshape(-1)
     _check(sim.get_state(), ref, w, flipped)
-    if flux == 0:
-        assert not flipped.any()
 
 
 def test_mixed_transport_only(oracle_mod, R):
@@ -102,14 +102,15 @@ def test_mixed_transport_only(oracle_mod, R):
     assert np.all(np.abs(resid) <= 1e-6 * b[:, 3])
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed32"])
 @pytest.mark.parametrize("flux", [1, 0])
-def test_mixed_vs_fp64_gpu_cosmo64(R, flux):
-    """The mixed path against the FP64 GPU path on a 64^3 box of the
+def test_mixed_vs_fp64_gpu_cosmo64(R, prec, flux):
+    """The mixed paths against the FP64 GPU path on a 64^3 box of the
     cosmological generator, 30 steps."""
     from paper_1304_7126_gb300 import workloads as W
     w = W.cosmo(64, 7, 8, 30, flux=flux)
     a = R.RT.from_workload(w)
-    b = R.RT.from_workload(w, precision=R.RT_MIXED)
+    b = R.RT.from_workload(w, precision={"mixed": R.RT_MIXED, "mixed32": R.RT_MIXED32}[prec])
     dt = a.courant_dt()
     flipped = np.zeros(w.ncells, dtype=bool)
     for _ in range(30):
