@@ -119,4 +119,5 @@ def test_mixed_vs_fp64_gpu_cosmo64(R, prec, flux):
         flipped |= (a.subcycles() != b.subcycles()).reshape(-1)
     _check(b.get_state(), a.get_state(), w, flipped)
     ba, bb = a.budget(), b.budget()
-    assert np.allclose(bb[:, :3], ba[:, :3], rtol=1e-3)
+    # budget columns against the photons emitted
+    assert np.all(np.abs(bb[:, :3] - ba[:, :3]) <= 1e-4 * ba[:, 3:4])
