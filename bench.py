@@ -33,10 +33,12 @@ UNIT = "cell-group updates/s"
 # per clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s, matching the 1.25 TFLOP/s
 # measured by an FMA-chain probe on the same part.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# FP64 flops executed per thermochemistry attempt, from ncu
-# (smsp__sass_thread_inst_executed_op_d{fma x2, add, mul}) divided by the
-# attempts of the same launches; see profiles/thermo_cosmo128.md.
-FP64_FLOP_PER_ATTEMPT = None
+# FP64 flops executed per thermochemistry attempt of the one-thread path:
+# ncu's smsp__sass_thread_inst_executed_op_d{fma x2, add, mul} of
+# thermo_pass1 on step 4 of cosmo128 (4.820e9) over the attempts that launch
+# made (2 104 447); see profiles/thermo_cosmo128.md.
+FP64_FLOP_PER_ATTEMPT = 2290.0
+PASS1_ATTEMPTS = 6
 
 
 def _peaks():
@@ -276,9 +278,9 @@ def main():
         sim.L.rt_get_subcycles(sim.h, sub.data_ptr(), 1)
         attempts += int(sub.sum().item())
         att_max = max(att_max, int(sub.max().item()))
-        q = sub > 6
+        q = sub > PASS1_ATTEMPTS
         queued += int(q.sum().item())
-        queued_att += int(sub[q].sum().item())
+        queued_att += int((sub[q] - PASS1_ATTEMPTS).sum().item())
     prof = sim.profile()
     sim.set_profiling(False)
     phases = {k: {"ms_total": round(v[0], 4), "launches": v[1],
@@ -293,14 +295,19 @@ def main():
                 "traffic": None, "kernel": "transport", "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": alg}
     else:
-        # thermochemistry is FP64-ALU bound: flops per attempt x attempts
-        att_per_launch = attempts / args.steps
+        # thermochemistry is FP64-ALU bound: flops per attempt x attempts the
+        # phase made (first pass: up to PASS1_ATTEMPTS per cell; queue
+        # drains: the rest)
+        if dominant == "thermo_pass1":
+            att_per_launch = (attempts - queued_att) / args.steps
+        else:
+            att_per_launch = queued_att / args.steps
         fpa = FP64_FLOP_PER_ATTEMPT
-        ach = (fpa * att_per_launch / (ms_launch / 1e3) / 1e9) if fpa else None
+        ach = fpa * att_per_launch / (ms_launch / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": (ach / FP64_PEAK_GFLOPS) if ach else None, "traffic": None, "kernel": dominant,
-                "peak_kind": "derived FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "attempts_per_step": att_per_launch}
+                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dominant + " (+ thermo_hard)",
+                "peak_kind": "derived FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz; 1.25 TFLOP/s measured)",
+                "flop_per_attempt": fpa, "attempts_per_launch": att_per_launch}
 
     # ---- end to end: host buffers through the C-ABI, copies in the timed region ----
     e2e = None
