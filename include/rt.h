@@ -172,6 +172,48 @@ int rt_set_profiling(rt_handle *h, int enable);
  * enabled, ms [RT_NPHASES], launches [RT_NPHASES].  Synchronises. */
 int rt_get_profile(rt_handle *h, double *ms, int64_t *launches);
 
+/* ---- Batched boxes ----
+ * Many independent boxes of uneven sizes advanced together: each box runs
+ * exactly the RT step above on its own grid, state, sources and photon
+ * groups; all boxes share the cell width dx_cm, the reduced light speed and
+ * the options, hence one Courant step.  Boxes with the same number of
+ * groups must share the group constants.  Every phase of a step covers all
+ * boxes in one launch per tile shape / group count, and rt_batch_run
+ * replays a step pair as a CUDA graph. */
+typedef struct rt_batch rt_batch;
+
+/* n_boxes grids (all with the same dx_cm), n_groups[b] in 1..RT_MAX_GROUPS,
+ * sigN[b], sigE[b] ([G_b][3] cm^2) and egy[b] ([G_b] erg) host pointers per
+ * box.  Returns RT_EINVAL for bad sizes, mixed dx or differing constants
+ * within a group count. */
+int rt_batch_create(int n_boxes, const rt_grid *grids, const int *n_groups, const rt_options *opt, double c_r,
+                    const double *const *sigN, const double *const *sigE, const double *const *egy,
+                    rt_batch **out);
+void rt_batch_destroy(rt_batch *b);
+int rt_batch_set_stream(rt_batch *b, void *stream);
+/* State of box `box` in the single-box layout of that box (see rt_set_state);
+ * restarts that box's budget. */
+int rt_batch_set_box_state(rt_batch *b, int box, const double *nH, const double *xHII, const double *xHeII,
+                           const double *xHeIII, const double *T, const double *N, const double *F,
+                           int device_ptrs);
+int rt_batch_get_box_state(rt_batch *b, int box, double *nH, double *xHII, double *xHeII, double *xHeIII,
+                           double *T, double *N, double *F, int device_ptrs);
+/* Sources of box `box` (cell indices within the box), as rt_set_sources. */
+int rt_batch_set_box_sources(rt_batch *b, int box, int n, const int32_t *ijk, const double *L);
+int rt_batch_courant_dt(const rt_batch *b, double *dt);
+int rt_batch_step(rt_batch *b, double dt);
+int rt_batch_run(rt_batch *b, double dt, int nsteps);
+/* Budget of box `box`, out [G_b][4] as rt_get_budget.  Synchronises. */
+int rt_batch_get_budget(rt_batch *b, int box, double *out);
+int rt_batch_sync(rt_batch *b);
+const char *rt_batch_last_error(const rt_batch *b);
+/* Times the transport of each distinct box shape with 32x8 and 16x16 tiles
+ * and 4, 8, 16 or 32 planes per CTA (`trials` launches each, on the current
+ * state, which it does not change) and keeps the fastest.  Synchronises. */
+int rt_batch_autotune(rt_batch *b, int trials);
+/* Tiling chosen for a box: shape 0 = 32x8, 1 = 16x16; planes per CTA. */
+int rt_batch_box_tiling(const rt_batch *b, int box, int *shape, int *planes);
+
 /* Allocation-free thermochemistry (no counterpart in the paper): the
  * sub-cycled thermochemistry of one RT step (what rt_step does after the
  * transport) applied in place to caller-owned device arrays, for callers

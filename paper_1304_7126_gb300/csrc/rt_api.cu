@@ -311,6 +311,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     rt_handle *h = new rt_handle();
     h->g.nx = grid->nx; h->g.ny = grid->ny; h->g.nz = grid->nz;
     h->g.nc = nc;
+    h->g.stride = nc;
     h->g.dx = grid->dx_cm;
     for (int i = 0; i < 6; ++i) h->g.bc[i] = grid->bc[i];
     h->G = n_groups;

@@ -34,8 +34,21 @@ struct GroupConsts {
 struct GridDev {
     int nx, ny, nz;
     long long nc;            // cells
+    long long stride;        // distance between consecutive groups / flux components
     double dx;               // cm
     int bc[6];
+};
+
+// Batched boxes: a box of a group-count class, and one CTA's work item.
+struct BatchBox {
+    GridDev g;               // g.stride = cells of the box's class
+    long long cell_off;      // first cell of the box within its class
+    int cls;                 // class index (boxes with the same G)
+    int G;
+};
+struct BatchItem {
+    int box, grp;
+    int x0, y0, z0, z1;
 };
 
 // Parameters of the thermochemistry kernels.
@@ -88,6 +101,13 @@ cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, d
                                  const float *F0, float *N1, float *F1, const float *hll_table,
                                  const Partials &p, cudaStream_t s);
 int transport_blocks_per_group(const GridDev &g);
+// Batched transport over items [item0, item0 + nitems) of one tile shape
+// (0: 32 x 8, 1: 16 x 16); N0/F0/N1/F1 are device arrays of per-class base
+// pointers; partials are indexed by item.
+cudaError_t launch_transport_batch(const BatchItem *items, const BatchBox *boxes, int item0, int nitems,
+                                   int shape, bool fp32, int flux, double cr, double dt, double dx,
+                                   const void *const *N0, const void *const *F0, void *const *N1,
+                                   void *const *F1, const void *tab, double *pin, double *pout, cudaStream_t s);
 void transport_init();   // kernel attributes; called once per handle
 
 // ev (optional, 4 events): recorded around the first pass (0, 1) and

@@ -28,11 +28,7 @@
 namespace rtgb {
 namespace {
 
-constexpr int TBX = 32;
-constexpr int TBY = 8;
-constexpr int TZC = 16;   // planes per CTA
-constexpr int SW = TBX + 2;
-constexpr int SH = TBY + 2;
+constexpr int TZC = 16;   // planes per CTA (single-box launches)
 
 template <typename S>
 struct CellQ {
@@ -183,26 +179,27 @@ __device__ __forceinline__ void load_U(const GridDev &g, const S *__restrict__ N
     long long i = ((long long)z * g.ny + y) * g.nx + x;
     n = __ldg(&N[i]);
     fx = __ldg(&F[i]);
-    fy = __ldg(&F[g.nc + i]);
-    fz = __ldg(&F[2 * g.nc + i]);
+    fy = __ldg(&F[g.stride + i]);
+    fz = __ldg(&F[2 * g.stride + i]);
     if (flip == 0) fx = -fx;
     if (flip == 1) fy = -fy;
     if (flip == 2) fz = -fz;
 }
 
 // Shared-memory plane of closure quantities needed by the x and y faces.
-template <typename S>
+template <typename S, int TBX, int TBY>
 struct PlaneSmem {
+    static constexpr int SW = TBX + 2, SH = TBY + 2;
     S N[SH][SW], Fx[SH][SW], Fy[SH][SW], Fz[SH][SW];
     S Pxx[SH][SW], Pxy[SH][SW], Pxz[SH][SW], Pyy[SH][SW], Pyz[SH][SW];
     S lminx[SH][SW], lmaxx[SH][SW], lminy[SH][SW], lmaxy[SH][SW];
-    S fxs[4][TBY][TBX + 1];     // x faces 0..32 of each row
-    S fys[4][TBY + 1][TBX];     // y faces 0..8 of each column
+    S fxs[4][TBY][TBX + 1];     // x faces 0..TBX of each row
+    S fys[4][TBY + 1][TBX];     // y faces 0..TBY of each column
     double red[2][TBX * TBY / 32];
 };
 
-template <typename S, int FLUX>
-__device__ __forceinline__ void put_plane(PlaneSmem<S> &s, int r, int c, const CellQ<S> &q)
+template <typename S, int FLUX, class SM>
+__device__ __forceinline__ void put_plane(SM &s, int r, int c, const CellQ<S> &q)
 {
     s.N[r][c] = q.N; s.Fx[r][c] = q.Fx; s.Fy[r][c] = q.Fy; s.Fz[r][c] = q.Fz;
     s.Pxx[r][c] = q.Pxx; s.Pxy[r][c] = q.Pxy; s.Pxz[r][c] = q.Pxz; s.Pyy[r][c] = q.Pyy; s.Pyz[r][c] = q.Pyz;
@@ -212,8 +209,8 @@ __device__ __forceinline__ void put_plane(PlaneSmem<S> &s, int r, int c, const C
     }
 }
 
-template <typename S, int FLUX>
-__device__ __forceinline__ void get_plane(const PlaneSmem<S> &s, int r, int c, CellQ<S> &q)
+template <typename S, int FLUX, class SM>
+__device__ __forceinline__ void get_plane(const SM &s, int r, int c, CellQ<S> &q)
 {
     q.N = s.N[r][c]; q.Fx = s.Fx[r][c]; q.Fy = s.Fy[r][c]; q.Fz = s.Fz[r][c];
     q.Pxx = s.Pxx[r][c]; q.Pxy = s.Pxy[r][c]; q.Pxz = s.Pxz[r][c]; q.Pyy = s.Pyy[r][c]; q.Pyz = s.Pyz[r][c];
@@ -225,29 +222,16 @@ __device__ __forceinline__ void get_plane(const PlaneSmem<S> &s, int r, int c, C
     }
 }
 
-template <typename S, int FLUX>
-__global__ void __launch_bounds__(TBX * TBY)
-transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
-                 const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
-                 const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
-                 int tiles_x, int tiles_y, int nblk)
+// One tile of one group: the (x0.., y0..) TBX x TBY column block of planes
+// z0 <= z < z1 of a box g, state at N0/F0 (group base pointers, component
+// stride g.stride), result to N1/F1.  Returns this thread's share of the
+// photons left in the box (sum N) and of the net boundary outflow (flux).
+template <typename S, int FLUX, int TBX, int TBY>
+__device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const GridDev &g, S c, S dtdx,
+                                               const S *__restrict__ N0, const S *__restrict__ F0,
+                                               S *__restrict__ N1, S *__restrict__ F1, const S *__restrict__ tab,
+                                               int x0, int y0, int z0, int z1, double &inbox, double &outflow)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PlaneSmem<S> &s = *reinterpret_cast<PlaneSmem<S> *>(smem_raw);
-
-    const int grp = blockIdx.y;
-    const int tile = blockIdx.x;
-    const int tile_x = tile % tiles_x;
-    const int tile_y = (tile / tiles_x) % tiles_y;
-    const int zc = tile / (tiles_x * tiles_y);
-    const int x0 = tile_x * TBX, y0 = tile_y * TBY;
-    const int z0 = zc * TZC;
-    const int z1 = min(z0 + TZC, g.nz);
-    const S *N0 = N0all + (long long)grp * g.nc;
-    const S *F0 = F0all + 3LL * grp * g.nc;
-    S *N1 = N1all + (long long)grp * g.nc;
-    S *F1 = F1all + 3LL * grp * g.nc;
-
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TBX + tx;
     const int x = x0 + tx, y = y0 + ty;
@@ -276,7 +260,8 @@ transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N
 
     CellQ<S> cur, nxt;
     S flo[4] = {0, 0, 0, 0}, fhi[4] = {0, 0, 0, 0};
-    double inbox = 0.0, outflow = 0.0;
+    inbox = 0.0;
+    outflow = 0.0;
     if (active) {
         S n, fx, fy, fz;
         load_U<S>(g, N0, F0, x, y, z0 - 1, n, fx, fy, fz);
@@ -404,8 +389,8 @@ transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N
             long long i = ((long long)z * g.ny + y) * g.nx + x;
             N1[i] = nw[0];
             F1[i] = nw[1];
-            F1[g.nc + i] = nw[2];
-            F1[2 * g.nc + i] = nw[3];
+            F1[g.stride + i] = nw[2];
+            F1[2 * g.stride + i] = nw[3];
             inbox += (double)nw[0];
             if (z == 0 && bc_z_lo) outflow -= (double)flo[0];
             if (z == g.nz - 1 && bc_z_hi) outflow += (double)fhi[0];
@@ -416,20 +401,82 @@ transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N
         __syncthreads();
     }
 
-    // fixed-order block reduction of the two budget sums
+}
+
+// fixed-order block reduction of the two budget sums (thread 0 gets them)
+template <int NT>
+__device__ __forceinline__ void block_reduce2(double *red, double &a, double &b)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        inbox += __shfl_down_sync(0xffffffffu, inbox, o);
-        outflow += __shfl_down_sync(0xffffffffu, outflow, o);
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
     }
     const int warp = tid >> 5, lane = tid & 31;
-    if (lane == 0) { s.red[0][warp] = inbox; s.red[1][warp] = outflow; }
+    if (lane == 0) { red[warp] = a; red[NT / 32 + warp] = b; }
     __syncthreads();
     if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < TBX * TBY / 32; ++w) { a += s.red[0][w]; b += s.red[1][w]; }
-        part_inbox[(long long)grp * nblk + tile] = a;
-        part_out[(long long)grp * nblk + tile] = b * area_dt;
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < NT / 32; ++w) { x += red[w]; y += red[NT / 32 + w]; }
+        a = x;
+        b = y;
+    }
+}
+
+template <typename S, int FLUX>
+__global__ void __launch_bounds__(256)
+transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
+                 const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
+                 const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
+                 int tiles_x, int tiles_y, int nblk)
+{
+    constexpr int TBX = 32, TBY = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PlaneSmem<S, TBX, TBY> &s = *reinterpret_cast<PlaneSmem<S, TBX, TBY> *>(smem_raw);
+    const int grp = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int tile_x = tile % tiles_x;
+    const int tile_y = (tile / tiles_x) % tiles_y;
+    const int zc = tile / (tiles_x * tiles_y);
+    const int z0 = zc * TZC;
+    double inbox, outflow;
+    transport_tile<S, FLUX, TBX, TBY>(s, g, c, dtdx, N0all + (long long)grp * g.stride,
+                                      F0all + 3LL * grp * g.stride, N1all + (long long)grp * g.stride,
+                                      F1all + 3LL * grp * g.stride, tab, tile_x * TBX, tile_y * TBY, z0,
+                                      min(z0 + TZC, g.nz), inbox, outflow);
+    block_reduce2<TBX * TBY>(&s.red[0][0], inbox, outflow);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        part_inbox[(long long)grp * nblk + tile] = inbox;
+        part_out[(long long)grp * nblk + tile] = outflow * area_dt;
+    }
+}
+
+// Batched boxes: CTA i works on item i (box, group, tile, z range) of a
+// work list; every box is described by its GridDev (component stride = the
+// stride of its group class) and the offset of its first cell in the class.
+template <typename S, int FLUX, int TBX, int TBY>
+__global__ void __launch_bounds__(TBX * TBY)
+transport_batch_kernel(const BatchItem *__restrict__ items, const BatchBox *__restrict__ boxes, S c, S dtdx,
+                       double area_dt, const S *const *__restrict__ N0cls, const S *const *__restrict__ F0cls,
+                       S *const *__restrict__ N1cls, S *const *__restrict__ F1cls, const S *__restrict__ tab,
+                       double *__restrict__ part_inbox, double *__restrict__ part_out, int item0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PlaneSmem<S, TBX, TBY> &s = *reinterpret_cast<PlaneSmem<S, TBX, TBY> *>(smem_raw);
+    const int it = item0 + blockIdx.x;
+    const BatchItem w = items[it];
+    const BatchBox b = boxes[w.box];
+    const long long base = (long long)w.grp * b.g.stride + b.cell_off;
+    const long long fbase = 3LL * w.grp * b.g.stride + b.cell_off;
+    double inbox, outflow;
+    transport_tile<S, FLUX, TBX, TBY>(s, b.g, c, dtdx, N0cls[b.cls] + base, F0cls[b.cls] + fbase,
+                                      N1cls[b.cls] + base, F1cls[b.cls] + fbase, tab, w.x0, w.y0, w.z0, w.z1,
+                                      inbox, outflow);
+    block_reduce2<TBX * TBY>(&s.red[0][0], inbox, outflow);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        part_inbox[it] = inbox;
+        part_out[it] = outflow * area_dt;
     }
 }
 
@@ -437,31 +484,43 @@ transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N
 
 int transport_blocks_per_group(const GridDev &g)
 {
-    int tx = (g.nx + TBX - 1) / TBX;
-    int ty = (g.ny + TBY - 1) / TBY;
+    int tx = (g.nx + 31) / 32;
+    int ty = (g.ny + 7) / 8;
     int tz = (g.nz + TZC - 1) / TZC;
     return tx * ty * tz;
 }
 
+template <typename S, int TBX, int TBY>
+static void set_smem_attr_batch()
+{
+    int sz = (int)sizeof(PlaneSmem<S, TBX, TBY>);
+    cudaFuncSetAttribute(transport_batch_kernel<S, RT_HLL, TBX, TBY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+    cudaFuncSetAttribute(transport_batch_kernel<S, RT_GLF, TBX, TBY>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+}
+
 void transport_init()
 {
-    int s8 = (int)sizeof(PlaneSmem<double>), s4 = (int)sizeof(PlaneSmem<float>);
+    int s8 = (int)sizeof(PlaneSmem<double, 32, 8>), s4 = (int)sizeof(PlaneSmem<float, 32, 8>);
     cudaFuncSetAttribute(transport_kernel<double, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
     cudaFuncSetAttribute(transport_kernel<double, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
     cudaFuncSetAttribute(transport_kernel<float, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
     cudaFuncSetAttribute(transport_kernel<float, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+    set_smem_attr_batch<double, 32, 8>();
+    set_smem_attr_batch<double, 16, 16>();
+    set_smem_attr_batch<float, 32, 8>();
+    set_smem_attr_batch<float, 16, 16>();
 }
 
 template <typename S>
 static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double dt, const S *N0, const S *F0,
                             S *N1, S *F1, const S *tab, const Partials &p, cudaStream_t st)
 {
-    int tiles_x = (g.nx + TBX - 1) / TBX;
-    int tiles_y = (g.ny + TBY - 1) / TBY;
+    int tiles_x = (g.nx + 31) / 32;
+    int tiles_y = (g.ny + 7) / 8;
     int nblk = transport_blocks_per_group(g);
     dim3 grid(nblk, G);
-    dim3 block(TBX, TBY);
-    size_t smem = sizeof(PlaneSmem<S>);
+    dim3 block(32, 8);
+    size_t smem = sizeof(PlaneSmem<S, 32, 8>);
     S dtdx = (S)(dt / g.dx);
     double area_dt = g.dx * g.dx * dt;
     if (flux == RT_HLL)
@@ -485,6 +544,51 @@ cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, d
                                  const Partials &p, cudaStream_t st)
 {
     return launch_t<float>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, p, st);
+}
+
+template <typename S>
+static cudaError_t launch_b(const BatchItem *items, const BatchBox *boxes, int item0, int nitems, int shape,
+                            int flux, double cr, double dt, double dx, const void *const *N0, const void *const *F0,
+                            void *const *N1, void *const *F1, const S *tab, double *pin, double *pout,
+                            cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    S dtdx = (S)(dt / dx);
+    double area_dt = dx * dx * dt;
+    auto n0 = reinterpret_cast<const S *const *>(N0);
+    auto f0 = reinterpret_cast<const S *const *>(F0);
+    auto n1 = reinterpret_cast<S *const *>(N1);
+    auto f1 = reinterpret_cast<S *const *>(F1);
+    if (shape == 0) {
+        size_t smem = sizeof(PlaneSmem<S, 32, 8>);
+        if (flux == RT_HLL)
+            transport_batch_kernel<S, RT_HLL, 32, 8><<<nitems, dim3(32, 8), smem, st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, tab, pin, pout, item0);
+        else
+            transport_batch_kernel<S, RT_GLF, 32, 8><<<nitems, dim3(32, 8), smem, st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, tab, pin, pout, item0);
+    } else {
+        size_t smem = sizeof(PlaneSmem<S, 16, 16>);
+        if (flux == RT_HLL)
+            transport_batch_kernel<S, RT_HLL, 16, 16><<<nitems, dim3(16, 16), smem, st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, tab, pin, pout, item0);
+        else
+            transport_batch_kernel<S, RT_GLF, 16, 16><<<nitems, dim3(16, 16), smem, st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, tab, pin, pout, item0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transport_batch(const BatchItem *items, const BatchBox *boxes, int item0, int nitems,
+                                   int shape, bool fp32, int flux, double cr, double dt, double dx,
+                                   const void *const *N0, const void *const *F0, void *const *N1,
+                                   void *const *F1, const void *tab, double *pin, double *pout, cudaStream_t st)
+{
+    if (fp32)
+        return launch_b<float>(items, boxes, item0, nitems, shape, flux, cr, dt, dx, N0, F0, N1, F1,
+                               static_cast<const float *>(tab), pin, pout, st);
+    return launch_b<double>(items, boxes, item0, nitems, shape, flux, cr, dt, dx, N0, F0, N1, F1,
+                            static_cast<const double *>(tab), pin, pout, st);
 }
 
 }  // namespace rtgb

@@ -79,6 +79,28 @@ def load(build: bool = True):
     L.rt_thermo_step_noalloc.argtypes = [C.c_longlong, C.c_int, C.POINTER(rt_options), C.c_double, dp, dp,
                                          dp, C.c_double, dp, dp, dp, dp, dp, dp, dp, ip, vp]
     L.rt_thermo_step_noalloc.restype = C.c_int
+    L.rt_batch_create.argtypes = [C.c_int, C.POINTER(rt_grid), C.POINTER(C.c_int), C.POINTER(rt_options),
+                                  C.c_double, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                  C.POINTER(vp)]
+    L.rt_batch_destroy.argtypes = [vp]
+    L.rt_batch_destroy.restype = None
+    L.rt_batch_set_stream.argtypes = [vp, vp]
+    L.rt_batch_set_box_state.argtypes = [vp, C.c_int, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+    L.rt_batch_get_box_state.argtypes = [vp, C.c_int, dp, dp, dp, dp, dp, dp, dp, C.c_int]
+    L.rt_batch_set_box_sources.argtypes = [vp, C.c_int, C.c_int, ip, dp]
+    L.rt_batch_courant_dt.argtypes = [vp, C.POINTER(C.c_double)]
+    L.rt_batch_step.argtypes = [vp, C.c_double]
+    L.rt_batch_run.argtypes = [vp, C.c_double, C.c_int]
+    L.rt_batch_get_budget.argtypes = [vp, C.c_int, dp]
+    L.rt_batch_sync.argtypes = [vp]
+    L.rt_batch_last_error.argtypes = [vp]
+    L.rt_batch_last_error.restype = C.c_char_p
+    L.rt_batch_autotune.argtypes = [vp, C.c_int]
+    L.rt_batch_box_tiling.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    for name in ("rt_batch_create", "rt_batch_set_stream", "rt_batch_set_box_state", "rt_batch_get_box_state",
+                 "rt_batch_set_box_sources", "rt_batch_courant_dt", "rt_batch_step", "rt_batch_run",
+                 "rt_batch_get_budget", "rt_batch_sync", "rt_batch_autotune", "rt_batch_box_tiling"):
+        getattr(L, name).restype = C.c_int
     L.rt_set_profiling.argtypes = [vp, C.c_int]
     L.rt_get_profile.argtypes = [vp, dp, dp]
     for name in ("rt_create", "rt_set_stream", "rt_set_state", "rt_get_state", "rt_set_sources",
@@ -249,4 +271,116 @@ class RT:
         r = cls(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, bc=w.bc, **o)
         r.set_state(w.state())
         r.set_sources(w.src_ijk, w.src_L)
+        return r
+
+
+class RTBatch:
+    """A batch of independent boxes (rt_batch_* C-ABI): one entry per box in
+    `boxes`, each a workloads.Workload sharing dx, c_r and options."""
+
+    def __init__(self, boxes, **opts):
+        L = load()
+        self.L = L
+        w0 = boxes[0]
+        o = dict(X=w0.X, isothermal=int(w0.isothermal), otsa=int(w0.otsa), flux=w0.flux, cfl=w0.cfl)
+        o.update(opts)
+        opt = default_options(**o)
+        n = len(boxes)
+        grids = (rt_grid * n)()
+        ng = (C.c_int * n)()
+        self._keep = []
+        sn, se, eg = (C.c_void_p * n)(), (C.c_void_p * n)(), (C.c_void_p * n)()
+        for i, w in enumerate(boxes):
+            nz, ny, nx = w.shape
+            grids[i].nx, grids[i].ny, grids[i].nz = nx, ny, nz
+            grids[i].dx_cm = float(w.dx)
+            for k in range(6):
+                grids[i].bc[k] = int(w.bc[k])
+            ng[i] = w.G
+            a = np.ascontiguousarray(w.sigN, dtype=np.float64).reshape(w.G, 3)
+            b = np.ascontiguousarray(w.sigE, dtype=np.float64).reshape(w.G, 3)
+            e = np.ascontiguousarray(w.egy, dtype=np.float64).reshape(w.G)
+            self._keep += [a, b, e]
+            sn[i], se[i], eg[i] = _ptr(a), _ptr(b), _ptr(e)
+        h = C.c_void_p()
+        rc = L.rt_batch_create(n, grids, ng, C.byref(opt), float(w0.cr), sn, se, eg, C.byref(h))
+        if rc:
+            raise RTError(rc, "rt_batch_create")
+        self.h = h
+        self.boxes = boxes
+
+    def _check(self, rc, what):
+        if rc:
+            raise RTError(rc, "%s: %s" % (what, self.L.rt_batch_last_error(self.h).decode()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        self._check(self.L.rt_batch_set_stream(self.h, stream_ptr), "rt_batch_set_stream")
+
+    def set_box_state(self, i, s):
+        keys = ("nH", "xHII", "xHeII", "xHeIII", "T", "N", "F")
+        dev = _is_dev(s["N"])
+        self._check(self.L.rt_batch_set_box_state(self.h, i, *[_ptr(s[k]) for k in keys], int(dev)),
+                    "rt_batch_set_box_state")
+
+    def get_box_state(self, i):
+        w = self.boxes[i]
+        nc, G = w.ncells, w.G
+        out = {"nH": np.empty(nc), "xHII": np.empty(nc), "xHeII": np.empty(nc), "xHeIII": np.empty(nc),
+               "T": np.empty(nc), "N": np.empty(G * nc), "F": np.empty(3 * G * nc)}
+        keys = ("nH", "xHII", "xHeII", "xHeIII", "T", "N", "F")
+        self._check(self.L.rt_batch_get_box_state(self.h, i, *[_ptr(out[k]) for k in keys], 0),
+                    "rt_batch_get_box_state")
+        return out
+
+    def set_box_sources(self, i, ijk, L):
+        w = self.boxes[i]
+        a = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+        l = np.ascontiguousarray(L, dtype=np.float64).reshape(a.shape[0], w.G)
+        self._check(self.L.rt_batch_set_box_sources(self.h, i, a.shape[0], _ptr(a), _ptr(l)),
+                    "rt_batch_set_box_sources")
+
+    def courant_dt(self):
+        d = C.c_double()
+        self._check(self.L.rt_batch_courant_dt(self.h, C.byref(d)), "rt_batch_courant_dt")
+        return d.value
+
+    def step(self, dt=0.0):
+        self._check(self.L.rt_batch_step(self.h, float(dt)), "rt_batch_step")
+
+    def run(self, dt, nsteps):
+        self._check(self.L.rt_batch_run(self.h, float(dt), int(nsteps)), "rt_batch_run")
+
+    def budget(self, i):
+        b = np.zeros((self.boxes[i].G, 4))
+        self._check(self.L.rt_batch_get_budget(self.h, i, _ptr(b)), "rt_batch_get_budget")
+        return b
+
+    def sync(self):
+        self._check(self.L.rt_batch_sync(self.h), "rt_batch_sync")
+
+    def autotune(self, trials=2):
+        self._check(self.L.rt_batch_autotune(self.h, int(trials)), "rt_batch_autotune")
+
+    def tiling(self, i):
+        a, b = C.c_int(), C.c_int()
+        self._check(self.L.rt_batch_box_tiling(self.h, i, C.byref(a), C.byref(b)), "rt_batch_box_tiling")
+        return a.value, b.value
+
+    @classmethod
+    def from_workloads(cls, boxes, **opts):
+        r = cls(boxes, **opts)
+        for i, w in enumerate(boxes):
+            r.set_box_state(i, w.state())
+            r.set_box_sources(i, w.src_ijk, w.src_L)
         return r

@@ -59,3 +59,7 @@ def test_workload_literals_match_oracle():
     assert np.array_equal(np.array(W.BB3_PHOTON_FRACTION), np.array(t["photon_fraction"]))
     a = groups.group_attributes(groups.THREE_BANDS, 1e5)
     assert np.allclose(a["sigN"], t["sigN"], rtol=1e-12, atol=0)
+    o = GC["one_band"]
+    assert np.array_equal(np.array(W.BB1_SIGN), np.array(o["sigN"]))
+    assert np.array_equal(np.array(W.BB1_SIGE), np.array(o["sigE"]))
+    assert np.array_equal(np.array(W.BB1_EGY_EV), np.array(o["egy_eV"]))
