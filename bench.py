@@ -207,7 +207,9 @@ def main():
     ap.add_argument("--workload", default="cosmo128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip timing the RT_MIXED variant")
+    ap.add_argument("--no-mixed", action="store_true", help="skip timing the RT_MIXED variants")
+    ap.add_argument("--no-batched", action="store_true", help="skip timing the batched-boxes variant")
+    ap.add_argument("--batched-boxes", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -364,6 +366,36 @@ def main():
             "transport_roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm_peak, "unit": "GB/s",
                                    "frac": ach32 / hbm_peak, "algorithmic_bytes_per_launch": alg32}}
         simm.close()
+
+    # ---- batched uneven boxes (512 boxes of 16..64 cells a side, 1 or 3
+    # groups, FP32 transport + FP64 thermochemistry), one graph per step pair ----
+    if not args.no_batched:
+        from paper_1304_7126_gb300 import workloads as W
+        boxes = W.batched(args.batched_boxes)
+        kb = min(args.steps, 100)
+        bt = R.RTBatch.from_workloads(boxes, precision=R.RT_MIXED)
+        bt.set_stream(stream.cuda_stream)
+        dtb = bt.courant_dt()
+        bt.autotune(1)
+        bt.run(dtb, max(args.warmup, 3))
+        bt.sync()
+        for i, wb in enumerate(boxes):
+            bt.set_box_state(i, wb.state())
+        bt.sync()
+        barrier()
+        ev0.record(stream)
+        bt.run(dtb, kb)
+        ev1.record(stream)
+        ev1.synchronize()
+        bt.sync()
+        tb = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        cgb = sum(wb.ncells * wb.G for wb in boxes)
+        variants["batched%d" % len(boxes)] = {
+            "value": cgb * kb * ws / tb, "ms_per_step": 1e3 * tb / kb, "steps": kb, "cell_groups": cgb,
+            "cells": sum(wb.ncells for wb in boxes), "precision": "mixed (FP32 transport, FP64 thermochemistry)",
+            "workload": "%d boxes, side in {16,24,32,48,64}, 1 or 3 groups, HLL, c_r=c/100" % len(boxes)}
+        bt.close()
+        del boxes
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

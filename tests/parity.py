@@ -1,5 +1,8 @@
 """Helpers shared by the GPU parity tests: run the oracle and the CUDA
-library on the same seeded inputs and compare field by field."""
+library on the same seeded inputs and compare field by field.  Flux
+components are measured against their local scale c_r N (flux_err): a
+component can vanish while |F| does not, so a per-component relative error
+would be meaningless there."""
 import numpy as np
 
 FIELDS = ("N", "F", "xHII", "xHeII", "xHeIII", "T")

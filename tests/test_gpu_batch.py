@@ -59,7 +59,7 @@ def test_batch_box_vs_oracle(oracle_mod, R):
         for _ in range(4):
             st, _, _, _ = p.step(ref, dt, w.src_ijk, w.src_L)
             assert st == 0
-        e = compare(bt.get_box_state(i), ref)
+        e = compare(bt.get_box_state(i), ref, cr=w.cr, G=w.G)
         assert max(e.values()) < 1e-10, (i, e)
     b = bt.budget(0)
     resid = b[:, 3] - b[:, 0] - b[:, 1] - b[:, 2]

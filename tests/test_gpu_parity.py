@@ -94,7 +94,7 @@ def test_full_step_parity_cosmo(oracle_mod, R, flux, n, nx, ny):
         assert np.all(mg[differ] < 1e-9), (step, int(differ.sum()))
         got = sim.get_state()
         if not differ.any():
-            e = compare(got, ref)
+            e = compare(got, ref, cr=w.cr, G=w.G)
             assert max(e.values()) < 1e-10, (step, e)
     assert sub_o.max() > 1
 
@@ -114,7 +114,7 @@ def test_stromgren_parity_and_front(oracle_mod, R):
         st, _, sub_o, mg = p.step(ref, dt, w.src_ijk, w.src_L)
     got = sim.get_state()
     assert np.array_equal(sim.subcycles(), sub_o)
-    e = compare(got, ref, ("N", "F", "xHII"))
+    e = compare(got, ref, ("N", "F", "xHII"), cr=w.cr, G=w.G)
     assert max(e.values()) < 1e-10, e
     r, _ = oracle_mod.rates(1e4)
     rS = A.stromgren_radius(w.extra["L_full"], 1e-3, r["alpha_HII"])
