@@ -154,6 +154,40 @@ int rt_sync(rt_handle *h);
 /* One-line description of the last error on this handle (never NULL). */
 const char *rt_last_error(const rt_handle *h);
 
+/* ---- adjoint (vector-Jacobian products of rt_step) ----
+ *
+ * The adjoint of the step U_k -> U_{k+1} of rt_step (injection, transport,
+ * thermochemistry, in the paper's order, Sec. 3): given lambda = dJ/dU_{k+1}
+ * for a scalar J, it returns lambda = dJ/dU_k and accumulates dJ/dn_H and
+ * dJ/dL.  The thermochemistry is differentiated along the sub-cycle
+ * schedule that the forward step takes (the schedule is piecewise constant
+ * in the inputs, so this is the derivative wherever it exists), the
+ * transport is the transposed GLF stencil.  Needs precision RT_FP64 and
+ * flux RT_GLF (else RT_EINVAL) and a state set by rt_set_state.
+ *
+ * All arrays are CUDA device pointers on the handle's device, used on the
+ * handle's stream, in the state layouts above:
+ *   lam_xHII, lam_xHeII, lam_xHeIII, lam_T  [cells]        in: dJ/dU_{k+1}, out: dJ/dU_k
+ *   lam_N [G][cells], lam_F [G][3][cells]                  in/out likewise
+ *   g_nH  [cells]                                          += dJ/dn_H of the step
+ *   g_L   [n][G]  (n, order: the last rt_set_sources)      += dJ/dL (s photons/s)^-1
+ * dt <= 0 means the Courant dt.  The handle's state is left at U_k; the
+ * budget and sub-cycle counts afterwards are those of recomputed steps.
+ * mismatches: NULL, or a host counter to which the number of cells whose
+ * recomputed attempt count differs from the forward kernels' is added (this
+ * re-runs the forward thermochemistry on a copy and synchronises; nonzero
+ * means the adjoint differentiated another schedule than the forward run). */
+int rt_step_vjp(rt_handle *h, double dt, double *lam_xHII, double *lam_xHeII, double *lam_xHeIII, double *lam_T,
+                double *lam_N, double *lam_F, double *g_nH, double *g_L, long long *mismatches);
+
+/* nsteps steps of rt_step_vjp from the handle's state U_0: recomputes and
+ * keeps the forward trajectory U_0..U_{nsteps-1} on the device (nsteps x
+ * (4 + 4G) x cells doubles, allocated for the call), then sweeps it back;
+ * lambda goes in as dJ/dU_nsteps and comes out as dJ/dU_0.  The handle ends
+ * at U_0.  Synchronises. */
+int rt_run_vjp(rt_handle *h, double dt, int nsteps, double *lam_xHII, double *lam_xHeII, double *lam_xHeIII,
+               double *lam_T, double *lam_N, double *lam_F, double *g_nH, double *g_L, long long *mismatches);
+
 /* Host-side HLL wave-speed table used by RT_HLL: extreme eigenvalues of the
  * M1 flux Jacobian (Sec. 3.2) in units of c, out [nf][nmu][2] =
  * (lambda_min, lambda_max) at f = k/(nf-1), mu = -1 + 2j/(nmu-1).

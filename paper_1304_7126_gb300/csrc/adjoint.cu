@@ -1,0 +1,363 @@
+// Adjoint (vector-Jacobian product) of one RT step, FP64, GLF transport.
+//
+// The forward step is U_k -> inject -> U_a -> transport -> U_b -> thermo ->
+// U_{k+1} (paper Sec. 3: Eq. (injnum), the Godunov update with the GLF
+// flux Eq. (glf), the App. A thermochemistry).  Given lambda = dJ/dU_{k+1}
+// the reverse sweep is
+//   thermo_vjp     lambda_b = (dthermo/dU_b)^T lambda, and dJ/dn_H += ...;
+//   transport_vjp  lambda_a = (dtransport/dU_a)^T lambda_b (photons; the
+//                  gas passes through unchanged);
+//   inject_vjp     dJ/dL_{s,i} += lambda_a(N_i at the source cell) dt / V,
+//                  lambda_k = lambda_a.
+//
+// thermo_vjp differentiates the sub-cycled thermochemistry of one cell in
+// forward mode: a team of lanes per cell, lane j seeded with the unit
+// tangent of input j (N_0..N_{G-1}, x_HII, x_HeII, x_HeIII, T, n_H), runs
+// the thermo_step code of the forward kernels instantiated on dual numbers.
+// Its values are the bits of the forward path, so it takes the same
+// sub-cycle decisions; the derivative is that of the step sequence the
+// forward run took (the schedule is piecewise constant in the inputs).
+// Lane j ends with column j of the cell's Jacobian and dots it with lambda.
+// The flux output is F' = F prod_s 1/(1 + h_s D_i): its derivative along
+// the other inputs enters through w_i = F_i . lambda_{F_i}.
+//
+// transport_vjp is the transpose of the GLF stencil: with r = dt/dx and
+// Phi_d the physical flux along d, every face (L, R) gives U'_L -= r Fhat,
+// U'_R += r Fhat with Fhat = (Phi(U_L) + Phi(U_R))/2 - c (U_R - U_L)/2, so
+// its co-flux mu = r (lambda'_R - lambda'_L) adds (J_L^T + c) mu/2 to
+// lambda_L and (J_R^T - c) mu/2 to lambda_R, J = dPhi_d/dU from the M1
+// closure (Sec. 2, Eqs. (edd2), (eddTens)).  Boundary ghosts are B U_c
+// (outflow: B = I; reflect: the normal flux negated) and carry no lambda'.
+// The realisability clamp of the forward update acts only at rounding level
+// for CFL <= 1 and is taken as the identity.
+#include <cuda_runtime.h>
+
+#include "rt_internal.h"
+#include "thermo_step.cuh"
+
+namespace rtgb {
+namespace {
+
+using namespace thermo_detail;
+
+constexpr double kClosureFloorN = 1e-30;   // as in the forward closure
+
+// ---------------------------------------------------------------------------
+// thermochemistry
+
+template <int G, int GS>
+__global__ void __launch_bounds__(128)
+thermo_vjp_kernel(ThermoParams p, const double *__restrict__ nH, const double *__restrict__ xHII,
+                  const double *__restrict__ xHeII, const double *__restrict__ xHeIII,
+                  const double *__restrict__ T, const double *__restrict__ N, const double *__restrict__ F,
+                  double *lx, double *ly2, double *ly3, double *lT, const double *__restrict__ lN_in,
+                  const double *__restrict__ lF_in, double *__restrict__ lN_out, double *__restrict__ lF_out,
+                  double *g_nH, int32_t *sub_out, unsigned *status)
+{
+    constexpr int NT = G + 5;   // N_i, x_HII, x_HeII, x_HeIII, T, n_H
+    static_assert(NT <= GS && 32 % GS == 0, "team size");
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long c = tid / GS;
+    const int j = (int)(tid % GS);
+    const bool valid = c < p.nc;
+    const long long nc = p.nc;
+
+    // every lane reads lambda' before any lane of the warp overwrites it
+    double lxv = 0.0, ly2v = 0.0, ly3v = 0.0, lTv = 0.0;
+    double lNv[G], w[G];
+    if (valid) {
+        lxv = lx[c];
+        ly2v = ly2[c];
+        ly3v = ly3[c];
+        lTv = lT[c];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            lNv[i] = lN_in[(long long)i * nc + c];
+            const long long b = 3LL * i * nc + c;
+            w[i] = F[b] * lF_in[b] + F[b + nc] * lF_in[b + nc] + F[b + 2 * nc] * lF_in[b + 2 * nc];
+        }
+    }
+    __syncwarp();
+    if (!valid || j >= NT) return;
+
+    CellState<G, Dual> st;
+    st.x = Dual(xHII[c], j == G ? 1.0 : 0.0);
+    st.y2 = Dual(xHeII[c], j == G + 1 ? 1.0 : 0.0);
+    st.y3 = Dual(xHeIII[c], j == G + 2 ? 1.0 : 0.0);
+    st.T = Dual(T[c], j == G + 3 ? 1.0 : 0.0);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        st.N[i] = Dual(N[(long long)i * nc + c], j == i ? 1.0 : 0.0);
+        st.Fs[i] = Dual(1.0);
+    }
+    const Dual n(nH[c], j == G + 4 ? 1.0 : 0.0);
+    IsoRates<Dual> iso;
+    CoolCache<Dual> cc;
+    cc.valid = false;
+    if (p.isothermal) {
+        TranscT<Dual> t;
+        transc_dual(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
+        h_rates_from(t, p.case_b, iso.h);
+        if (p.helium) he_rates_from(t, p.case_b, iso.he);
+    }
+    double t_left = p.dt, dt_tc = p.dt;
+    int att = 0;
+    bool done = false;
+    while (!done) {
+        done = subcycle_once<G, false, false, Dual>(p, n, st, t_left, dt_tc, att, iso, cc);
+        if (!done && att >= p.max_sub) {
+            atomicOr(status, kStatusSubcycle);
+            done = true;
+        }
+    }
+
+    double g = lxv * st.x.d + ly2v * st.y2.d + ly3v * st.y3.d + lTv * st.T.d;
+#pragma unroll
+    for (int i = 0; i < G; ++i) g += lNv[i] * st.N[i].d + w[i] * st.Fs[i].d;
+    if (!isfinite(g)) atomicOr(status, kStatusNonFinite);
+
+    if (j < G) {
+        lN_out[(long long)j * nc + c] = g;
+    } else if (j == G) {
+        lx[c] = g;
+    } else if (j == G + 1) {
+        ly2[c] = g;
+    } else if (j == G + 2) {
+        ly3[c] = g;
+    } else if (j == G + 3) {
+        lT[c] = g;
+    } else {
+        g_nH[c] += g;
+    }
+    if (j == 0) {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const long long b = 3LL * i * nc + c;
+            const double s = st.Fs[i].v;
+            lF_out[b] = s * lF_in[b];
+            lF_out[b + nc] = s * lF_in[b + nc];
+            lF_out[b + 2 * nc] = s * lF_in[b + 2 * nc];
+        }
+        if (sub_out) sub_out[c] = att;
+    }
+}
+
+template <int G>
+cudaError_t launch_thermo_vjp_g(const ThermoParams &tp, const double *nH, const double *xHII, const double *xHeII,
+                                const double *xHeIII, const double *T, const double *N, const double *F, double *lx,
+                                double *ly2, double *ly3, double *lT, const double *lN_in, const double *lF_in,
+                                double *lN_out, double *lF_out, double *g_nH, int32_t *sub_out, unsigned *status,
+                                cudaStream_t s)
+{
+    constexpr int GS = (G + 5 <= 8) ? 8 : 16;
+    const long long threads = tp.nc * GS;
+    const long long blocks = (threads + 127) / 128;
+    thermo_vjp_kernel<G, GS><<<(unsigned)blocks, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, lx, ly2, ly3, lT,
+                                                               lN_in, lF_in, lN_out, lF_out, g_nH, sub_out, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// transport
+
+// v^T dPhi_d/dU at U = (N, F): the gradient of s(U) = v_N F_d + v_F . P e_d
+// with P = c^2 N (a I + b n n^T), a = (1 - chi)/2, b = (3 chi - 1)/2,
+// f = |F|/(c N), n = F/|F|.  With f' = df/dN = -f/N, df/dF = n/(c N),
+// dn/dF = (I - n n^T)/|F|:
+//   ds/dN = c^2 (a v_d + b (v.n) n_d) - c^2 f (a' v_d + b' (v.n) n_d)
+//   ds/dF = v_N e_d + c (a' v_d + b' (v.n) n_d) n
+//           + (c^2 N b / |F|) (n_d (v - (v.n) n) + (v.n)(e_d - n_d n))
+// (v is the flux part of v here).  f is clamped to 1 in the closure, so
+// where the clamp acts the terms through df vanish; below the N floor or at
+// F = 0 the closure is isotropic (f = 0, a = 1/3, b = 0).
+__device__ __forceinline__ void phi_vjp(double N, const double F[3], int d, double c, const double v[4],
+                                        double out[4])
+{
+    const double F2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    double f = 0.0, n[3] = {0.0, 0.0, 0.0}, mag = 0.0;
+    bool clamped = false, dir = false;
+    if (N > kClosureFloorN && F2 > 0.0) {
+        mag = sqrt(F2);
+        const double fr = mag / (c * N);
+        clamped = fr > 1.0;
+        f = clamped ? 1.0 : fr;
+        n[0] = F[0] / mag; n[1] = F[1] / mag; n[2] = F[2] / mag;
+        dir = true;
+    }
+    const double f2 = f * f;
+    const double q = sqrt(4.0 - 3.0 * f2);
+    const double den = 5.0 + 2.0 * q;
+    const double chi = (3.0 + 4.0 * f2) / den;
+    const double dchi = (8.0 * f * den + 6.0 * f * (3.0 + 4.0 * f2) / q) / (den * den);
+    const double a = 0.5 * (1.0 - chi), b = 0.5 * (3.0 * chi - 1.0);
+    const double da = -0.5 * dchi, db = 1.5 * dchi;
+    const double vn = v[1] * n[0] + v[2] * n[1] + v[3] * n[2];
+    const double vd = v[1 + d], nd = n[d];
+    const double c2 = c * c;
+    double gN = c2 * (a * vd + b * vn * nd);
+    if (!clamped) gN -= c2 * f * (da * vd + db * vn * nd);
+    out[0] = gN;
+    out[1] = out[2] = out[3] = 0.0;
+    out[1 + d] = v[0];
+    if (dir) {
+        const double k1 = clamped ? 0.0 : c * (da * vd + db * vn * nd);
+        const double K = c2 * N * b / mag;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            out[1 + k] += k1 * n[k] + K * (nd * (v[1 + k] - vn * n[k]) + vn * ((k == d ? 1.0 : 0.0) - nd * n[k]));
+    }
+}
+
+__global__ void __launch_bounds__(128)
+transport_vjp_kernel(GridDev g, double c, double r, const double *__restrict__ N, const double *__restrict__ F,
+                     const double *__restrict__ lN1, const double *__restrict__ lF1, double *__restrict__ lN0,
+                     double *__restrict__ lF0)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nc) return;
+    const long long go = (long long)blockIdx.y * g.stride;   // group offset of N and lambda_N
+    const double *Ng = N + go, *Fg = F + 3 * go, *lNg = lN1 + go, *lFg = lF1 + 3 * go;
+    const int x = (int)(i % g.nx);
+    const int y = (int)((i / g.nx) % g.ny);
+    const int z = (int)(i / ((long long)g.nx * g.ny));
+    const int pos[3] = {x, y, z};
+    const int ext[3] = {g.nx, g.ny, g.nz};
+    const long long step[3] = {1, g.nx, (long long)g.nx * g.ny};
+
+    const double Nc = Ng[i];
+    const double Fc[3] = {Fg[i], Fg[g.stride + i], Fg[2 * g.stride + i]};
+    double lp[4] = {lNg[i], lFg[i], lFg[g.stride + i], lFg[2 * g.stride + i]};
+    double acc[4] = {lp[0], lp[1], lp[2], lp[3]};
+
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double m[4] = {0.0, 0.0, 0.0, 0.0};   // times J_c^T
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {   // 0: low face, 1: high face
+            const int bcode = g.bc[2 * d + side];
+            const bool at_edge = side ? (pos[d] == ext[d] - 1) : (pos[d] == 0);
+            double mu[4];
+            if (!at_edge || bcode == RT_BC_PERIODIC) {
+                long long nb;
+                if (!at_edge) nb = side ? i + step[d] : i - step[d];
+                else nb = side ? i - (long long)(ext[d] - 1) * step[d] : i + (long long)(ext[d] - 1) * step[d];
+                const double ln[4] = {lNg[nb], lFg[nb], lFg[g.stride + nb], lFg[2 * g.stride + nb]};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mu[k] = side ? r * (ln[k] - lp[k]) : r * (lp[k] - ln[k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    m[k] += 0.5 * mu[k];
+                    acc[k] += side ? 0.5 * c * mu[k] : -0.5 * c * mu[k];
+                }
+            } else {
+                // ghost B U_c: high face mu = -r lambda'_c, low face mu = r lambda'_c
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mu[k] = side ? -r * lp[k] : r * lp[k];
+                // this cell's own side of the face
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    m[k] += 0.5 * mu[k];
+                    acc[k] += side ? 0.5 * c * mu[k] : -0.5 * c * mu[k];
+                }
+                // the ghost's side, through B (B^T = B)
+                const double sgn = side ? -0.5 * c : 0.5 * c;
+                if (bcode == RT_BC_REFLECT) {
+                    double Fgh[3] = {Fc[0], Fc[1], Fc[2]};
+                    Fgh[d] = -Fgh[d];
+                    double jg[4];
+                    phi_vjp(Nc, Fgh, d, c, mu, jg);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        double t = 0.5 * jg[k] + sgn * mu[k];
+                        acc[k] += (k == 1 + d) ? -t : t;
+                    }
+                } else {   // outflow: B = I, J_ghost = J_c
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        m[k] += 0.5 * mu[k];
+                        acc[k] += sgn * mu[k];
+                    }
+                }
+            }
+        }
+        double jm[4];
+        phi_vjp(Nc, Fc, d, c, m, jm);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += jm[k];
+    }
+    double *lNo = lN0 + go, *lFo = lF0 + 3 * go;
+    lNo[i] = acc[0];
+    lFo[i] = acc[1];
+    lFo[g.stride + i] = acc[2];
+    lFo[2 * g.stride + i] = acc[3];
+}
+
+// dJ/dL_{s,i} += lambda_a(N_i at the cell of source s) dt / V
+__global__ void inject_vjp_kernel(int nsrc, int G, long long nc, const long long *__restrict__ cells,
+                                  const double *__restrict__ lN, double dt_over_V, double *g_L)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsrc) return;
+    const long long c = cells[s];
+    for (int k = 0; k < G; ++k) g_L[(long long)s * G + k] += lN[(long long)k * nc + c] * dt_over_V;
+}
+
+__global__ void count_mismatch_kernel(long long n, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                                      unsigned long long *count)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool m = i < n && a[i] != b[i];
+    const unsigned ball = __ballot_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(count, (unsigned long long)__popc(ball));
+}
+
+}  // namespace
+
+cudaError_t launch_thermo_vjp(const ThermoParams &tp, int G, const double *nH, const double *xHII,
+                              const double *xHeII, const double *xHeIII, const double *T, const double *N,
+                              const double *F, double *lx, double *ly2, double *ly3, double *lT,
+                              const double *lN_in, const double *lF_in, double *lN_out, double *lF_out,
+                              double *g_nH, int32_t *sub_out, unsigned *status, cudaStream_t s)
+{
+#define RTGB_TVJP(GG)                                                                                             \
+    case GG:                                                                                                      \
+        return launch_thermo_vjp_g<GG>(tp, nH, xHII, xHeII, xHeIII, T, N, F, lx, ly2, ly3, lT, lN_in, lF_in, lN_out, \
+                                       lF_out, g_nH, sub_out, status, s);
+    switch (G) {
+        RTGB_TVJP(1)
+        RTGB_TVJP(2)
+        RTGB_TVJP(3)
+        RTGB_TVJP(4)
+        RTGB_TVJP(5)
+        RTGB_TVJP(6)
+        RTGB_TVJP(7)
+        RTGB_TVJP(8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef RTGB_TVJP
+}
+
+cudaError_t launch_transport_vjp(const GridDev &g, int G, double cr, double dt, const double *N, const double *F,
+                                 const double *lN1, const double *lF1, double *lN0, double *lF0, cudaStream_t s)
+{
+    dim3 grid((unsigned)((g.nc + 127) / 128), (unsigned)G);
+    transport_vjp_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, lN1, lF1, lN0, lF0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_vjp(int nsrc, int G, long long nc, const long long *cells, const double *lN,
+                              double dt_over_V, double *g_L, cudaStream_t s)
+{
+    if (nsrc <= 0) return cudaSuccess;
+    inject_vjp_kernel<<<(nsrc + 127) / 128, 128, 0, s>>>(nsrc, G, nc, cells, lN, dt_over_V, g_L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_mismatch(long long n, const int32_t *a, const int32_t *b, unsigned long long *count,
+                                  cudaStream_t s)
+{
+    count_mismatch_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b, count);
+    return cudaGetLastError();
+}
+
+}  // namespace rtgb

@@ -319,7 +319,7 @@ int enqueue_batch_step(rt_batch *b, double dt)
             e = launch_thermo(tp, c.G, c.nH, c.xHII, c.xHeII, c.xHeIII, c.T, (double *)c.N[b->cur],
                               (double *)c.F[b->cur], c.sub, c.q, b->status, b->n_sm, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "thermo");
-        reset_counters_kernel<<<1, 32, 0, b->stream>>>(c.q.counters, 4);
+        reset_counters_kernel<<<1, 32, 0, b->stream>>>(c.q.counters, kQueueCounters);
     }
     if (f32)
         batch_reduce_kernel<float><<<b->nbg, kRB, 0, b->stream>>>(b->d_boxes, b->d_bg_box, b->d_bg_grp,
@@ -497,7 +497,7 @@ int rt_batch_create(int n_boxes, const rt_grid *grids, const int *n_groups, cons
                 (rc = balloc(b, &c.q.a.dt_tc, nc)) || (rc = balloc(b, &c.q.a.attempts, nc)) ||
                 (rc = balloc(b, &c.q.b.cell, nc)) || (rc = balloc(b, &c.q.b.t_left, nc)) ||
                 (rc = balloc(b, &c.q.b.dt_tc, nc)) || (rc = balloc(b, &c.q.b.attempts, nc)) ||
-                (rc = balloc(b, &c.q.counters, 4)))
+                (rc = balloc(b, &c.q.counters, kQueueCounters)))
                 goto bad;
             c.q.capacity = c.nc;
             for (int k = 0; k < 2; ++k) {
@@ -509,7 +509,7 @@ int rt_batch_create(int n_boxes, const rt_grid *grids, const int *n_groups, cons
                 cudaMemset(c.N[k], 0, G * nc * pb);
                 cudaMemset(c.F[k], 0, 3 * G * nc * pb);
             }
-            cudaMemset(c.q.counters, 0, 4 * sizeof(unsigned long long));
+            cudaMemset(c.q.counters, 0, kQueueCounters * sizeof(unsigned long long));
             cudaMemset(c.sub, 0, nc * sizeof(int32_t));
         }
         // box descriptors and (box, group) tables

@@ -104,10 +104,7 @@ __global__ void __launch_bounds__(RB) finalize_kernel(int G, int mode, const dou
         }
     }
     if (threadIdx.x == 0 && qcounters) {
-        qcounters[0] = 0ULL;
-        qcounters[1] = 0ULL;
-        qcounters[2] = 0ULL;
-        qcounters[3] = 0ULL;
+        for (int k = 0; k < kQueueCounters; ++k) qcounters[k] = 0ULL;
     }
 }
 

@@ -20,6 +20,8 @@
 
 #include <cuda_runtime.h>
 
+#include "dual.cuh"
+
 namespace rtgb {
 
 // exp arguments: exp(fma(a, ln T, fma(b, 1/T, c)))
@@ -49,12 +51,15 @@ struct RateTable {           // one per recombination case (A, B)
     double A_aHeII, p_aHeII;  // alpha_HeII = A (570670/T)^p
 };
 
-struct Transc {
-    double lnT, sqrtT, invT, u;   // u = 1 / (1 + sqrt(T / 1e5))
-    double e[NEXP];
-    double l[NHG];                 // log1p(w)
-    double v[NHG];                 // exp(p ln lam - s log1p(w))
+// S: double, or Dual (dual.cuh) when the adjoint differentiates the rates
+template <typename S>
+struct TranscT {
+    S lnT, sqrtT, invT, u;   // u = 1 / (1 + sqrt(T / 1e5))
+    S e[NEXP];
+    S l[NHG];                 // log1p(w)
+    S v[NHG];                 // exp(p ln lam - s log1p(w))
 };
+using Transc = TranscT<double>;
 
 // Rate tables: exp(a ln T + b/T + c) arguments and the Hui &
 // Gnedin parameters, case A then case B; the logarithms are of the fits'
@@ -192,10 +197,42 @@ __device__ __forceinline__ void transc_warp_f(double T, int case_b, Transc &t)
     }
 }
 
-// d ln v / dT of a Hui & Gnedin fit: -(1/T) (p - s r w / (1 + w))
-__device__ __forceinline__ double hg_dlog(const HGPar &h, const Transc &t, int j)
+// Stage 1 for a dual temperature: values from transc_serial (so they are
+// the bits of the double path), derivatives by the chain rule:
+// d lnT = dT/T, d sqrtT = sqrtT dT/(2T), d(1/T) = -dT/T^2, du = -u^2 k d sqrtT,
+// d exp(a lnT + b/T + c) = e (a d lnT + b d(1/T)), d log1p(w) = dw/(1 + w),
+// d exp(p (lnT1 - lnT) - s l) = v (-p d lnT - s dl).
+__device__ __forceinline__ void transc_dual(const Dual &T, int case_b, unsigned need, TranscT<Dual> &t)
 {
-    double w = t.e[E_W0 + j];
+    const RateTable &R = c_rate_tab[case_b];
+    Transc p;
+    transc_serial(T.v, case_b, need, p);
+    const double dT = T.d;
+    const double dln = p.invT * dT, dinv = -p.invT * p.invT * dT;
+    const double dsq = 0.5 * p.sqrtT * p.invT * dT;
+    t.lnT = Dual(p.lnT, dln);
+    t.sqrtT = Dual(p.sqrtT, dsq);
+    t.invT = Dual(p.invT, dinv);
+    t.u = Dual(p.u, -p.u * p.u * 0.003162277660168379 * dsq);
+#pragma unroll
+    for (int k = 0; k < NEXP; ++k)
+        if (need & (1u << k)) t.e[k] = Dual(p.e[k], p.e[k] * (R.ea[k].a * dln + R.ea[k].b * dinv));
+#pragma unroll
+    for (int j = 0; j < NHG; ++j) {
+        if (need & (1u << (NEXP + j))) {
+            const double w = p.e[E_W0 + j];
+            const double dl = t.e[E_W0 + j].d / (1.0 + w);
+            t.l[j] = Dual(p.l[j], dl);
+            t.v[j] = Dual(p.v[j], p.v[j] * (-R.hg[j].p * dln - R.hg[j].s * dl));
+        }
+    }
+}
+
+// d ln v / dT of a Hui & Gnedin fit: -(1/T) (p - s r w / (1 + w))
+template <typename S>
+__device__ __forceinline__ S hg_dlog(const HGPar &h, const TranscT<S> &t, int j)
+{
+    S w = t.e[E_W0 + j];
     return -t.invT * (h.p - h.s * h.r * w / (1.0 + w));
 }
 
@@ -211,21 +248,27 @@ constexpr unsigned kNeedCoolHe = (1u << E_BETA_HEI) | (1u << E_BETA_HEII) | (1u 
                                  (1u << E_OMEGA1) | (1u << E_OMEGA2) | (1u << E_ALPHA_HEII) |
                                  (1u << (E_W0 + HG_ETA_HEIII)) | (1u << (NEXP + HG_ETA_HEIII));
 
-struct HRates {       // rates needed by the x_HII update
-    double beta, dbeta, alpha, dalpha;
+template <typename S>
+struct HRatesT {      // rates needed by the x_HII update
+    S beta, dbeta, alpha, dalpha;
 };
-struct HeRates {
-    double beta_HeI, beta_HeII, alpha_HeII, alpha_HeIII;
+template <typename S>
+struct HeRatesT {
+    S beta_HeI, beta_HeII, alpha_HeII, alpha_HeIII;
 };
+using HRates = HRatesT<double>;
+using HeRates = HeRatesT<double>;
 
 // Cen (1992) form A sqrt(T) u exp(-T0/T)
-__device__ __forceinline__ void cen_fit(double A, double T0, double e, const Transc &t, double &v, double &dv)
+template <typename S>
+__device__ __forceinline__ void cen_fit(double A, double T0, const S &e, const TranscT<S> &t, S &v, S &dv)
 {
     v = A * t.sqrtT * t.u * e;
     dv = v * (0.5 * t.u * t.invT + T0 * t.invT * t.invT);
 }
 
-__device__ __forceinline__ void h_rates_from(const Transc &t, int case_b, HRates &r)
+template <typename S>
+__device__ __forceinline__ void h_rates_from(const TranscT<S> &t, int case_b, HRatesT<S> &r)
 {
     const RateTable &R = c_rate_tab[case_b];
     cen_fit(5.85e-11, 157809.1, t.e[E_BETA_HI], t, r.beta, r.dbeta);
@@ -233,10 +276,11 @@ __device__ __forceinline__ void h_rates_from(const Transc &t, int case_b, HRates
     r.dalpha = r.alpha * hg_dlog(R.hg[HG_ALPHA_HII], t, HG_ALPHA_HII);
 }
 
-__device__ __forceinline__ void he_rates_from(const Transc &t, int case_b, HeRates &r)
+template <typename S>
+__device__ __forceinline__ void he_rates_from(const TranscT<S> &t, int case_b, HeRatesT<S> &r)
 {
     const RateTable &R = c_rate_tab[case_b];
-    double d;
+    S d;
     cen_fit(2.38e-11, 285335.4, t.e[E_BETA_HEI], t, r.beta_HeI, d);
     cen_fit(5.68e-12, 631515.0, t.e[E_BETA_HEII], t, r.beta_HeII, d);
     r.alpha_HeII = R.A_aHeII * t.e[E_ALPHA_HEII];
@@ -245,52 +289,53 @@ __device__ __forceinline__ void he_rates_from(const Transc &t, int case_b, HeRat
 
 // Primordial cooling magnitude L (Eq. (rate_cooling), positive = cooling)
 // and dL/dT for the given densities and electron density.
-__device__ __forceinline__ void cooling_from(const Transc &t, int case_b, double a_exp, bool helium, double T,
-                                             double ne, double nHI, double nHII, double nHeI, double nHeII,
-                                             double nHeIII, double &L, double &dL)
+template <typename S>
+__device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, double a_exp, bool helium, const S &T,
+                                             const S &ne, const S &nHI, const S &nHII, const S &nHeI,
+                                             const S &nHeII, const S &nHeIII, S &L, S &dL)
 {
     const RateTable &R = c_rate_tab[case_b];
     const double kB = 1.380649e-16;
-    double v, dv;
+    S v, dv;
     cen_fit(1.27e-21, 157809.1, t.e[E_BETA_HI], t, v, dv);
-    double psi = 7.5e-19 * t.u * t.e[E_PSI_HI];
-    double dpsi = psi * (-0.5 * (1.0 - t.u) * t.invT + 118348.0 * t.invT * t.invT);
-    double Ls = (v + psi) * nHI;
-    double dLs = (dv + dpsi) * nHI;
-    double eta = R.hg[HG_ETA_HII].A * t.v[HG_ETA_HII];
-    double deta = eta * hg_dlog(R.hg[HG_ETA_HII], t, HG_ETA_HII);
+    S psi = 7.5e-19 * t.u * t.e[E_PSI_HI];
+    S dpsi = psi * (-0.5 * (1.0 - t.u) * t.invT + 118348.0 * t.invT * t.invT);
+    S Ls = (v + psi) * nHI;
+    S dLs = (dv + dpsi) * nHI;
+    S eta = R.hg[HG_ETA_HII].A * t.v[HG_ETA_HII];
+    S deta = eta * hg_dlog(R.hg[HG_ETA_HII], t, HG_ETA_HII);
     Ls += T * eta * nHII;
     dLs += (eta + T * deta) * nHII;
-    double th = 1.42e-27 * t.sqrtT;
-    double dth = 0.5 * th * t.invT;
+    S th = 1.42e-27 * t.sqrtT;
+    S dth = 0.5 * th * t.invT;
     Ls += th * (nHII + nHeII + 4.0 * nHeIII);
     dLs += dth * (nHII + nHeII + 4.0 * nHeIII);
     if (helium) {
         cen_fit(9.38e-22, 285335.4, t.e[E_BETA_HEI], t, v, dv);
         Ls += v * nHeI;
         dLs += dv * nHeI;
-        double zs, dzs;
+        S zs, dzs;
         cen_fit(4.95e-22, 631515.0, t.e[E_BETA_HEII], t, zs, dzs);
-        double p2 = 5.54e-17 * t.u * t.e[E_PSI_HEII];
-        double dp2 = p2 * (-0.397 * t.invT - 0.5 * (1.0 - t.u) * t.invT + 473638.0 * t.invT * t.invT);
-        double a2 = R.A_aHeII * t.e[E_ALPHA_HEII];
-        double da2 = -a2 * R.p_aHeII * t.invT;
-        double et2 = kB * T * a2;
-        double det2 = kB * (a2 + T * da2);
-        double base = 1.24e-13 * t.e[E_OMEGA1];
-        double e7 = t.e[E_OMEGA2];
-        double om = base * (1.0 + 0.3 * e7);
-        double dom = om * (-1.5 * t.invT + 470000.0 * t.invT * t.invT) + base * 0.3 * e7 * 94000.0 * t.invT * t.invT;
+        S p2 = 5.54e-17 * t.u * t.e[E_PSI_HEII];
+        S dp2 = p2 * (-0.397 * t.invT - 0.5 * (1.0 - t.u) * t.invT + 473638.0 * t.invT * t.invT);
+        S a2 = R.A_aHeII * t.e[E_ALPHA_HEII];
+        S da2 = -a2 * R.p_aHeII * t.invT;
+        S et2 = kB * T * a2;
+        S det2 = kB * (a2 + T * da2);
+        S base = 1.24e-13 * t.e[E_OMEGA1];
+        S e7 = t.e[E_OMEGA2];
+        S om = base * (1.0 + 0.3 * e7);
+        S dom = om * (-1.5 * t.invT + 470000.0 * t.invT * t.invT) + base * 0.3 * e7 * 94000.0 * t.invT * t.invT;
         Ls += (zs + p2 + et2 + om) * nHeII;
         dLs += (dzs + dp2 + det2 + dom) * nHeII;
-        double e3h = R.hg[HG_ETA_HEIII].A * t.v[HG_ETA_HEIII];
-        double de3h = e3h * hg_dlog(R.hg[HG_ETA_HEIII], t, HG_ETA_HEIII);
+        S e3h = R.hg[HG_ETA_HEIII].A * t.v[HG_ETA_HEIII];
+        S de3h = e3h * hg_dlog(R.hg[HG_ETA_HEIII], t, HG_ETA_HEIII);
         Ls += T * e3h * nHeIII;
         dLs += (e3h + T * de3h) * nHeIII;
     }
     double Tg = 2.727 / a_exp;
     double Tg4 = Tg * Tg * Tg * Tg;
-    double vp = 1.017e-37 * Tg4 * (T - Tg);
+    S vp = 1.017e-37 * Tg4 * (T - Tg);
     L = ne * (Ls + vp);
     dL = ne * (dLs + 1.017e-37 * Tg4);
 }

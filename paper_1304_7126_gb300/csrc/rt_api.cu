@@ -47,6 +47,13 @@ struct rt_handle {
     long long *src_cell = nullptr;
     double *src_L = nullptr;
     std::vector<double> src_Lsum_host;   // total luminosity per group
+    int nsrc_orig = 0;                    // sources as given (not merged per cell)
+    long long *src_cell_orig = nullptr;
+
+    // adjoint scratch (rt_step_vjp, rt_run_vjp)
+    double *adj = nullptr;               // NA, FA, NB, FB, lNb, lFb, gas copy
+    int32_t *adj_sub = nullptr;          // [2][nc] attempts: adjoint, forward check
+    unsigned long long *adj_count = nullptr;
 
     bool state_set = false;
     cudaGraphExec_t graph = nullptr;
@@ -114,7 +121,8 @@ void free_all(rt_handle *h)
     void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
                     h->Nf[0], h->Nf[1], h->Ff[0], h->Ff[1], h->hllf, h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
                     h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
-                    h->budget, h->status, h->src_cell, h->src_L};
+                    h->budget, h->status, h->src_cell, h->src_L, h->src_cell_orig, h->adj, h->adj_sub,
+                    h->adj_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->status_host) cudaFreeHost(h->status_host);
@@ -253,6 +261,77 @@ void invalidate_graph(rt_handle *h)
     }
 }
 
+
+int ensure_adj(rt_handle *h)
+{
+    if (h->adj) return RT_OK;
+    const long long nc = h->g.nc;
+    int rc;
+    if ((rc = dalloc(h, &h->adj, (size_t)(12 * h->G + 4) * nc)) || (rc = dalloc(h, &h->adj_sub, 2 * (size_t)nc)) ||
+        (rc = dalloc(h, &h->adj_count, 1)))
+        return rc;
+    return RT_OK;
+}
+
+// Adjoint of one step from the handle's state U_k (left unchanged); see
+// rt_step_vjp.  check: also re-run the forward thermochemistry on a copy of
+// U_b and count the cells whose attempt count differs from the adjoint's
+// recomputation into adj_count.
+int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, double *lT, double *lN,
+                double *lF, double *g_nH, double *g_L, bool check)
+{
+    const long long nc = h->g.nc;
+    const int G = h->G;
+    const double V = h->g.dx * h->g.dx * h->g.dx;
+    int rc = ensure_adj(h);
+    if (rc) return rc;
+    double *NA = h->adj, *FA = NA + G * nc, *NB = FA + 3 * G * nc, *FB = NB + G * nc;
+    double *lNb = FB + 3 * G * nc, *lFb = lNb + G * nc, *gas = lFb + 3 * G * nc;
+    cudaStream_t st = h->stream;
+    const int c0 = h->cur;
+    cudaError_t e;
+    RT_CUDA(h, cudaMemcpyAsync(NA, h->N[c0], G * nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RT_CUDA(h, cudaMemcpyAsync(FA, h->F[c0], 3 * G * nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (h->nsrc > 0) {
+        e = launch_inject(h->nsrc, G, nc, h->src_cell, h->src_L, dt / V, NA, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "inject");
+    }
+    e = launch_transport(h->g, G, h->opt.flux, h->cr, dt, NA, FA, NB, FB, h->hll, h->part, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "transport");
+    ThermoParams tp = thermo_params(h, dt);
+    int32_t *sub_adj = check ? h->adj_sub : nullptr;
+    e = launch_thermo_vjp(tp, G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, NB, FB, lx, ly2, ly3, lT, lN, lF, lNb,
+                          lFb, g_nH, sub_adj, h->status, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "thermo_vjp");
+    e = launch_transport_vjp(h->g, G, h->cr, dt, NA, FA, lNb, lFb, lN, lF, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "transport_vjp");
+    e = launch_inject_vjp(h->nsrc_orig, G, nc, h->src_cell_orig, lN, dt / V, g_L, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "inject_vjp");
+    if (check) {
+        double *gx = gas, *gy2 = gas + nc, *gy3 = gas + 2 * nc, *gT = gas + 3 * nc;
+        RT_CUDA(h, cudaMemcpyAsync(gx, h->xHII, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RT_CUDA(h, cudaMemcpyAsync(gy2, h->xHeII, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RT_CUDA(h, cudaMemcpyAsync(gy3, h->xHeIII, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RT_CUDA(h, cudaMemcpyAsync(gT, h->T, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        e = launch_thermo(tp, G, h->nH, gx, gy2, gy3, gT, NB, FB, h->adj_sub + nc, h->q, h->status, h->n_sm, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "thermo");
+        RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, kQueueCounters * sizeof(unsigned long long), st));
+        e = launch_count_mismatch(nc, h->adj_sub, h->adj_sub + nc, h->adj_count, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "count");
+    }
+    return RT_OK;
+}
+
+int vjp_args(rt_handle *h, double *dt, double *lx, double *ly2, double *ly3, double *lT, double *lN, double *lF,
+             double *g_nH, double *g_L)
+{
+    if (h->opt.precision != RT_FP64 || h->opt.flux != RT_GLF)
+        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64 and flux RT_GLF");
+    if (!lx || !ly2 || !ly3 || !lT || !lN || !lF || !g_nH || (h->nsrc_orig > 0 && !g_L))
+        return fail(h, RT_EINVAL, "null adjoint array");
+    return check_dt(h, dt);
+}
+
 }  // namespace
 
 extern "C" {
@@ -348,7 +427,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
             (rc = dalloc(h, &h->q.a.dt_tc, nc)) || (rc = dalloc(h, &h->q.a.attempts, nc)) ||
             (rc = dalloc(h, &h->q.b.cell, nc)) || (rc = dalloc(h, &h->q.b.t_left, nc)) ||
             (rc = dalloc(h, &h->q.b.dt_tc, nc)) || (rc = dalloc(h, &h->q.b.attempts, nc)) ||
-            (rc = dalloc(h, &h->q.counters, 4)) ||
+            (rc = dalloc(h, &h->q.counters, kQueueCounters)) ||
             (rc = dalloc(h, &h->part.tr_inbox, G * h->part.n_tr_blocks)) ||
             (rc = dalloc(h, &h->part.tr_outflow, G * h->part.n_tr_blocks)) ||
             (rc = dalloc(h, &h->part.th_inbox, G * h->part.n_red_blocks)) ||
@@ -383,7 +462,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
                 rc = cuda_fail(h, e, "hll copy"); goto bad;
             }
         }
-        if ((e = cudaMemset(h->q.counters, 0, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+        if ((e = cudaMemset(h->q.counters, 0, kQueueCounters * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMemset(h->status, 0, sizeof(unsigned))) != cudaSuccess ||
             (e = cudaMemset(h->budget, 0, 4 * G * sizeof(double))) != cudaSuccess ||
             (e = cudaMemset(h->subcycles, 0, nc * sizeof(int32_t))) != cudaSuccess) {
@@ -473,7 +552,7 @@ int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const doubl
         RT_CUDA(h, cudaStreamSynchronize(h->stream));
     }
     RT_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-    RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, 4 * sizeof(unsigned long long), h->stream));
+    RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, kQueueCounters * sizeof(unsigned long long), h->stream));
     cudaError_t e = h->mixed ? launch_reduce_N_f32(G, nc, h->Nf[0], h->part, h->stream)
                              : launch_reduce_N(G, nc, h->N[0], h->part, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
@@ -570,6 +649,17 @@ int rt_set_sources(rt_handle *h, int n, const int32_t *ijk, const double *L)
     }
     h->nsrc = m;
     h->src_Lsum_host = tot;
+    if (h->src_cell_orig) { cudaFree(h->src_cell_orig); h->src_cell_orig = nullptr; }
+    h->nsrc_orig = 0;
+    if (n > 0) {
+        std::vector<long long> oc(n);
+        for (int s = 0; s < n; ++s)
+            oc[s] = ((long long)ijk[3 * s + 2] * h->g.ny + ijk[3 * s + 1]) * h->g.nx + ijk[3 * s];
+        int rc = dalloc(h, &h->src_cell_orig, n);
+        if (rc) return rc;
+        RT_CUDA(h, cudaMemcpy(h->src_cell_orig, oc.data(), n * sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    h->nsrc_orig = n;
     invalidate_graph(h);
     return RT_OK;
 }
@@ -653,6 +743,83 @@ int rt_get_profile(rt_handle *h, double *ms, int64_t *launches)
     int rc = sync_and_check(h);
     for (int k = 0; k < RT_NPHASES; ++k) { ms[k] = h->prof_ms[k]; launches[k] = h->prof_n[k]; }
     return rc;
+}
+
+int rt_step_vjp(rt_handle *h, double dt, double *lam_xHII, double *lam_xHeII, double *lam_xHeIII, double *lam_T,
+                double *lam_N, double *lam_F, double *g_nH, double *g_L, long long *mismatches)
+{
+    if (!h) return RT_EINVAL;
+    int rc = vjp_args(h, &dt, lam_xHII, lam_xHeII, lam_xHeIII, lam_T, lam_N, lam_F, g_nH, g_L);
+    if (rc) return rc;
+    const bool check = mismatches != nullptr;
+    if ((rc = ensure_adj(h))) return rc;
+    if (check) RT_CUDA(h, cudaMemsetAsync(h->adj_count, 0, sizeof(unsigned long long), h->stream));
+    rc = enqueue_vjp(h, dt, lam_xHII, lam_xHeII, lam_xHeIII, lam_T, lam_N, lam_F, g_nH, g_L, check);
+    if (rc) return rc;
+    if (check) {
+        rc = sync_and_check(h);
+        if (rc) return rc;
+        unsigned long long n = 0;
+        RT_CUDA(h, cudaMemcpy(&n, h->adj_count, sizeof(n), cudaMemcpyDeviceToHost));
+        *mismatches += (long long)n;
+    }
+    return RT_OK;
+}
+
+int rt_run_vjp(rt_handle *h, double dt, int nsteps, double *lam_xHII, double *lam_xHeII, double *lam_xHeIII,
+               double *lam_T, double *lam_N, double *lam_F, double *g_nH, double *g_L, long long *mismatches)
+{
+    if (!h) return RT_EINVAL;
+    if (nsteps < 0) return fail(h, RT_EINVAL, "nsteps < 0");
+    int rc = vjp_args(h, &dt, lam_xHII, lam_xHeII, lam_xHeIII, lam_T, lam_N, lam_F, g_nH, g_L);
+    if (rc) return rc;
+    if (nsteps == 0) return RT_OK;
+    const long long nc = h->g.nc;
+    const size_t per = (size_t)(4 + 4 * h->G) * nc;   // gas x_HII, x_HeII, x_HeIII, T + N, F
+    double *traj = nullptr;
+    cudaError_t e = cudaMalloc((void **)&traj, per * nsteps * sizeof(double));
+    if (e != cudaSuccess) return fail(h, RT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    auto copy_state = [&](double *dst, bool save) -> int {
+        double *gas[4] = {h->xHII, h->xHeII, h->xHeIII, h->T};
+        const size_t b1 = nc * sizeof(double);
+        for (int k = 0; k < 4; ++k) {
+            cudaError_t ee = save ? cudaMemcpyAsync(dst + k * nc, gas[k], b1, cudaMemcpyDeviceToDevice, h->stream)
+                                  : cudaMemcpyAsync(gas[k], dst + k * nc, b1, cudaMemcpyDeviceToDevice, h->stream);
+            if (ee != cudaSuccess) return cuda_fail(h, ee, "trajectory copy");
+        }
+        double *Nd = dst + 4 * nc, *Fd = Nd + (size_t)h->G * nc;
+        const size_t bN = (size_t)h->G * nc * sizeof(double);
+        cudaError_t e1 = save ? cudaMemcpyAsync(Nd, h->N[h->cur], bN, cudaMemcpyDeviceToDevice, h->stream)
+                              : cudaMemcpyAsync(h->N[h->cur], Nd, bN, cudaMemcpyDeviceToDevice, h->stream);
+        cudaError_t e2 = save ? cudaMemcpyAsync(Fd, h->F[h->cur], 3 * bN, cudaMemcpyDeviceToDevice, h->stream)
+                              : cudaMemcpyAsync(h->F[h->cur], Fd, 3 * bN, cudaMemcpyDeviceToDevice, h->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(h, e1 != cudaSuccess ? e1 : e2, "trajectory copy");
+        return RT_OK;
+    };
+    const bool check = mismatches != nullptr;
+    if ((rc = ensure_adj(h))) { cudaFree(traj); return rc; }
+    if (check) RT_CUDA(h, cudaMemsetAsync(h->adj_count, 0, sizeof(unsigned long long), h->stream));
+    invalidate_graph(h);
+    // recompute the forward trajectory, keeping every step's input state
+    for (int k = 0; k < nsteps && !rc; ++k) {
+        rc = copy_state(traj + per * k, true);
+        if (!rc) rc = enqueue_step(h, dt);
+    }
+    // reverse sweep; the handle ends at the state it started from
+    for (int k = nsteps - 1; k >= 0 && !rc; --k) {
+        rc = copy_state(traj + per * k, false);
+        if (!rc) rc = enqueue_vjp(h, dt, lam_xHII, lam_xHeII, lam_xHeIII, lam_T, lam_N, lam_F, g_nH, g_L, check);
+    }
+    int rs = sync_and_check(h);
+    cudaFree(traj);
+    if (rc) return rc;
+    if (rs) return rs;
+    if (check) {
+        unsigned long long n = 0;
+        RT_CUDA(h, cudaMemcpy(&n, h->adj_count, sizeof(n), cudaMemcpyDeviceToHost));
+        *mismatches += (long long)n;
+    }
+    return RT_OK;
 }
 
 int rt_sync(rt_handle *h)

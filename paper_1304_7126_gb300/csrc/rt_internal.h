@@ -69,7 +69,10 @@ struct ThermoParams {
 };
 
 // Device work queues of cells whose sub-cycling outlasted the first pass
-// (a) and the lane-per-cell drain (b).
+// (a) and the lane-per-cell drain (b); queue c, the input of the
+// warp-per-cell kernel, reuses the arrays of a once a is drained.
+constexpr int kQueueCounters = 8;
+
 struct QueueArrays {
     uint32_t *cell;
     double *t_left;
@@ -78,7 +81,8 @@ struct QueueArrays {
 };
 struct Queue {
     QueueArrays a, b;
-    unsigned long long *counters;   // [0] a.count, [1] a.head, [2] b.count, [3] b.head
+    unsigned long long *counters;   // kQueueCounters: [0] a.count, [1] a.head, [2] b.count,
+                                    // [3] b.head, [4] c.count, [5] c.head
     long long capacity;             // items per queue
 };
 
@@ -134,6 +138,26 @@ cudaError_t launch_inject_f32(int nsrc, int G, long long nc, const long long *ce
 cudaError_t launch_reduce_N_f32(int G, long long nc, const float *N, const Partials &p, cudaStream_t s);
 cudaError_t launch_convert_d2f(long long n, const double *in, float *out, cudaStream_t s);
 cudaError_t launch_convert_f2d(long long n, const float *in, double *out, cudaStream_t s);
+
+// ---- adjoint (adjoint.cu) ----
+// thermo_vjp: lambda' (gas lx..lT in place; photons lN_in/lF_in) of the
+// state after the thermochemistry -> lambda of the state U_b before it
+// (gas in place, photons to lN_out/lF_out); g_nH += dJ/dn_H.  N, F, gas:
+// U_b.  sub_out (optional): attempts of the recomputation per cell.
+cudaError_t launch_thermo_vjp(const ThermoParams &tp, int G, const double *nH, const double *xHII,
+                              const double *xHeII, const double *xHeIII, const double *T, const double *N,
+                              const double *F, double *lx, double *ly2, double *ly3, double *lT,
+                              const double *lN_in, const double *lF_in, double *lN_out, double *lF_out,
+                              double *g_nH, int32_t *sub_out, unsigned *status, cudaStream_t s);
+// transport_vjp (GLF): lambda of the transported photons (lN1, lF1) -> lambda
+// of the photons before transport (lN0, lF0); N, F: the state before it.
+cudaError_t launch_transport_vjp(const GridDev &g, int G, double cr, double dt, const double *N, const double *F,
+                                 const double *lN1, const double *lF1, double *lN0, double *lF0, cudaStream_t s);
+// g_L[s][i] += lN[i][cells[s]] dt / V for every source s (unmerged list)
+cudaError_t launch_inject_vjp(int nsrc, int G, long long nc, const long long *cells, const double *lN,
+                              double dt_over_V, double *g_L, cudaStream_t s);
+cudaError_t launch_count_mismatch(long long n, const int32_t *a, const int32_t *b, unsigned long long *count,
+                                  cudaStream_t s);
 
 int reduce_blocks_per_group();
 

@@ -38,238 +38,23 @@
 
 #include "rates.cuh"
 #include "rt_internal.h"
+#include "thermo_step.cuh"
 
 namespace rtgb {
 
 
 namespace {
 
-constexpr double kEV = 1.602176634e-12;
-constexpr double kEps0 = 13.60 * kEV, kEps1 = 24.59 * kEV, kEps2 = 54.42 * kEV;
-constexpr double kFloorN = 1e-30;
-constexpr double kXMin = 1e-6;
-constexpr double kNeFloor = 1e-6;
-constexpr double kTFloor = 1.0;
+using namespace thermo_detail;
+
 constexpr int kPass1Block = 128;
-constexpr int kDrainBudget = 192;   // attempts a cell may spend in thermo_drain
-
-template <int G>
-struct CellState {
-    double x, y2, y3, T;
-    double N[G];
-    double Fs[G];     // accumulated flux scale prod 1/(1 + h D_i)
-};
-
-struct IsoRates {     // rates at the fixed temperature of an isothermal cell
-    HRates h;
-    HeRates he;
-};
-
-struct CoolCache {    // cooling L and dL/dT of the current state at t
-    double L, dL;
-    bool valid;
-};
-
-__device__ __forceinline__ double mu_of(double X, double x, double y2, double y3)
-{
-    return 1.0 / (X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3));
-}
-
-template <bool WARP, bool MIX>
-__device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, Transc &t)
-{
-    if (MIX) {
-        if (WARP) transc_warp_f(T, case_b, t);
-        else transc_serial_f(T, case_b, need, t);
-    } else {
-        if (WARP) transc_warp(T, case_b, t);
-        else transc_serial(T, case_b, need, t);
-    }
-}
-
-// One thermo_step over h.  Returns true and fills `o` and `maxrel` when the
-// 10% rule holds.  MIX (the RT_MIXED path): rates from FP32 transcendentals
-// and the photon update in FP32; T/mu, x_HII, helium and 1 - x stay FP64.
-template <int G, bool WARP, bool MIX>
-__device__ __forceinline__ bool attempt(const ThermoParams &p, double nH, const CellState<G> &s, double h,
-                                        const IsoRates &iso, CoolCache &cc, CellState<G> &o, double &maxrel)
-{
-    const double nHe = nH * p.he_ratio;
-    const double x = s.x, y2 = s.y2, y3 = s.y3;
-    const double nHI = nH * (1.0 - x);
-    const double nHII = nH * x;
-    const double nHeI = nHe * (1.0 - y2 - y3);
-    const double nHeII = nHe * y2;
-    const double nHeIII = nHe * y3;
-    const double ne = nHII + (y2 + 2.0 * y3) * nHe;
-    const double cr = p.cr;
-    double rel_max = 0.0;
-    double gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
-
-    // 1. photons
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-        double Nn;
-        if (MIX) {
-            float D = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
-                                   (float)p.gc.sigN[i][2] * (float)nHeII);
-            float inv = 1.0f / (1.0f + (float)h * D);
-            float N0 = (float)s.N[i];
-            float Nf = N0 * inv;
-            float rel = fabsf(Nf - N0) / fmaxf(N0, (float)kFloorN);
-            if (rel > 0.1f) return false;
-            rel_max = fmax(rel_max, (double)rel);
-            Nn = Nf;
-            o.Fs[i] = (float)s.Fs[i] * inv;
-        } else {
-            double D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
-            double inv = 1.0 / (1.0 + h * D);
-            Nn = s.N[i] * inv;
-            double rel = fabs(Nn - s.N[i]) / fmax(s.N[i], kFloorN);
-            if (rel > 0.1) return false;
-            rel_max = fmax(rel_max, rel);
-            o.Fs[i] = s.Fs[i] * inv;
-        }
-        o.N[i] = Nn;
-        double crN = cr * Nn;
-        gam0 += p.gc.sigN[i][0] * crN;
-        gam1 += p.gc.sigN[i][1] * crN;
-        gam2 += p.gc.sigN[i][2] * crN;
-        if (!p.isothermal) {
-            heat += crN * (nHI * (p.gc.egy[i] * p.gc.sigE[i][0] - kEps0 * p.gc.sigN[i][0]) +
-                           nHeI * (p.gc.egy[i] * p.gc.sigE[i][1] - kEps1 * p.gc.sigN[i][1]) +
-                           nHeII * (p.gc.egy[i] * p.gc.sigE[i][2] - kEps2 * p.gc.sigN[i][2]));
-        }
-    }
-
-    // 2. temperature
-    const double mu = mu_of(p.X, x, y2, y3);
-    double Tmu1 = 0.0;
-    if (!p.isothermal) {
-        if (!cc.valid) {
-            Transc t;
-            get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
-            cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L,
-                         cc.dL);
-            cc.valid = true;
-        }
-        double lam = heat - cc.L;
-        double dlam = -mu * cc.dL;
-        double K = p.kfac / nH;
-        double Tmu = s.T / mu;
-        double dT = lam * K * h / (1.0 - dlam * K * h);
-        Tmu1 = Tmu + dT;
-        double rel = fabs(dT) / Tmu;
-        if (rel > 0.1) return false;
-        if (fabs(K * lam * h) / Tmu > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
-    }
-
-    // 3. hydrogen
-    HRates hr;
-    if (p.isothermal) {
-        hr = iso.h;
-    } else {
-        Transc t;
-        get_transc<WARP, MIX>(Tmu1 * mu, p.case_b, kNeedH, t);
-        h_rates_from(t, p.case_b, hr);
-    }
-    double C = hr.beta * ne + gam0;
-    double Dd = hr.alpha * ne;
-    double dC = nH * hr.beta, dD = nH * hr.alpha;
-    if (!p.isothermal) {
-        double f = ne * Tmu1 * mu * mu * p.X;
-        dC -= f * hr.dbeta;
-        dD -= f * hr.dalpha;
-    }
-    double J = dC - (C + Dd) - x * (dC + dD);
-    double xdot = C - x * (C + Dd);
-    double x1 = x + h * xdot / (1.0 - J * h);
-    x1 = fmin(fmax(x1, kXMin), 1.0);
-    {
-        double xden = fmax(x, kXMin);
-        double rel = fabs(x1 - x) / xden;
-        if (rel > 0.1) return false;
-        if (fabs(xdot) * h / xden > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
-    }
-
-    // 4. helium
-    double y2n = y2, y3n = y3;
-    if (p.helium) {
-        double yI = 1.0 - y2 - y3;
-        double ne2 = x1 * nH + (y2 + 2.0 * y3) * nHe;
-        HeRates r2;
-        if (p.isothermal) {
-            r2 = iso.he;
-        } else {
-            Transc t;
-            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
-            he_rates_from(t, p.case_b, r2);
-        }
-        double C1 = y2 * r2.alpha_HeII * ne2;
-        double D1 = r2.beta_HeI * ne2 + gam1;
-        double yI1 = (yI + C1 * h) / (1.0 + D1 * h);
-        double C2 = yI1 * (r2.beta_HeI * ne2 + gam1) + y3 * r2.alpha_HeIII * ne2;
-        double D2 = (r2.beta_HeII + r2.alpha_HeII) * ne2 + gam2;
-        y2n = (y2 + C2 * h) / (1.0 + D2 * h);
-        double ne3 = x1 * nH + (y2n + 2.0 * y3) * nHe;
-        HeRates r3;
-        if (p.isothermal) {
-            r3 = iso.he;
-        } else {
-            Transc t;
-            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
-            he_rates_from(t, p.case_b, r3);
-        }
-        double C3 = y2n * (r3.beta_HeII * ne3 + gam2);
-        double D3 = r3.alpha_HeIII * ne3;
-        y3n = (y3 + C3 * h) / (1.0 + D3 * h);
-        // conservation: lower the largest fraction (HeI largest: no change)
-        if (y2n >= yI1 && y2n >= y3n) y2n = 1.0 - yI1 - y3n;
-        else if (y3n >= yI1 && y3n > y2n) y3n = 1.0 - yI1 - y2n;
-        y2n = fmin(fmax(y2n, 0.0), 1.0);
-        y3n = fmin(fmax(y3n, 0.0), 1.0);
-    }
-    {
-        double ne1 = x1 * nH + (y2n + 2.0 * y3n) * nHe;
-        double rel = fabs(ne1 - ne) / fmax(ne, kNeFloor * nH);
-        if (rel > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
-    }
-    double Tf = p.isothermal ? s.T : Tmu1 * mu_of(p.X, x1, y2n, y3n);
-    o.x = x1;
-    o.y2 = y2n;
-    o.y3 = y3n;
-    o.T = fmax(Tf, kTFloor);
-    maxrel = rel_max;
-    return true;
-}
-
-// One attempt of the sub-cycling loop; returns true when the cell is done.
-template <int G, bool WARP, bool MIX>
-__device__ __forceinline__ bool subcycle_once(const ThermoParams &p, double nH, CellState<G> &st, double &t_left,
-                                              double &dt_tc, int &att, const IsoRates &iso, CoolCache &cc)
-{
-    double h = (dt_tc < t_left) ? dt_tc : t_left;
-    ++att;
-    CellState<G> o;
-    double mr = 0.0;
-    if (attempt<G, WARP, MIX>(p, nH, st, h, iso, cc, o, mr)) {
-        st = o;
-        cc.valid = false;
-        t_left = (h == t_left) ? 0.0 : t_left - h;
-        dt_tc = (mr < 0.05) ? 2.0 * h : h;
-    } else {
-        dt_tc = 0.5 * h;
-    }
-    return !(t_left > 0.0);
-}
+constexpr int kDrainBudget = 192;   // attempts a cell may spend in the first drain stage
+constexpr int kDrain2Budget = 512;  // ... and in the second
 
 template <int G, bool WARP, typename P, bool R32>
 __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, const double *xHII,
                                           const double *xHeII, const double *xHeIII, const double *T,
-                                          const P *N, CellState<G> &st, IsoRates &iso, CoolCache &cc)
+                                          const P *N, CellState<G> &st, IsoRates<> &iso, CoolCache<> &cc)
 {
     st.x = xHII[c];
     st.y2 = xHeII[c];
@@ -339,8 +124,8 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     int att = 0;
     if (valid) {
         CellState<G> st;
-        IsoRates iso;
-        CoolCache cc;
+        IsoRates<> iso;
+        CoolCache<> cc;
         load_cell<G, false, P, R32>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         double n = nH[c];
         bool done = false;
@@ -369,28 +154,51 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     }
 }
 
+// One lane-per-cell drain stage: cells of queue `src` (count and head in
+// counters[cnt], counters[cnt + 1]) sub-cycle here for at most `budget`
+// attempts; a cell still unfinished moves to queue `dst` (count in
+// counters[dst_cnt]).  When `src` holds no more than `pass_below` cells the
+// stage only moves them to `dst`: so few long sub-cyclers finish sooner one
+// warp each than sharing warps.
+struct DrainStage {
+    QueueArrays src, dst;
+    int cnt, dst_cnt, budget;
+    long long pass_below;
+};
+
 template <int G, typename P, bool R32>
 __global__ void __launch_bounds__(128)
 thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
-             double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
+             double *T, P *N, P *F, int32_t *subcycles, Queue q, DrainStage ds, unsigned *status)
 {
-    unsigned long long count = q.counters[0];
+    unsigned long long count = q.counters[ds.cnt];
     if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
     if (count == 0) return;
+    if ((long long)count <= ds.pass_below) {
+        const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        for (long long it = gt; it < (long long)count; it += (long long)gridDim.x * blockDim.x) {
+            ds.dst.cell[it] = ds.src.cell[it];
+            ds.dst.t_left[it] = ds.src.t_left[it];
+            ds.dst.dt_tc[it] = ds.src.dt_tc[it];
+            ds.dst.attempts[it] = ds.src.attempts[it];
+        }
+        if (gt == 0) q.counters[ds.dst_cnt] = count;
+        return;
+    }
     CellState<G> st;
-    IsoRates iso;
-    CoolCache cc;
+    IsoRates<> iso;
+    CoolCache<> cc;
     double t_left = 0.0, dt_tc = 0.0, n = 0.0;
     int att = 0, used = 0;
     long long c = -1;
     bool have = false;
     auto fetch = [&]() {
-        unsigned long long it = atomicAdd(&q.counters[1], 1ULL);
+        unsigned long long it = atomicAdd(&q.counters[ds.cnt + 1], 1ULL);
         if (it < count) {
-            c = q.a.cell[it];
-            t_left = q.a.t_left[it];
-            dt_tc = q.a.dt_tc[it];
-            att = q.a.attempts[it];
+            c = ds.src.cell[it];
+            t_left = ds.src.t_left[it];
+            dt_tc = ds.src.dt_tc[it];
+            att = ds.src.attempts[it];
             n = nH[c];
             used = 0;
             load_cell<G, false, P, R32>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
@@ -410,11 +218,11 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             store_cell<G, P>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
             subcycles[c] = att;
             fetch();
-        } else if (++used >= kDrainBudget) {
-            // long sub-cycler: hand it to the warp-per-cell kernel
+        } else if (++used >= ds.budget) {
+            // long sub-cycler: hand it to the next stage
             store_cell<G, P>(p, c, xHII, xHeII, xHeIII, T, N, F, st, status);
-            unsigned long long slot = atomicAdd(&q.counters[2], 1ULL);
-            push_item(q.b, slot, q.capacity, (uint32_t)c, t_left, dt_tc, att, status);
+            unsigned long long slot = atomicAdd(&q.counters[ds.dst_cnt], 1ULL);
+            push_item(ds.dst, slot, q.capacity, (uint32_t)c, t_left, dt_tc, att, status);
             fetch();
         }
     }
@@ -425,23 +233,23 @@ __global__ void __launch_bounds__(128)
 thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
             double *T, P *N, P *F, int32_t *subcycles, Queue q, unsigned *status)
 {
-    unsigned long long count = q.counters[2];
+    unsigned long long count = q.counters[4];
     if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
     if (count == 0) return;
     const int lane = threadIdx.x & 31;
     while (true) {
         unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(&q.counters[3], 1ULL);
+        if (lane == 0) it = atomicAdd(&q.counters[5], 1ULL);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= count) break;
-        const long long c = q.b.cell[it];
-        double t_left = q.b.t_left[it];
-        double dt_tc = q.b.dt_tc[it];
-        int att = q.b.attempts[it];
+        const long long c = q.a.cell[it];
+        double t_left = q.a.t_left[it];
+        double dt_tc = q.a.dt_tc[it];
+        int att = q.a.attempts[it];
         const double n = nH[c];
         CellState<G> st;
-        IsoRates iso;
-        CoolCache cc;
+        IsoRates<> iso;
+        CoolCache<> cc;
         load_cell<G, true, P, R32>(p, c, xHII, xHeII, xHeIII, T, N, st, iso, cc);
         bool done = false;
         while (!done) {
@@ -479,15 +287,23 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     long long need = (tp.nc + 127) / 128;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
-    thermo_drain<G, P, R32><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     // one warp per long sub-cycler: two 4-warp blocks per SM
     long long hgrid = 2LL * n_sm;
     long long hneed = (tp.nc + 3) / 4;
     if (hgrid > hneed) hgrid = hneed;
     if (hgrid < 1) hgrid = 1;
+    if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
+    DrainStage d1{q.a, q.b, 0, 2, kDrainBudget, 0};
+    thermo_drain<G, P, R32><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, d1, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // many more long sub-cyclers than the warp-per-cell kernel has warps:
+    // they share the FP64 pipes anyway, so a lane per cell does more per
+    // cycle; up to twice its warps, the warps keep each cell's path short
+    DrainStage d2{q.b, q.a, 2, 4, kDrain2Budget, 8 * hgrid};
+    thermo_drain<G, P, R32><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, d2, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     thermo_hard<G, P, R32><<<(unsigned)hgrid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, sub, q, status);
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
@@ -545,7 +361,7 @@ namespace rtgb {
 namespace {
 
 constexpr long long kNoAllocMaxCells = 1LL << 18;   // 262144 cells
-// layout: [0,32) queue counters, [32,36) status; from byte 256 the two
+// layout: [0,64) queue counters, [64,68) status; from byte 256 the two
 // queues, each cell / attempts / t_left / dt_tc arrays of kNoAllocMaxCells
 constexpr size_t kNoAllocHeader = 256;
 constexpr size_t kNoAllocQueueBytes =
@@ -628,7 +444,7 @@ extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_o
     }
     Queue q{};
     q.counters = reinterpret_cast<unsigned long long *>(base);
-    unsigned *status = reinterpret_cast<unsigned *>(base + 32);
+    unsigned *status = reinterpret_cast<unsigned *>(base + 8 * kQueueCounters);
     const size_t K = (size_t)kNoAllocMaxCells;
     QueueArrays *qa[2] = {&q.a, &q.b};
     for (int k = 0; k < 2; ++k) {

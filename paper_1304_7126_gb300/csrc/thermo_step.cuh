@@ -1,0 +1,253 @@
+// One thermo_step of the per-cell thermochemistry (paper App. A) and one
+// attempt of its sub-cycling loop (Sec. 3.3.1), shared by the forward
+// kernels (thermo.cu) and the adjoint's differentiated recomputation
+// (adjoint.cu).  The scalar type S is double, or Dual for the adjoint.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dual.cuh"
+#include "rates.cuh"
+#include "rt_internal.h"
+
+namespace rtgb {
+namespace thermo_detail {
+
+constexpr double kEV = 1.602176634e-12;
+constexpr double kEps0 = 13.60 * kEV, kEps1 = 24.59 * kEV, kEps2 = 54.42 * kEV;
+constexpr double kFloorN = 1e-30;
+constexpr double kXMin = 1e-6;
+constexpr double kNeFloor = 1e-6;
+constexpr double kTFloor = 1.0;
+
+template <int G, typename S = double>
+struct CellState {
+    S x, y2, y3, T;
+    S N[G];
+    S Fs[G];          // accumulated flux scale prod 1/(1 + h D_i)
+};
+
+template <typename S = double>
+struct IsoRates {     // rates at the fixed temperature of an isothermal cell
+    HRatesT<S> h;
+    HeRatesT<S> he;
+};
+
+template <typename S = double>
+struct CoolCache {    // cooling L and dL/dT of the current state at t
+    S L, dL;
+    bool valid;
+};
+
+template <typename S>
+__device__ __forceinline__ S mu_of(double X, const S &x, const S &y2, const S &y3)
+{
+    return 1.0 / (X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3));
+}
+
+template <bool WARP, bool MIX>
+__device__ __forceinline__ void get_transc(const Dual &T, int case_b, unsigned need, TranscT<Dual> &t)
+{
+    static_assert(!WARP && !MIX, "dual rates: one thread, FP64");
+    transc_dual(T, case_b, need, t);
+}
+
+template <bool WARP, bool MIX>
+__device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, Transc &t)
+{
+    if (MIX) {
+        if (WARP) transc_warp_f(T, case_b, t);
+        else transc_serial_f(T, case_b, need, t);
+    } else {
+        if (WARP) transc_warp(T, case_b, t);
+        else transc_serial(T, case_b, need, t);
+    }
+}
+
+// One thermo_step over h.  Returns true and fills `o` and `maxrel` when the
+// 10% rule holds.  MIX (the RT_MIXED path): rates from FP32 transcendentals
+// and the photon update in FP32; T/mu, x_HII, helium and 1 - x stay FP64.
+//
+// S is double, or Dual for the adjoint's differentiated recomputation
+// (values bit-identical to the double path; MIX only with double).
+template <int G, bool WARP, bool MIX, typename S = double>
+__device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, const CellState<G, S> &s, double h,
+                                        const IsoRates<S> &iso, CoolCache<S> &cc, CellState<G, S> &o,
+                                        double &maxrel)
+{
+    static_assert(!MIX || sizeof(S) == sizeof(double), "the mixed path is not differentiated");
+    const S nHe = nH * p.he_ratio;
+    const S x = s.x, y2 = s.y2, y3 = s.y3;
+    const S nHI = nH * (1.0 - x);
+    const S nHII = nH * x;
+    const S nHeI = nHe * (1.0 - y2 - y3);
+    const S nHeII = nHe * y2;
+    const S nHeIII = nHe * y3;
+    const S ne = nHII + (y2 + 2.0 * y3) * nHe;
+    const double cr = p.cr;
+    S rel_max = 0.0;
+    S gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
+
+    // 1. photons
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        S Nn;
+        if constexpr (MIX) {
+            float D = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
+                                   (float)p.gc.sigN[i][2] * (float)nHeII);
+            float inv = 1.0f / (1.0f + (float)h * D);
+            float N0 = (float)s.N[i];
+            float Nf = N0 * inv;
+            float rel = fabsf(Nf - N0) / fmaxf(N0, (float)kFloorN);
+            if (rel > 0.1f) return false;
+            rel_max = fmax(rel_max, (double)rel);
+            Nn = Nf;
+            o.Fs[i] = (float)s.Fs[i] * inv;
+        } else {
+            S D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
+            S inv = 1.0 / (1.0 + h * D);
+            Nn = s.N[i] * inv;
+            S rel = fabs(Nn - s.N[i]) / fmax(s.N[i], kFloorN);
+            if (rel > 0.1) return false;
+            rel_max = fmax(rel_max, rel);
+            o.Fs[i] = s.Fs[i] * inv;
+        }
+        o.N[i] = Nn;
+        S crN = cr * Nn;
+        gam0 += p.gc.sigN[i][0] * crN;
+        gam1 += p.gc.sigN[i][1] * crN;
+        gam2 += p.gc.sigN[i][2] * crN;
+        if (!p.isothermal) {
+            heat += crN * (nHI * (p.gc.egy[i] * p.gc.sigE[i][0] - kEps0 * p.gc.sigN[i][0]) +
+                           nHeI * (p.gc.egy[i] * p.gc.sigE[i][1] - kEps1 * p.gc.sigN[i][1]) +
+                           nHeII * (p.gc.egy[i] * p.gc.sigE[i][2] - kEps2 * p.gc.sigN[i][2]));
+        }
+    }
+
+    // 2. temperature
+    const S mu = mu_of(p.X, x, y2, y3);
+    S Tmu1 = 0.0;
+    if (!p.isothermal) {
+        if (!cc.valid) {
+            TranscT<S> t;
+            get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
+            cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L,
+                         cc.dL);
+            cc.valid = true;
+        }
+        S lam = heat - cc.L;
+        S dlam = -mu * cc.dL;
+        S K = p.kfac / nH;
+        S Tmu = s.T / mu;
+        S dT = lam * K * h / (1.0 - dlam * K * h);
+        Tmu1 = Tmu + dT;
+        S rel = fabs(dT) / Tmu;
+        if (rel > 0.1) return false;
+        if (fabs(K * lam * h) / Tmu > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+    }
+
+    // 3. hydrogen
+    HRatesT<S> hr;
+    if (p.isothermal) {
+        hr = iso.h;
+    } else {
+        TranscT<S> t;
+        get_transc<WARP, MIX>(Tmu1 * mu, p.case_b, kNeedH, t);
+        h_rates_from(t, p.case_b, hr);
+    }
+    S C = hr.beta * ne + gam0;
+    S Dd = hr.alpha * ne;
+    S dC = nH * hr.beta, dD = nH * hr.alpha;
+    if (!p.isothermal) {
+        S f = ne * Tmu1 * mu * mu * p.X;
+        dC -= f * hr.dbeta;
+        dD -= f * hr.dalpha;
+    }
+    S J = dC - (C + Dd) - x * (dC + dD);
+    S xdot = C - x * (C + Dd);
+    S x1 = x + h * xdot / (1.0 - J * h);
+    x1 = fmin(fmax(x1, kXMin), 1.0);
+    {
+        S xden = fmax(x, kXMin);
+        S rel = fabs(x1 - x) / xden;
+        if (rel > 0.1) return false;
+        if (fabs(xdot) * h / xden > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+    }
+
+    // 4. helium
+    S y2n = y2, y3n = y3;
+    if (p.helium) {
+        S yI = 1.0 - y2 - y3;
+        S ne2 = x1 * nH + (y2 + 2.0 * y3) * nHe;
+        HeRatesT<S> r2;
+        if (p.isothermal) {
+            r2 = iso.he;
+        } else {
+            TranscT<S> t;
+            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
+            he_rates_from(t, p.case_b, r2);
+        }
+        S C1 = y2 * r2.alpha_HeII * ne2;
+        S D1 = r2.beta_HeI * ne2 + gam1;
+        S yI1 = (yI + C1 * h) / (1.0 + D1 * h);
+        S C2 = yI1 * (r2.beta_HeI * ne2 + gam1) + y3 * r2.alpha_HeIII * ne2;
+        S D2 = (r2.beta_HeII + r2.alpha_HeII) * ne2 + gam2;
+        y2n = (y2 + C2 * h) / (1.0 + D2 * h);
+        S ne3 = x1 * nH + (y2n + 2.0 * y3) * nHe;
+        HeRatesT<S> r3;
+        if (p.isothermal) {
+            r3 = iso.he;
+        } else {
+            TranscT<S> t;
+            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
+            he_rates_from(t, p.case_b, r3);
+        }
+        S C3 = y2n * (r3.beta_HeII * ne3 + gam2);
+        S D3 = r3.alpha_HeIII * ne3;
+        y3n = (y3 + C3 * h) / (1.0 + D3 * h);
+        // conservation: lower the largest fraction (HeI largest: no change)
+        if (y2n >= yI1 && y2n >= y3n) y2n = 1.0 - yI1 - y3n;
+        else if (y3n >= yI1 && y3n > y2n) y3n = 1.0 - yI1 - y2n;
+        y2n = fmin(fmax(y2n, 0.0), 1.0);
+        y3n = fmin(fmax(y3n, 0.0), 1.0);
+    }
+    {
+        S ne1 = x1 * nH + (y2n + 2.0 * y3n) * nHe;
+        S rel = fabs(ne1 - ne) / fmax(ne, kNeFloor * nH);
+        if (rel > 0.1) return false;
+        rel_max = fmax(rel_max, rel);
+    }
+    S Tf = p.isothermal ? s.T : Tmu1 * mu_of(p.X, x1, y2n, y3n);
+    o.x = x1;
+    o.y2 = y2n;
+    o.y3 = y3n;
+    o.T = fmax(Tf, kTFloor);
+    maxrel = val(rel_max);
+    return true;
+}
+
+// One attempt of the sub-cycling loop; returns true when the cell is done.
+template <int G, bool WARP, bool MIX, typename S = double>
+__device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH, CellState<G, S> &st,
+                                              double &t_left, double &dt_tc, int &att, const IsoRates<S> &iso,
+                                              CoolCache<S> &cc)
+{
+    double h = (dt_tc < t_left) ? dt_tc : t_left;
+    ++att;
+    CellState<G, S> o;
+    double mr = 0.0;
+    if (attempt<G, WARP, MIX, S>(p, nH, st, h, iso, cc, o, mr)) {
+        st = o;
+        cc.valid = false;
+        t_left = (h == t_left) ? 0.0 : t_left - h;
+        dt_tc = (mr < 0.05) ? 2.0 * h : h;
+    } else {
+        dt_tc = 0.5 * h;
+    }
+    return !(t_left > 0.0);
+}
+
+}  // namespace thermo_detail
+}  // namespace rtgb

@@ -76,6 +76,8 @@ def load(build: bool = True):
     L.rt_last_error.restype = C.c_char_p
     L.rt_hll_table.argtypes = [C.c_int, C.c_int, dp]
     L.rt_version.argtypes = []
+    L.rt_step_vjp.argtypes = [vp, C.c_double, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
+    L.rt_run_vjp.argtypes = [vp, C.c_double, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_thermo_step_noalloc.argtypes = [C.c_longlong, C.c_int, C.POINTER(rt_options), C.c_double, dp, dp,
                                          dp, C.c_double, dp, dp, dp, dp, dp, dp, dp, ip, vp]
     L.rt_thermo_step_noalloc.restype = C.c_int
@@ -263,6 +265,26 @@ class RT:
 
     def sync(self):
         self._check(self.L.rt_sync(self.h), "rt_sync")
+
+    LAM_KEYS = ("xHII", "xHeII", "xHeIII", "T", "N", "F")
+
+    def step_vjp(self, dt: float, lam: dict, g_nH, g_L=None, check: bool = False):
+        """rt_step_vjp: lam (CUDA float64 tensors keyed as LAM_KEYS) goes in
+        as dJ/dU_{k+1} and is overwritten with dJ/dU_k; g_nH and g_L
+        accumulate.  Returns the schedule-mismatch count when `check`."""
+        m = C.c_longlong(0)
+        args = [_ptr(lam[k]) for k in self.LAM_KEYS]
+        self._check(self.L.rt_step_vjp(self.h, float(dt), *args, _ptr(g_nH), _ptr(g_L),
+                                       C.byref(m) if check else None), "rt_step_vjp")
+        return m.value if check else None
+
+    def run_vjp(self, dt: float, nsteps: int, lam: dict, g_nH, g_L=None, check: bool = False):
+        """rt_run_vjp over nsteps steps from the current state."""
+        m = C.c_longlong(0)
+        args = [_ptr(lam[k]) for k in self.LAM_KEYS]
+        self._check(self.L.rt_run_vjp(self.h, float(dt), int(nsteps), *args, _ptr(g_nH), _ptr(g_L),
+                                      C.byref(m) if check else None), "rt_run_vjp")
+        return m.value if check else None
 
     @classmethod
     def from_workload(cls, w, **opts):
