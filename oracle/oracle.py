@@ -75,6 +75,7 @@ class OracleCfg(C.Structure):
         ("hll_nf", C.c_int), ("hll_nmu", C.c_int),
         ("nthreads", C.c_int),
         ("skip_thermo", C.c_int),
+        ("smooth", C.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ def lib():
             L.oracle_eddington.argtypes = [C.c_double, C.c_double, dp, dp, dp, dp]
             L.oracle_hll_lookup.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp]
             L.oracle_thermo_cell.argtypes = [C.POINTER(OracleCfg), C.c_double, C.c_double,
-                                             dp, dp, dp, C.c_int, C.POINTER(C.c_int), dp, dp]
+                                             dp, dp, dp, dp, dp, C.c_int, C.POINTER(C.c_int), dp, dp]
             L.oracle_courant_dt.argtypes = [C.c_double, C.c_double, C.c_double]
             L.oracle_courant_dt.restype = C.c_double
             L.oracle_step.argtypes = [C.POINTER(OracleCfg), C.c_double, dp, dp, dp, dp, dp, dp, dp,
@@ -149,7 +150,7 @@ class Problem:
 
     def __init__(self, shape, dx, G, cr, sigN, sigE, egy, X=1.0, isothermal=False,
                  otsa=True, flux=GLF, bc=(0, 0, 0, 0, 0, 0), a_exp=1.0,
-                 max_subcycles=1_000_000, hll_table=None, nthreads=1, skip_thermo=False):
+                 max_subcycles=1_000_000, hll_table=None, nthreads=1, skip_thermo=False, smooth=False):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.G = int(G)
@@ -181,6 +182,7 @@ class Problem:
         cfg.hll_nf, cfg.hll_nmu = self._tab.shape[0], self._tab.shape[1]
         cfg.nthreads = int(nthreads)
         cfg.skip_thermo = int(bool(skip_thermo))
+        cfg.smooth = int(bool(smooth))
         self.cfg = cfg
 
     @property
@@ -219,17 +221,21 @@ class Problem:
             sub.ctypes.data_as(C.POINTER(C.c_int32)), _dp(mg))
         return st, budget, sub.reshape(self.shape), mg.reshape(self.shape)
 
-    def thermo_cell(self, dt: float, nH: float, s, N, F, fixed_photons=False):
+    def thermo_cell(self, dt: float, nH: float, s, N, F, fixed_photons=False, Ndot=None, Fdot=None):
         """Sub-cycle one cell over dt.  s = [x_HII, x_HeII, x_HeIII, T];
-        N [G]; F [G][3].  Returns (status, s, N, F, attempts, absorbed, margin)."""
+        N [G]; F [G][3]; Ndot [G], Fdot [G][3]: smoothed-RT rates (Sec. 3.4)
+        or None.  Returns (status, s, N, F, attempts, absorbed, margin)."""
         s = np.array(s, dtype=np.float64)
         N = np.array(N, dtype=np.float64).reshape(self.G)
         F = np.array(F, dtype=np.float64).reshape(self.G, 3).copy()
         att = C.c_int(0)
         ab = np.zeros(self.G)
         mg = np.zeros(1)
+        nd = None if Ndot is None else np.ascontiguousarray(Ndot, dtype=np.float64).reshape(self.G)
+        fd = None if Fdot is None else np.ascontiguousarray(Fdot, dtype=np.float64).reshape(self.G, 3)
         st = lib().oracle_thermo_cell(C.byref(self.cfg), float(dt), float(nH), _dp(s), _dp(N),
-                                      _dp(F), int(bool(fixed_photons)), C.byref(att), _dp(ab), _dp(mg))
+                                      _dp(F), None if nd is None else _dp(nd), None if fd is None else _dp(fd),
+                                      int(bool(fixed_photons)), C.byref(att), _dp(ab), _dp(mg))
         return st, s, N, F, att.value, ab, float(mg[0])
 
 

@@ -17,6 +17,8 @@
  *                    (xhei_update), (xheii_update), (xheiii_update)
  *   10% rule         Sec. 3.3.1 and App. A, task 5
  *   OTSA             Sec. 3.3.2 (case B rates, no recombination photons)
+ *   smoothed RT      Sec. 3.4, Eqs. (thchem_N_smooth), (thchem_F_smooth),
+ *                    (smoothrate1), (smoothrate2); App. A Eq. (SIE photons)
  *   Courant step     Sec. 4.1, Eq. (dt_courant)
  *   rate fits        appendix "Interaction rate coefficients"
  *
@@ -461,6 +463,7 @@ static void note_margin(double v, double thr, double *margin)
  * n_e).  Returns 0 if the 10% rule is broken (caller halves h). */
 static int thermo_step(const oracle_cfg *cfg, double h, double nH,
                        const double *s0 /* x, y2, y3, T */, const double *N0,
+                       const double *Ndot /* smoothed RT rates, or NULL */,
                        double *s1, double *N1, double *Fscale, double *absorbed,
                        double *maxrel, double *margin, int fixed_photons)
 {
@@ -490,7 +493,9 @@ static int thermo_step(const oracle_cfg *cfg, double h, double nH,
             absorbed[i] = 0.0;
             continue;
         }
-        N1[i] = N0[i] / (1.0 + h * Di);
+        /* smoothed RT: the transport and injection change of the RT step
+         * enters as the rate Ndot_i, Eq. (SIE photons) with Ndot_i + C_i */
+        N1[i] = Ndot ? (N0[i] + h * Ndot[i]) / (1.0 + h * Di) : N0[i] / (1.0 + h * Di);
         Fscale[i] = 1.0 / (1.0 + h * Di);
         double rel = fabs(N1[i] - N0[i]) / fmax(N0[i], FLOOR_N);
         note_margin(rel, 0.1, margin);
@@ -643,7 +648,8 @@ static int thermo_step(const oracle_cfg *cfg, double h, double nH,
  * task 5: first try dt_TC = dt_rt; halve and redo on a broken 10% rule;
  * double the next dt_TC after a sub-step whose largest change is < 5%. */
 int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s,
-                       double *N, double *F /* [G][3] */, int fixed_photons,
+                       double *N, double *F /* [G][3] */, const double *Ndot /* [G] or NULL */,
+                       const double *Fdot /* [G][3] or NULL */, int fixed_photons,
                        int *attempts_out, double *absorbed_out, double *margin_out)
 {
     const int G = cfg->G;
@@ -658,14 +664,19 @@ int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s
         double h = (dt_tc < t_left) ? dt_tc : t_left;
         double maxrel = 0.0;
         attempts++;
-        int ok = thermo_step(cfg, h, nH, s, N, s1, N1, Fs, ab, &maxrel, &margin, fixed_photons);
+        int ok = thermo_step(cfg, h, nH, s, N, Ndot, s1, N1, Fs, ab, &maxrel, &margin, fixed_photons);
         if (!ok) { dt_tc = 0.5 * h; continue; }
         for (int q = 0; q < 4; q++) s[q] = s1[q];
         for (int i = 0; i < G; i++) {
             N[i] = N1[i];
-            F[3 * i + 0] *= Fs[i];
-            F[3 * i + 1] *= Fs[i];
-            F[3 * i + 2] *= Fs[i];
+            if (Fdot) {
+                /* Eq. (SIE photons) for F with the rate Fdot_i */
+                for (int d = 0; d < 3; d++) F[3 * i + d] = (F[3 * i + d] + h * Fdot[3 * i + d]) * Fs[i];
+            } else {
+                F[3 * i + 0] *= Fs[i];
+                F[3 * i + 1] *= Fs[i];
+                F[3 * i + 2] *= Fs[i];
+            }
             absorbed_out[i] += ab[i];
         }
         t_left = (h == t_left) ? 0.0 : t_left - h;
@@ -697,6 +708,17 @@ int oracle_step(const oracle_cfg *cfg, double dt, const double *nH, double *xHII
     if (G < 1 || G > ORACLE_MAXG) return ORACLE_EINVAL;
     for (int i = 0; i < 4 * G; i++) budget[i] = 0.0;
 
+    /* smoothed RT (Sec. 3.4): keep the state before injection and transport;
+     * their result only defines the rates Ndot, Fdot of Eqs. (smoothrate1),
+     * (smoothrate2), and the thermochemistry starts from the kept state */
+    double *N0 = NULL, *F0 = NULL;
+    if (cfg->smooth && !cfg->skip_thermo) {
+        N0 = (double *)malloc(sizeof(double) * nc * G);
+        F0 = (double *)malloc(sizeof(double) * nc * 3 * G);
+        memcpy(N0, N, sizeof(double) * nc * G);
+        memcpy(F0, F, sizeof(double) * nc * 3 * G);
+    }
+
     /* 1. injection, Eq. (injnum) with point sources of fixed luminosity */
     for (int s = 0; s < nsrc; s++) {
         size_t c = cidx(cfg, src_ijk[3 * s], src_ijk[3 * s + 1], src_ijk[3 * s + 2]);
@@ -718,13 +740,24 @@ int oracle_step(const oracle_cfg *cfg, double dt, const double *nH, double *xHII
         for (long c = 0; c < (long)nc; c++) {
             double s[4] = {xHII[c], xHeII[c], xHeIII[c], T[c]};
             double Nc[ORACLE_MAXG], Fc[3 * ORACLE_MAXG], ab[ORACLE_MAXG];
+            double Nd[ORACLE_MAXG], Fd[3 * ORACLE_MAXG];
             for (int i = 0; i < G; i++) {
                 Nc[i] = N[(size_t)i * nc + c];
                 for (int d = 0; d < 3; d++) Fc[3 * i + d] = F[((size_t)3 * i + d) * nc + c];
+                if (N0) {
+                    Nd[i] = (Nc[i] - N0[(size_t)i * nc + c]) / dt;
+                    Nc[i] = N0[(size_t)i * nc + c];
+                    for (int d = 0; d < 3; d++) {
+                        double f0 = F0[((size_t)3 * i + d) * nc + c];
+                        Fd[3 * i + d] = (Fc[3 * i + d] - f0) / dt;
+                        Fc[3 * i + d] = f0;
+                    }
+                }
             }
             int att = 0;
             double mg = 0.0;
-            int st = oracle_thermo_cell(cfg, dt, nH[c], s, Nc, Fc, 0, &att, ab, &mg);
+            int st = oracle_thermo_cell(cfg, dt, nH[c], s, Nc, Fc, N0 ? Nd : NULL, N0 ? Fd : NULL, 0, &att, ab,
+                                        &mg);
             if (st) bad = 1;
             xHII[c] = s[0]; xHeII[c] = s[1]; xHeIII[c] = s[2]; T[c] = s[3];
             for (int i = 0; i < G; i++) {
@@ -736,6 +769,8 @@ int oracle_step(const oracle_cfg *cfg, double dt, const double *nH, double *xHII
             if (margins) margins[c] = mg;
         }
         if (bad) status = ORACLE_ESUBCYCLE;
+        free(N0);
+        free(F0);
         for (int i = 0; i < G; i++) {
             double a = 0.0;
             for (size_t c = 0; c < nc; c++) a += absorbed[(size_t)i * nc + c];

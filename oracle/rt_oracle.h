@@ -42,6 +42,7 @@ typedef struct {
     int hll_nf, hll_nmu;
     int nthreads;           /* OpenMP threads over cells (<=1: serial) */
     int skip_thermo;        /* transport-only tests */
+    int smooth;             /* smoothed RT, Sec. 3.4 */
 } oracle_cfg;
 
 void oracle_rates(double T, double a_exp, int case_b, double *r, double *dr);
@@ -51,8 +52,9 @@ void oracle_eddington(double c, double N, const double F[3], double D[9],
 void oracle_hll_lookup(const double *tab, int nf, int nmu, double f, double mu,
                        double *lmin, double *lmax);
 int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s,
-                       double *N, double *F, int fixed_photons, int *attempts_out,
-                       double *absorbed_out, double *margin_out);
+                       double *N, double *F, const double *Ndot, const double *Fdot,
+                       int fixed_photons, int *attempts_out, double *absorbed_out,
+                       double *margin_out);
 double oracle_courant_dt(double cfl, double dx, double cr);
 int oracle_step(const oracle_cfg *cfg, double dt, const double *nH, double *xHII,
                 double *xHeII, double *xHeIII, double *T, double *N, double *F,
