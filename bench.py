@@ -211,6 +211,13 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip timing the RT_MIXED variants")
     ap.add_argument("--no-batched", action="store_true", help="skip timing the batched-boxes variant")
     ap.add_argument("--batched-boxes", type=int, default=512)
+    ap.add_argument("--no-c3", action="store_true", help="skip the 256^3 precision comparison")
+    ap.add_argument("--smooth", action="store_true",
+                    help="also time smoothed RT (Sec. 3.4); off by default: on this workload cells whose net "
+                         "outflow rate and absorption empty them within a step sub-cycle without end under the "
+                         "10%% rule with its 1e-30 floor")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip timing the adjoint")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -338,10 +345,13 @@ def main():
         e2e = {"value": units / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "how": "per step: rt_set_state from pinned host buffers, rt_step, rt_get_state to pinned host"}
 
-    # ---- the mixed-precision variant (FP32 transport, FP32 rates, FP64 stiff updates) ----
+    # ---- variants on the same workload: RT_MIXED, RT_MIXED32 and smoothed RT (Sec. 3.4) ----
     variants = {}
-    for vname, vprec in (() if args.no_mixed else (("mixed", R.RT_MIXED), ("mixed32", R.RT_MIXED32))):
-        simm = R.RT.from_workload(w, precision=vprec)
+    vlist = [] if args.no_mixed else [("mixed", R.RT_MIXED, 0), ("mixed32", R.RT_MIXED32, 0)]
+    if args.smooth:
+        vlist += [("smoothed", R.RT_FP64, 1), ("smoothed_mixed32", R.RT_MIXED32, 1)]
+    for vname, vprec, vsmooth in vlist:
+        simm = R.RT.from_workload(w, precision=vprec, smooth=vsmooth)
         simm.set_stream(stream.cuda_stream)
         simm.run(dt, max(args.warmup, 3))
         simm.sync()
@@ -360,11 +370,13 @@ def main():
             simm.step(dt)
         pm = simm.profile()
         simm.set_profiling(False)
+        subm = simm.subcycles()
         tr_ms = pm["transport"][0] / max(pm["transport"][1], 1)
         alg32 = 32.0 * cg
         ach32 = alg32 / (tr_ms / 1e3) / 1e9
         variants[vname] = {
             "value": units / tm, "ms_per_step": 1e3 * tm / args.steps, "speedup_vs_fp64": t / tm,
+            "smoothed_rt": bool(vsmooth), "last_step_attempts": {"total": int(subm.sum()), "max": int(subm.max())},
             "phases_ms_per_launch": {k: round(v[0] / v[1], 5) if v[1] else None for k, v in pm.items()},
             "transport_roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm_peak, "unit": "GB/s",
                                    "frac": ach32 / hbm_peak, "algorithmic_bytes_per_launch": alg32}}
@@ -399,6 +411,86 @@ def main():
             "workload": "%d boxes, side in {16,24,32,48,64}, 1 or 3 groups, HLL, c_r=c/100" % len(boxes)}
         bt.close()
         del boxes
+
+    # ---- 256^3 (seed 11, 64 sources): FP64, RT_MIXED and RT_MIXED32 from the
+    # same state, per-field error of the reduced-precision states against FP64 ----
+    if not args.no_c3:
+        from paper_1304_7126_gb300 import workloads as W
+        w3 = W.cosmo256()
+        k3 = min(args.steps, w3.steps)
+        init3 = {k: torch.from_numpy(v).cuda() for k, v in w3.state().items()}
+        cg3 = w3.ncells * w3.G
+        res, fin = {}, {}
+        for name, prec in (("fp64", R.RT_FP64), ("mixed", R.RT_MIXED), ("mixed32", R.RT_MIXED32)):
+            s3 = R.RT.from_workload(w3, precision=prec)
+            s3.set_stream(stream.cuda_stream)
+            dt3 = s3.courant_dt()
+            s3.run(dt3, 3)
+            s3.set_state(init3)
+            s3.sync()
+            barrier()
+            ev0.record(stream)
+            s3.run(dt3, k3)
+            ev1.record(stream)
+            ev1.synchronize()
+            s3.sync()
+            t3 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+            fin[name] = s3.get_state(device=True)
+            res[name] = {"value": cg3 * k3 * ws / t3, "ms_per_step": 1e3 * t3 / k3}
+            s3.close()
+        ref = fin["fp64"]
+        nmax = float(ref["N"].abs().max())
+        for name in ("mixed", "mixed32"):
+            g = fin[name]
+            res[name]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res[name]["ms_per_step"]
+            res[name]["error_vs_fp64_gpu"] = {
+                "xHII_abs": float((g["xHII"] - ref["xHII"]).abs().max()),
+                "xHeII_abs": float((g["xHeII"] - ref["xHeII"]).abs().max()),
+                "xHeIII_abs": float((g["xHeIII"] - ref["xHeIII"]).abs().max()),
+                "T_rel": float(((g["T"] - ref["T"]).abs() / ref["T"]).max()),
+                "N_rel": float(((g["N"] - ref["N"]).abs() / ref["N"].abs().clamp_min(1e-6 * nmax)).max())}
+        variants["cosmo256"] = {"steps": k3, "cell_groups": cg3,
+                                "workload": "256^3, 3 groups, seed 11, 64 sources of 1e52/s, HLL, c_r=c/10",
+                                "tolerance": {"x_abs": 1e-4, "T_rel": 1e-3, "N_rel": 1e-4}, **res}
+        del fin, ref, init3
+
+    # ---- adjoint: 64^3, 3 groups, 8 sources, GLF, FP64; forward with a checkpoint
+    # every 20 steps, then the backward pass (recompute + hand-written VJPs) ----
+    if not args.no_adjoint:
+        from paper_1304_7126_gb300 import adjoint as A
+        from paper_1304_7126_gb300 import workloads as W
+        w5 = W.adjoint64()
+        k5 = args.adjoint_steps
+        s5 = R.RT.from_workload(w5)
+        dt5 = s5.courant_dt()
+        st5 = {k: torch.from_numpy(v).cuda() for k, v in w5.state().items()}
+        Ld = torch.from_numpy(w5.src_L).cuda()
+
+        def fwd_bwd(k):
+            nH = st5["nH"].clone().requires_grad_(True)
+            L = Ld.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            out = A.run(s5, dt5, k, w5.src_ijk, nH, L, st5, every=20)
+            loss = A.neutral_hydrogen_mass(out, w5.dx)
+            e1.record()
+            loss.backward()
+            e2.record()
+            e2.synchronize()
+            return e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3, nH.grad, L.grad
+
+        fwd_bwd(3)
+        barrier()
+        tf, tb, gnh, gl = fwd_bwd(k5)
+        tf, tb = max_over_ranks(tf), max_over_ranks(tb)
+        cg5 = w5.ncells * w5.G
+        variants["adjoint64"] = {
+            "value": cg5 * k5 * ws / (tf + tb), "unit": UNIT + " (forward + backward)", "steps": k5,
+            "checkpoint_every": 20, "forward_s": tf, "backward_s": tb, "backward_over_forward": tb / tf,
+            "grad_L_per_source": (gl * (Ld / Ld.sum(dim=1, keepdim=True))).sum(dim=1).tolist(),
+            "grad_nH_abs_max": float(gnh.abs().max()),
+            "workload": "64^3, 3 groups, H+He, seed 7, 8 sources of 1e52/s, GLF, FP64; d M_HI / d(n_H, L)"}
+        s5.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -43,13 +43,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP over cells is its only parallelism)."""
+    """Compile the oracle with gcc (OpenMP over cells is its only parallelism).
+    -ffp-contract=off: every operation is rounded on its own, as written, so
+    the oracle gives the same bits on every host (x86 and Arm alike)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "rt_oracle.h"))
+        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "rt_oracle.h")), os.path.getmtime(__file__)
     ):
         tmp = LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(
-            ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+            ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
         )
         os.replace(tmp, LIB)
     return LIB

@@ -313,11 +313,11 @@ int enqueue_batch_step(rt_batch *b, double dt)
         ThermoParams tp = class_params(b, c, dt);
         if (f32)
             e = launch_thermo_mixed(tp, c.G, b->opt.precision == RT_MIXED32, c.nH, c.xHII, c.xHeII, c.xHeIII, c.T,
-                                    (float *)c.N[b->cur], (float *)c.F[b->cur], c.sub, c.q, b->status, b->n_sm,
-                                    b->stream);
+                                    (float *)c.N[b->cur], (float *)c.F[b->cur], nullptr, nullptr, c.sub, c.q,
+                                    b->status, b->n_sm, b->stream);
         else
             e = launch_thermo(tp, c.G, c.nH, c.xHII, c.xHeII, c.xHeIII, c.T, (double *)c.N[b->cur],
-                              (double *)c.F[b->cur], c.sub, c.q, b->status, b->n_sm, b->stream);
+                              (double *)c.F[b->cur], nullptr, nullptr, c.sub, c.q, b->status, b->n_sm, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "thermo");
         reset_counters_kernel<<<1, 32, 0, b->stream>>>(c.q.counters, kQueueCounters);
     }

@@ -32,6 +32,7 @@ struct rt_handle {
     double *F[2] = {nullptr, nullptr};
     float *Nf[2] = {nullptr, nullptr};   // RT_MIXED photon state
     float *Ff[2] = {nullptr, nullptr};
+    void *Npre = nullptr, *Fpre = nullptr;   // smoothed RT: photon state before injection
     bool mixed = false;
     int cur = 0;
     double *hll = nullptr;
@@ -121,7 +122,7 @@ void free_all(rt_handle *h)
     void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
                     h->Nf[0], h->Nf[1], h->Ff[0], h->Ff[1], h->hllf, h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
                     h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
-                    h->budget, h->status, h->src_cell, h->src_L, h->src_cell_orig, h->adj, h->adj_sub,
+                    h->budget, h->status, h->src_cell, h->src_L, h->src_cell_orig, h->adj, h->adj_sub, h->Npre, h->Fpre,
                     h->adj_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -192,6 +193,16 @@ int enqueue_step(rt_handle *h, double dt, bool capturing = false)
     const long long nc = h->g.nc;
     const double V = h->g.dx * h->g.dx * h->g.dx;
     cudaError_t e;
+    if (h->opt.smooth) {
+        // smoothed RT (Sec. 3.4): keep the state before injection and transport
+        const size_t es = h->mixed ? sizeof(float) : sizeof(double);
+        const void *n0 = h->mixed ? (const void *)h->Nf[h->cur] : (const void *)h->N[h->cur];
+        const void *f0 = h->mixed ? (const void *)h->Ff[h->cur] : (const void *)h->F[h->cur];
+        e = cudaMemcpyAsync(h->Npre, n0, es * h->G * nc, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->Fpre, f0, es * 3 * h->G * nc, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "smoothing copy");
+    }
     if (h->nsrc > 0) {
         if (prof) { prof_pair(h, 0, &a, &b); cudaEventRecord(a, h->stream); }
         if (h->mixed) e = launch_inject_f32(h->nsrc, h->G, nc, h->src_cell, h->src_L, dt / V, h->Nf[h->cur], h->stream);
@@ -217,12 +228,13 @@ int enqueue_step(rt_handle *h, double dt, bool capturing = false)
         prof_pair(h, 3, &tev[2], &tev[3]);
     }
     if (h->mixed)
-        e = launch_thermo_mixed(tp, h->G, h->opt.precision == RT_MIXED32, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->Nf[h->cur],
-                                h->Ff[h->cur], h->subcycles, h->q, h->status, h->n_sm, h->stream,
-                                prof ? tev : nullptr);
+        e = launch_thermo_mixed(tp, h->G, h->opt.precision == RT_MIXED32, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T,
+                                h->Nf[h->cur], h->Ff[h->cur], (float *)h->Npre, (float *)h->Fpre, h->subcycles, h->q,
+                                h->status, h->n_sm, h->stream, prof ? tev : nullptr);
     else
         e = launch_thermo(tp, h->G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[h->cur], h->F[h->cur],
-                          h->subcycles, h->q, h->status, h->n_sm, h->stream, prof ? tev : nullptr);
+                          (double *)h->Npre, (double *)h->Fpre, h->subcycles, h->q, h->status, h->n_sm, h->stream,
+                          prof ? tev : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "thermo");
     if (prof) { prof_pair(h, 4, &a, &b); cudaEventRecord(a, h->stream); }
     e = h->mixed ? launch_reduce_N_f32(h->G, nc, h->Nf[h->cur], h->part, h->stream)
@@ -313,7 +325,8 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
         RT_CUDA(h, cudaMemcpyAsync(gy2, h->xHeII, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RT_CUDA(h, cudaMemcpyAsync(gy3, h->xHeIII, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RT_CUDA(h, cudaMemcpyAsync(gT, h->T, nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        e = launch_thermo(tp, G, h->nH, gx, gy2, gy3, gT, NB, FB, h->adj_sub + nc, h->q, h->status, h->n_sm, st);
+        e = launch_thermo(tp, G, h->nH, gx, gy2, gy3, gT, NB, FB, nullptr, nullptr, h->adj_sub + nc, h->q, h->status,
+                          h->n_sm, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "thermo");
         RT_CUDA(h, cudaMemsetAsync(h->q.counters, 0, kQueueCounters * sizeof(unsigned long long), st));
         e = launch_count_mismatch(nc, h->adj_sub, h->adj_sub + nc, h->adj_count, st);
@@ -325,8 +338,8 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
 int vjp_args(rt_handle *h, double *dt, double *lx, double *ly2, double *ly3, double *lT, double *lN, double *lF,
              double *g_nH, double *g_L)
 {
-    if (h->opt.precision != RT_FP64 || h->opt.flux != RT_GLF)
-        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64 and flux RT_GLF");
+    if (h->opt.precision != RT_FP64 || h->opt.flux != RT_GLF || h->opt.smooth)
+        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64, flux RT_GLF and no smoothing");
     if (!lx || !ly2 || !ly3 || !lT || !lN || !lF || !g_nH || (h->nsrc_orig > 0 && !g_L))
         return fail(h, RT_EINVAL, "null adjoint array");
     return check_dt(h, dt);
@@ -378,7 +391,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     if (!(opt->X > 0.0 && opt->X <= 1.0)) return RT_EINVAL;
     if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return RT_EINVAL;
     if (opt->flux != RT_GLF && opt->flux != RT_HLL) return RT_EINVAL;
-    if (opt->otsa != 1 || opt->smooth != 0) return RT_EINVAL;
+    if (opt->otsa != 1 || (opt->smooth != 0 && opt->smooth != 1)) return RT_EINVAL;
     if (opt->precision != RT_FP64 && opt->precision != RT_MIXED && opt->precision != RT_MIXED32) return RT_EINVAL;
     if (!(opt->a_exp > 0.0) || opt->max_subcycles < 1) return RT_EINVAL;
     for (int i = 0; i < 3 * n_groups; ++i)
@@ -442,6 +455,13 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
                 if ((rc = dalloc(h, &h->N[k], G * nc)) || (rc = dalloc(h, &h->F[k], 3 * G * nc))) goto bad;
                 cudaMemset(h->N[k], 0, G * nc * sizeof(double));
                 cudaMemset(h->F[k], 0, 3 * G * nc * sizeof(double));
+            }
+        }
+        if (opt->smooth) {
+            const size_t es = h->mixed ? sizeof(float) : sizeof(double);
+            if ((e = cudaMalloc(&h->Npre, es * G * nc)) != cudaSuccess ||
+                (e = cudaMalloc(&h->Fpre, es * 3 * G * nc)) != cudaSuccess) {
+                rc = fail(h, RT_ENOMEM, "cudaMalloc"); goto bad;
             }
         }
         h->q.capacity = nc;

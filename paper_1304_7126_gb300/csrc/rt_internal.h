@@ -115,18 +115,24 @@ cudaError_t launch_transport_batch(const BatchItem *items, const BatchBox *boxes
 void transport_init();   // kernel attributes; called once per handle
 
 // ev (optional, 4 events): recorded around the first pass (0, 1) and
-// around the queue drains (2, 3).
+// around the queue drains (2, 3).  Npre, Fpre: NULL, or smoothed RT (Sec.
+// 3.4): the photon state before injection and transport, N, F the state
+// after them; both pairs are overwritten.
 cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, double *xHII,
                           double *xHeII, double *xHeIII, double *T, double *N, double *F,
-                          int32_t *subcycles, Queue q, unsigned *status, int n_sm,
-                          cudaStream_t s, cudaEvent_t *ev = nullptr);
+                          double *Npre, double *Fpre, int32_t *subcycles, Queue q, unsigned *status,
+                          int n_sm, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // FP32 photon state (RT_MIXED: FP64 thermochemistry; RT_MIXED32, rates32:
-// FP32 rate transcendentals and photon update, FP64 stiff x/T updates).
+// FP32 rate transcendentals and absorption coefficients, FP64 updates).
 cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, bool rates32, const double *nH, double *xHII,
-                                double *xHeII, double *xHeIII, double *T, float *N, float *F,
-                                int32_t *subcycles, Queue q, unsigned *status, int n_sm,
+                                double *xHeII, double *xHeIII, double *T, float *N, float *F, float *Npre,
+                                float *Fpre, int32_t *subcycles, Queue q, unsigned *status, int n_sm,
                                 cudaStream_t s, cudaEvent_t *ev = nullptr);
+cudaError_t launch_thermo_mixed32(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
+                                  double *xHeIII, double *T, float *N, float *F, float *Npre, float *Fpre,
+                                  int32_t *subcycles, Queue q, unsigned *status, int n_sm, cudaStream_t s,
+                                  cudaEvent_t *ev = nullptr);
 
 cudaError_t launch_inject(int nsrc, int G, long long nc, const long long *cells,
                           const double *Lsum, double dt_over_V, double *N, cudaStream_t s);

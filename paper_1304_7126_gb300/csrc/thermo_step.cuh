@@ -25,6 +25,8 @@ struct CellState {
     S x, y2, y3, T;
     S N[G];
     S Fs[G];          // accumulated flux scale prod 1/(1 + h D_i)
+    S Nd[G];          // smoothed RT: photon density rate Ndot_i (Sec. 3.4)
+    S Fb[G];          // smoothed RT: weight of Fdot_i in F, sum h prod 1/(1 + h D_i)
 };
 
 template <typename S = double>
@@ -39,10 +41,42 @@ struct CoolCache {    // cooling L and dL/dT of the current state at t
     bool valid;
 };
 
+// 1/mu, mu the mean particle mass in m_H (App. A)
+template <typename S>
+__device__ __forceinline__ S mu_den(double X, const S &x, const S &y2, const S &y3)
+{
+    return X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3);
+}
+
 template <typename S>
 __device__ __forceinline__ S mu_of(double X, const S &x, const S &y2, const S &y3)
 {
-    return 1.0 / (X * (1.0 + x) + 0.25 * (1.0 - X) * (1.0 + y2 + 2.0 * y3));
+    return 1.0 / mu_den(X, x, y2, y3);
+}
+
+// fl(a / b) > t and fl(a / b) < t (a >= 0, b > 0), decided exactly as the
+// rounded quotient would decide them: the product t b settles everything
+// outside a band of a few ulps around the threshold, where the quotient
+// itself is formed.  The 10% rule's decisions thus match a statement of it
+// that divides, including at exact ties (a sub-cycled cell whose photon
+// density grows linearly from zero meets relative changes of exactly 1/10
+// and 1/20).
+template <typename S>
+__device__ __forceinline__ bool ratio_gt(const S &a, const S &b, double t)
+{
+    const S tb = t * b;
+    if (a > tb * (1.0 + 1e-15)) return true;
+    if (a < tb * (1.0 - 1e-15)) return false;
+    return a / b > t;
+}
+
+template <typename S>
+__device__ __forceinline__ bool ratio_lt(const S &a, const S &b, double t)
+{
+    const S tb = t * b;
+    if (a < tb * (1.0 - 1e-15)) return true;
+    if (a > tb * (1.0 + 1e-15)) return false;
+    return a / b < t;
 }
 
 template <bool WARP, bool MIX>
@@ -64,16 +98,19 @@ __device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, 
     }
 }
 
-// One thermo_step over h.  Returns true and fills `o` and `maxrel` when the
-// 10% rule holds.  MIX (the RT_MIXED path): rates from FP32 transcendentals
-// and the photon update in FP32; T/mu, x_HII, helium and 1 - x stay FP64.
+// One thermo_step over h.  Returns true and fills `o` when the 10% rule
+// holds; `small` then tells whether every checked change stayed below 5%.
+// The checks |dX| / den > 0.1 go through ratio_gt / ratio_lt (a division
+// only near the threshold).
+// MIX (RT_MIXED32): rate transcendentals and absorption coefficients in
+// FP32; the photon, T/mu, x_HII and helium updates and 1 - x in FP64.
 //
 // S is double, or Dual for the adjoint's differentiated recomputation
 // (values bit-identical to the double path; MIX only with double).
-template <int G, bool WARP, bool MIX, typename S = double>
+template <int G, bool WARP, bool MIX, typename S = double, bool SM = false>
 __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, const CellState<G, S> &s, double h,
                                         const IsoRates<S> &iso, CoolCache<S> &cc, CellState<G, S> &o,
-                                        double &maxrel)
+                                        bool &small)
 {
     static_assert(!MIX || sizeof(S) == sizeof(double), "the mixed path is not differentiated");
     const S nHe = nH * p.he_ratio;
@@ -85,7 +122,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     const S nHeIII = nHe * y3;
     const S ne = nHII + (y2 + 2.0 * y3) * nHe;
     const double cr = p.cr;
-    S rel_max = 0.0;
+    bool sm = true;
     S gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
 
     // 1. photons
@@ -93,26 +130,35 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     for (int i = 0; i < G; ++i) {
         S Nn;
         if constexpr (MIX) {
-            float D = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
-                                   (float)p.gc.sigN[i][2] * (float)nHeII);
-            float inv = 1.0f / (1.0f + (float)h * D);
-            float N0 = (float)s.N[i];
-            float Nf = N0 * inv;
-            float rel = fabsf(Nf - N0) / fmaxf(N0, (float)kFloorN);
-            if (rel > 0.1f) return false;
-            rel_max = fmax(rel_max, (double)rel);
-            Nn = Nf;
-            o.Fs[i] = (float)s.Fs[i] * inv;
+            // absorption coefficient in FP32; the update itself in FP64, since
+            // a cell may take thousands of sub-steps and FP32 roundings of
+            // N would accumulate past the stated 1e-4
+            float Df = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
+                                    (float)p.gc.sigN[i][2] * (float)nHeII);
+            double inv = 1.0 / (1.0 + h * (double)Df);
+            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i])) * inv;
+            else Nn = s.N[i] * inv;
+            double dN = fabs(Nn - s.N[i]), den = fmax(s.N[i], kFloorN);
+            if (ratio_gt(dN, den, 0.1)) return false;
+            sm = sm && ratio_lt(dN, den, 0.05);
+            o.Fs[i] = s.Fs[i] * inv;
+            if constexpr (SM) o.Fb[i] = (s.Fb[i] + h) * inv;
         } else {
             S D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
             S inv = 1.0 / (1.0 + h * D);
-            Nn = s.N[i] * inv;
-            S rel = fabs(Nn - s.N[i]) / fmax(s.N[i], kFloorN);
-            if (rel > 0.1) return false;
-            rel_max = fmax(rel_max, rel);
+            // smoothed RT: Eq. (SIE photons) with the rate Ndot_i; N + h Ndot
+            // rounded step by step (no fused multiply-add), so a cell growing
+            // linearly from zero meets its relative changes 1/k exactly
+            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i])) * inv;
+            else Nn = s.N[i] * inv;
+            S dN = fabs(Nn - s.N[i]), den = fmax(s.N[i], kFloorN);
+            if (ratio_gt(dN, den, 0.1)) return false;
+            sm = sm && ratio_lt(dN, den, 0.05);
             o.Fs[i] = s.Fs[i] * inv;
+            if constexpr (SM) o.Fb[i] = (s.Fb[i] + h) * inv;
         }
         o.N[i] = Nn;
+        if constexpr (SM) o.Nd[i] = s.Nd[i];
         S crN = cr * Nn;
         gam0 += p.gc.sigN[i][0] * crN;
         gam1 += p.gc.sigN[i][1] * crN;
@@ -125,7 +171,8 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     }
 
     // 2. temperature
-    const S mu = mu_of(p.X, x, y2, y3);
+    const S mden = mu_den(p.X, x, y2, y3);
+    const S mu = 1.0 / mden;
     S Tmu1 = 0.0;
     if (!p.isothermal) {
         if (!cc.valid) {
@@ -138,13 +185,13 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         S lam = heat - cc.L;
         S dlam = -mu * cc.dL;
         S K = p.kfac / nH;
-        S Tmu = s.T / mu;
+        S Tmu = s.T * mden;
         S dT = lam * K * h / (1.0 - dlam * K * h);
         Tmu1 = Tmu + dT;
-        S rel = fabs(dT) / Tmu;
-        if (rel > 0.1) return false;
-        if (fabs(K * lam * h) / Tmu > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
+        S adT = fabs(dT);
+        if (ratio_gt(adT, Tmu, 0.1)) return false;
+        if (ratio_gt(fabs(K * lam * h), Tmu, 0.1)) return false;
+        sm = sm && ratio_lt(adT, Tmu, 0.05);
     }
 
     // 3. hydrogen
@@ -170,10 +217,10 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     x1 = fmin(fmax(x1, kXMin), 1.0);
     {
         S xden = fmax(x, kXMin);
-        S rel = fabs(x1 - x) / xden;
-        if (rel > 0.1) return false;
-        if (fabs(xdot) * h / xden > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
+        S dx = fabs(x1 - x);
+        if (ratio_gt(dx, xden, 0.1)) return false;
+        if (ratio_gt(fabs(xdot) * h, xden, 0.1)) return false;
+        sm = sm && ratio_lt(dx, xden, 0.05);
     }
 
     // 4. helium
@@ -186,7 +233,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             r2 = iso.he;
         } else {
             TranscT<S> t;
-            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
+            get_transc<WARP, MIX>(Tmu1 / mu_den(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
             he_rates_from(t, p.case_b, r2);
         }
         S C1 = y2 * r2.alpha_HeII * ne2;
@@ -201,7 +248,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             r3 = iso.he;
         } else {
             TranscT<S> t;
-            get_transc<WARP, MIX>(Tmu1 * mu_of(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
+            get_transc<WARP, MIX>(Tmu1 / mu_den(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
             he_rates_from(t, p.case_b, r3);
         }
         S C3 = y2n * (r3.beta_HeII * ne3 + gam2);
@@ -215,21 +262,21 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     }
     {
         S ne1 = x1 * nH + (y2n + 2.0 * y3n) * nHe;
-        S rel = fabs(ne1 - ne) / fmax(ne, kNeFloor * nH);
-        if (rel > 0.1) return false;
-        rel_max = fmax(rel_max, rel);
+        S dne = fabs(ne1 - ne), den = fmax(ne, kNeFloor * nH);
+        if (ratio_gt(dne, den, 0.1)) return false;
+        sm = sm && ratio_lt(dne, den, 0.05);
     }
-    S Tf = p.isothermal ? s.T : Tmu1 * mu_of(p.X, x1, y2n, y3n);
+    S Tf = p.isothermal ? s.T : Tmu1 / mu_den(p.X, x1, y2n, y3n);
     o.x = x1;
     o.y2 = y2n;
     o.y3 = y3n;
     o.T = fmax(Tf, kTFloor);
-    maxrel = val(rel_max);
+    small = sm;
     return true;
 }
 
 // One attempt of the sub-cycling loop; returns true when the cell is done.
-template <int G, bool WARP, bool MIX, typename S = double>
+template <int G, bool WARP, bool MIX, typename S = double, bool SM = false>
 __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH, CellState<G, S> &st,
                                               double &t_left, double &dt_tc, int &att, const IsoRates<S> &iso,
                                               CoolCache<S> &cc)
@@ -237,12 +284,12 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH
     double h = (dt_tc < t_left) ? dt_tc : t_left;
     ++att;
     CellState<G, S> o;
-    double mr = 0.0;
-    if (attempt<G, WARP, MIX, S>(p, nH, st, h, iso, cc, o, mr)) {
+    bool small = false;
+    if (attempt<G, WARP, MIX, S, SM>(p, nH, st, h, iso, cc, o, small)) {
         st = o;
         cc.valid = false;
         t_left = (h == t_left) ? 0.0 : t_left - h;
-        dt_tc = (mr < 0.05) ? 2.0 * h : h;
+        dt_tc = small ? 2.0 * h : h;
     } else {
         dt_tc = 0.5 * h;
     }

@@ -1,6 +1,6 @@
 """RT_MIXED (FP32 photon state and transport with compensated face sums,
 FP64 thermochemistry) and RT_MIXED32 (as RT_MIXED with FP32 rate
-transcendentals and photon update, FP64 x/T updates) against the FP64
+transcendentals and absorption coefficients, FP64 updates) against the FP64
 oracle and the FP64 GPU path.
 
 Stated accuracy of the mixed form (per field, max over cells):
