@@ -78,6 +78,7 @@ class OracleCfg(C.Structure):
         ("nthreads", C.c_int),
         ("skip_thermo", C.c_int),
         ("smooth", C.c_int),
+        ("rec_group", C.c_int * 3),
     ]
 
 
@@ -152,7 +153,8 @@ class Problem:
 
     def __init__(self, shape, dx, G, cr, sigN, sigE, egy, X=1.0, isothermal=False,
                  otsa=True, flux=GLF, bc=(0, 0, 0, 0, 0, 0), a_exp=1.0,
-                 max_subcycles=1_000_000, hll_table=None, nthreads=1, skip_thermo=False, smooth=False):
+                 max_subcycles=1_000_000, hll_table=None, nthreads=1, skip_thermo=False, smooth=False,
+                 rec_group=None):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.G = int(G)
@@ -185,6 +187,12 @@ class Problem:
         cfg.nthreads = int(nthreads)
         cfg.skip_thermo = int(bool(skip_thermo))
         cfg.smooth = int(bool(smooth))
+        # without the OTSA: the group that HII, HeII, HeIII recombinations
+        # emit into; by default the groups are taken as ordered by band, so
+        # species j emits into group min(j, G - 1)
+        rg = rec_group if rec_group is not None else [min(j, self.G - 1) for j in range(3)]
+        for j in range(3):
+            cfg.rec_group[j] = int(rg[j])
         self.cfg = cfg
 
     @property
@@ -226,7 +234,9 @@ class Problem:
     def thermo_cell(self, dt: float, nH: float, s, N, F, fixed_photons=False, Ndot=None, Fdot=None):
         """Sub-cycle one cell over dt.  s = [x_HII, x_HeII, x_HeIII, T];
         N [G]; F [G][3]; Ndot [G], Fdot [G][3]: smoothed-RT rates (Sec. 3.4)
-        or None.  Returns (status, s, N, F, attempts, absorbed, margin)."""
+        or None.  Returns (status, s, N, F, attempts, absorbed, margin);
+        absorbed is net of the recombination photons created without the
+        OTSA."""
         s = np.array(s, dtype=np.float64)
         N = np.array(N, dtype=np.float64).reshape(self.G)
         F = np.array(F, dtype=np.float64).reshape(self.G, 3).copy()

@@ -16,7 +16,9 @@
  *                    (T integration num eq 2), (xhii_update_2),
  *                    (xhei_update), (xheii_update), (xheiii_update)
  *   10% rule         Sec. 3.3.1 and App. A, task 5
- *   OTSA             Sec. 3.3.2 (case B rates, no recombination photons)
+ *   OTSA             Sec. 3.3.2 (case B rates, no recombination photons);
+ *                    without it case A rates and the recombination photons
+ *                    of Eqs. (thchem_N), (cool_N_cr)
  *   smoothed RT      Sec. 3.4, Eqs. (thchem_N_smooth), (thchem_F_smooth),
  *                    (smoothrate1), (smoothrate2); App. A Eq. (SIE photons)
  *   Courant step     Sec. 4.1, Eq. (dt_courant)
@@ -465,7 +467,7 @@ static int thermo_step(const oracle_cfg *cfg, double h, double nH,
                        const double *s0 /* x, y2, y3, T */, const double *N0,
                        const double *Ndot /* smoothed RT rates, or NULL */,
                        double *s1, double *N1, double *Fscale, double *absorbed,
-                       double *maxrel, double *margin, int fixed_photons)
+                       double *created, double *maxrel, double *margin, int fixed_photons)
 {
     const int G = cfg->G;
     const double X = cfg->X, Y = 1.0 - X;
@@ -483,6 +485,23 @@ static int thermo_step(const oracle_cfg *cfg, double h, double nH,
     double nHII = nH * x;
     double ne = ne_of(nH, nHe, x, y2, y3);
 
+    /* recombination photons without the OTSA, Eq. (cool_N_cr):
+     * C_i = sum_j b_ji (alpha^A_j - alpha^B_j) n_j n_e at T(t), j = HII,
+     * HeII, HeIII emitting into group rec_group[j] */
+    double Crec[ORACLE_MAXG];
+    for (int i = 0; i < G; i++) Crec[i] = 0.0;
+    if (!cfg->otsa) {
+        double rA[R_COUNT], dA[R_COUNT], rB[R_COUNT], dB[R_COUNT];
+        oracle_rates(T, cfg->a_exp, 0, rA, dA);
+        oracle_rates(T, cfg->a_exp, 1, rB, dB);
+        const double nj[3] = {nHII, nHeII, nHeIII};
+        const int aj[3] = {R_ALPHA_HII, R_ALPHA_HEII, R_ALPHA_HEIII};
+        for (int j = 0; j < 3; j++) {
+            int g = cfg->rec_group[j];
+            if (g >= 0 && g < G) Crec[g] += (rA[aj[j]] - rB[aj[j]]) * nj[j] * ne;
+        }
+    }
+
     /* task 1: photon density and flux, Eq. (SIE photons); OTSA => C_i = 0 */
     for (int i = 0; i < G; i++) {
         double Di = cr * (cfg->sigN[3 * i + 0] * nHI + cfg->sigN[3 * i + 1] * nHeI
@@ -491,17 +510,24 @@ static int thermo_step(const oracle_cfg *cfg, double h, double nH,
             N1[i] = N0[i];
             Fscale[i] = 1.0;
             absorbed[i] = 0.0;
+            created[i] = 0.0;
             continue;
         }
         /* smoothed RT: the transport and injection change of the RT step
          * enters as the rate Ndot_i, Eq. (SIE photons) with Ndot_i + C_i */
-        N1[i] = Ndot ? (N0[i] + h * Ndot[i]) / (1.0 + h * Di) : N0[i] / (1.0 + h * Di);
+        if (Ndot || !cfg->otsa) {
+            double src = (Ndot ? Ndot[i] : 0.0) + Crec[i];
+            N1[i] = (N0[i] + h * src) / (1.0 + h * Di);
+        } else {
+            N1[i] = N0[i] / (1.0 + h * Di);
+        }
         Fscale[i] = 1.0 / (1.0 + h * Di);
         double rel = fabs(N1[i] - N0[i]) / fmax(N0[i], FLOOR_N);
         note_margin(rel, 0.1, margin);
         if (rel > 0.1) return 0;
         if (rel > rel_max) rel_max = rel;
         absorbed[i] = h * Di * N1[i];
+        created[i] = h * Crec[i];
     }
 
     /* photoionisation rates with the forward photon densities */
@@ -653,7 +679,7 @@ int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s
                        int *attempts_out, double *absorbed_out, double *margin_out)
 {
     const int G = cfg->G;
-    double N1[ORACLE_MAXG], Fs[ORACLE_MAXG], ab[ORACLE_MAXG], s1[4];
+    double N1[ORACLE_MAXG], Fs[ORACLE_MAXG], ab[ORACLE_MAXG], cre[ORACLE_MAXG], s1[4];
     double t_left = dt_rt, dt_tc = dt_rt;
     double margin = 1e300;
     int attempts = 0;
@@ -664,7 +690,7 @@ int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s
         double h = (dt_tc < t_left) ? dt_tc : t_left;
         double maxrel = 0.0;
         attempts++;
-        int ok = thermo_step(cfg, h, nH, s, N, Ndot, s1, N1, Fs, ab, &maxrel, &margin, fixed_photons);
+        int ok = thermo_step(cfg, h, nH, s, N, Ndot, s1, N1, Fs, ab, cre, &maxrel, &margin, fixed_photons);
         if (!ok) { dt_tc = 0.5 * h; continue; }
         for (int q = 0; q < 4; q++) s[q] = s1[q];
         for (int i = 0; i < G; i++) {
@@ -677,7 +703,7 @@ int oracle_thermo_cell(const oracle_cfg *cfg, double dt_rt, double nH, double *s
                 F[3 * i + 1] *= Fs[i];
                 F[3 * i + 2] *= Fs[i];
             }
-            absorbed_out[i] += ab[i];
+            absorbed_out[i] += ab[i] - cre[i];   /* net: absorbed minus created */
         }
         t_left = (h == t_left) ? 0.0 : t_left - h;
         note_margin(maxrel, 0.05, &margin);

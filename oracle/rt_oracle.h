@@ -43,6 +43,8 @@ typedef struct {
     int nthreads;           /* OpenMP threads over cells (<=1: serial) */
     int skip_thermo;        /* transport-only tests */
     int smooth;             /* smoothed RT, Sec. 3.4 */
+    int rec_group[3];       /* without OTSA: group that HII, HeII, HeIII
+                               recombinations emit into (-1: none) */
 } oracle_cfg;
 
 void oracle_rates(double T, double a_exp, int case_b, double *r, double *dr);
