@@ -54,6 +54,7 @@ extern "C" {
 enum { RT_BC_OUTFLOW = 0, RT_BC_REFLECT = 1, RT_BC_PERIODIC = 2 };
 enum { RT_GLF = 0, RT_HLL = 1 };
 enum { RT_FP64 = 0, RT_MIXED = 1, RT_MIXED32 = 2 };
+#define RT_REC_BY_BAND -2
 
 typedef struct rt_handle rt_handle;
 
@@ -68,7 +69,7 @@ typedef struct {
 
 /* Options.  X: hydrogen mass fraction (Y = 1 - X; helium is skipped when
  * Y = 0).  isothermal: T held fixed.  otsa: on-the-spot approximation
- * (case-B rates, no recombination photons; Sec. 3.3.2) - must be 1.
+ * (case-B rates, no recombination photons; Sec. 3.3.2; default 1).
  * flux: RT_GLF (default) or RT_HLL.  cfl: Courant factor (0.8).
  * precision: RT_FP64; RT_MIXED (photon state and transport in FP32 with
  * compensated face sums, thermochemistry in FP64); RT_MIXED32 (as
@@ -80,7 +81,13 @@ typedef struct {
  * thermochemistry as the rates (N'_i - N^t_i)/dt, (F'_i - F^t_i)/dt of its
  * photon update, which starts from the state before injection
  * (Eqs. (smoothrate1), (smoothrate2)); single-box handles only (the batch,
- * the adjoint and rt_thermo_step_noalloc take 0). */
+ * the adjoint and rt_thermo_step_noalloc take 0).  otsa = 0 (single-box
+ * handles only): case-A rates and recombination photons
+ * C_i = sum_j b_ji (alpha^A_j - alpha^B_j) n_j n_e (Eqs. (thchem_N),
+ * (cool_N_cr)); rec_group[j] is the group that recombinations of HII,
+ * HeII, HeIII emit into, -1 for none, RT_REC_BY_BAND (the default) for
+ * group min(j, G - 1) (groups ordered by band); the budget's absorbed
+ * column is then absorbed minus created. */
 typedef struct {
     double X;
     int isothermal;
@@ -91,6 +98,7 @@ typedef struct {
     double a_exp;
     int max_subcycles;
     int smooth;
+    int rec_group[3];
 } rt_options;
 
 /* Fill *o with the defaults listed above (X = 0.76). */

@@ -94,6 +94,7 @@ thermo_vjp_kernel(ThermoParams p, const double *__restrict__ nH, const double *_
     IsoRates<Dual> iso;
     CoolCache<Dual> cc;
     cc.valid = false;
+    cc.rvalid = false;
     if (p.isothermal) {
         TranscT<Dual> t;
         transc_dual(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);

@@ -244,6 +244,10 @@ constexpr unsigned kNeedHe3 = (1u << E_BETA_HEII) | (1u << (E_W0 + HG_ALPHA_HEII
                               (1u << (NEXP + HG_ALPHA_HEIII));
 constexpr unsigned kNeedCoolH = (1u << E_BETA_HI) | (1u << E_PSI_HI) | (1u << (E_W0 + HG_ETA_HII)) |
                                 (1u << (NEXP + HG_ETA_HII));
+// the three recombination rates alpha_HII, alpha_HeII, alpha_HeIII
+constexpr unsigned kNeedRec = (1u << E_ALPHA_HEII) | (1u << (E_W0 + HG_ALPHA_HII)) |
+                              (1u << (E_W0 + HG_ALPHA_HEIII)) | (1u << (NEXP + HG_ALPHA_HII)) |
+                              (1u << (NEXP + HG_ALPHA_HEIII));
 constexpr unsigned kNeedCoolHe = (1u << E_BETA_HEI) | (1u << E_BETA_HEII) | (1u << E_PSI_HEII) |
                                  (1u << E_OMEGA1) | (1u << E_OMEGA2) | (1u << E_ALPHA_HEII) |
                                  (1u << (E_W0 + HG_ETA_HEIII)) | (1u << (NEXP + HG_ETA_HEIII));
@@ -285,6 +289,17 @@ __device__ __forceinline__ void he_rates_from(const TranscT<S> &t, int case_b, H
     cen_fit(5.68e-12, 631515.0, t.e[E_BETA_HEII], t, r.beta_HeII, d);
     r.alpha_HeII = R.A_aHeII * t.e[E_ALPHA_HEII];
     r.alpha_HeIII = R.hg[HG_ALPHA_HEIII].A * t.v[HG_ALPHA_HEIII];
+}
+
+// Recombination rates of HII, HeII, HeIII (the case of the table t was
+// evaluated with)
+template <typename S>
+__device__ __forceinline__ void recomb_alphas(const TranscT<S> &t, int case_b, S a[3])
+{
+    const RateTable &R = c_rate_tab[case_b];
+    a[0] = R.hg[HG_ALPHA_HII].A * t.v[HG_ALPHA_HII];
+    a[1] = R.A_aHeII * t.e[E_ALPHA_HEII];
+    a[2] = R.hg[HG_ALPHA_HEIII].A * t.v[HG_ALPHA_HEIII];
 }
 
 // Primordial cooling magnitude L (Eq. (rate_cooling), positive = cooling)

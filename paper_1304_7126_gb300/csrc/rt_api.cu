@@ -155,6 +155,11 @@ ThermoParams thermo_params(const rt_handle *h, double dt)
     p.case_b = h->opt.otsa ? 1 : 0;
     p.max_sub = h->opt.max_subcycles;
     p.pass1_attempts = 6;
+    p.emit = h->opt.otsa ? 0 : 1;
+    for (int j = 0; j < 3; ++j) {
+        int r = h->opt.rec_group[j];
+        p.rec_g[j] = (r == RT_REC_BY_BAND) ? std::min(j, h->G - 1) : r;
+    }
     p.gc = h->gc;
     return p;
 }
@@ -338,8 +343,8 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
 int vjp_args(rt_handle *h, double *dt, double *lx, double *ly2, double *ly3, double *lT, double *lN, double *lF,
              double *g_nH, double *g_L)
 {
-    if (h->opt.precision != RT_FP64 || h->opt.flux != RT_GLF || h->opt.smooth)
-        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64, flux RT_GLF and no smoothing");
+    if (h->opt.precision != RT_FP64 || h->opt.flux != RT_GLF || h->opt.smooth || !h->opt.otsa)
+        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64, flux RT_GLF, the OTSA and no smoothing");
     if (!lx || !ly2 || !ly3 || !lT || !lN || !lF || !g_nH || (h->nsrc_orig > 0 && !g_L))
         return fail(h, RT_EINVAL, "null adjoint array");
     return check_dt(h, dt);
@@ -361,6 +366,7 @@ void rt_default_options(rt_options *o)
     o->a_exp = 1.0;
     o->max_subcycles = 1000000;
     o->smooth = 0;
+    o->rec_group[0] = o->rec_group[1] = o->rec_group[2] = RT_REC_BY_BAND;
 }
 
 int rt_version(void) { return 100; }
@@ -391,7 +397,10 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     if (!(opt->X > 0.0 && opt->X <= 1.0)) return RT_EINVAL;
     if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return RT_EINVAL;
     if (opt->flux != RT_GLF && opt->flux != RT_HLL) return RT_EINVAL;
-    if (opt->otsa != 1 || (opt->smooth != 0 && opt->smooth != 1)) return RT_EINVAL;
+    if ((opt->otsa != 0 && opt->otsa != 1) || (opt->smooth != 0 && opt->smooth != 1)) return RT_EINVAL;
+    for (int j = 0; j < 3; ++j)
+        if (opt->rec_group[j] != RT_REC_BY_BAND && (opt->rec_group[j] < -1 || opt->rec_group[j] >= n_groups))
+            return RT_EINVAL;
     if (opt->precision != RT_FP64 && opt->precision != RT_MIXED && opt->precision != RT_MIXED32) return RT_EINVAL;
     if (!(opt->a_exp > 0.0) || opt->max_subcycles < 1) return RT_EINVAL;
     for (int i = 0; i < 3 * n_groups; ++i)

@@ -65,6 +65,8 @@ struct ThermoParams {
     int case_b;
     int max_sub;
     int pass1_attempts;      // attempts before a cell is handed to the queue
+    int emit;                // no OTSA: recombination photons (Sec. 3.3.2)
+    int rec_g[3];            // group receiving HII, HeII, HeIII recombination photons (-1: none)
     GroupConsts gc;
 };
 

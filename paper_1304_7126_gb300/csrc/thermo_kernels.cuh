@@ -58,6 +58,7 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, bo
         st.Fs[i] = 1.0;
     }
     cc.valid = false;
+    cc.rvalid = false;
     if (p.isothermal) {
         Transc t;
         get_transc<WARP, R32>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);

@@ -36,9 +36,10 @@ struct IsoRates {     // rates at the fixed temperature of an isothermal cell
 };
 
 template <typename S = double>
-struct CoolCache {    // cooling L and dL/dT of the current state at t
-    S L, dL;
-    bool valid;
+struct CoolCache {    // quantities of the current state at t, kept over rejected attempts
+    S L, dL;          // cooling and dL/dT
+    S rj[3];          // without the OTSA: (alpha^A_j - alpha^B_j) n_j n_e, j = HII, HeII, HeIII
+    bool valid, rvalid;
 };
 
 // 1/mu, mu the mean particle mass in m_H (App. A)
@@ -61,13 +62,27 @@ __device__ __forceinline__ S mu_of(double X, const S &x, const S &y2, const S &y
 // that divides, including at exact ties (a sub-cycled cell whose photon
 // density grows linearly from zero meets relative changes of exactly 1/10
 // and 1/20).
+// the quotient itself, kept out of line so that the compiler does not
+// evaluate it on the common path
+template <typename S>
+__device__ __noinline__ bool quotient_gt(S a, S b, double t)
+{
+    return a / b > t;
+}
+
+template <typename S>
+__device__ __noinline__ bool quotient_lt(S a, S b, double t)
+{
+    return a / b < t;
+}
+
 template <typename S>
 __device__ __forceinline__ bool ratio_gt(const S &a, const S &b, double t)
 {
     const S tb = t * b;
     if (a > tb * (1.0 + 1e-15)) return true;
     if (a < tb * (1.0 - 1e-15)) return false;
-    return a / b > t;
+    return quotient_gt<S>(a, b, t);
 }
 
 template <typename S>
@@ -76,7 +91,7 @@ __device__ __forceinline__ bool ratio_lt(const S &a, const S &b, double t)
     const S tb = t * b;
     if (a < tb * (1.0 - 1e-15)) return true;
     if (a > tb * (1.0 + 1e-15)) return false;
-    return a / b < t;
+    return quotient_lt<S>(a, b, t);
 }
 
 template <bool WARP, bool MIX>
@@ -96,6 +111,29 @@ __device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, 
         if (WARP) transc_warp(T, case_b, t);
         else transc_serial(T, case_b, need, t);
     }
+}
+
+// (alpha^A_j - alpha^B_j) n_j n_e of HII, HeII, HeIII at temperature T
+// (Eq. (cool_N_cr)); out of line: it only runs without the OTSA, and
+// inlined its two rate tables would raise the register count of every
+// kernel
+template <bool WARP, bool MIX, typename S>
+__device__ __noinline__ void recomb_rates(S T, S nHII, S nHeII, S nHeIII, S ne, S *rj)
+{
+    S aA[3], aB[3];
+    {
+        TranscT<S> t;
+        get_transc<WARP, MIX>(T, 0, kNeedRec, t);
+        recomb_alphas(t, 0, aA);
+    }
+    {
+        TranscT<S> t;
+        get_transc<WARP, MIX>(T, 1, kNeedRec, t);
+        recomb_alphas(t, 1, aB);
+    }
+    rj[0] = (aA[0] - aB[0]) * nHII * ne;
+    rj[1] = (aA[1] - aB[1]) * nHeII * ne;
+    rj[2] = (aA[2] - aB[2]) * nHeIII * ne;
 }
 
 // One thermo_step over h.  Returns true and fills `o` when the 10% rule
@@ -125,10 +163,23 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     bool sm = true;
     S gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
 
+    // recombination photons without the OTSA, Eq. (cool_N_cr), at T(t) with
+    // the backward abundances; group i gains C_i = sum_j [rec_g[j] == i] rj[j]
+    if (p.emit && !cc.rvalid) {
+        recomb_rates<WARP, MIX>(s.T, nHII, nHeII, nHeIII, ne, cc.rj);
+        cc.rvalid = true;
+    }
+
     // 1. photons
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         S Nn;
+        S Crec = 0.0;
+        if (p.emit) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (p.rec_g[j] == i) Crec += cc.rj[j];
+        }
         if constexpr (MIX) {
             // absorption coefficient in FP32; the update itself in FP64, since
             // a cell may take thousands of sub-steps and FP32 roundings of
@@ -136,7 +187,8 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             float Df = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
                                     (float)p.gc.sigN[i][2] * (float)nHeII);
             double inv = 1.0 / (1.0 + h * (double)Df);
-            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i])) * inv;
+            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
+            else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
             else Nn = s.N[i] * inv;
             double dN = fabs(Nn - s.N[i]), den = fmax(s.N[i], kFloorN);
             if (ratio_gt(dN, den, 0.1)) return false;
@@ -149,7 +201,8 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             // smoothed RT: Eq. (SIE photons) with the rate Ndot_i; N + h Ndot
             // rounded step by step (no fused multiply-add), so a cell growing
             // linearly from zero meets its relative changes 1/k exactly
-            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i])) * inv;
+            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
+            else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
             else Nn = s.N[i] * inv;
             S dN = fabs(Nn - s.N[i]), den = fmax(s.N[i], kFloorN);
             if (ratio_gt(dN, den, 0.1)) return false;
@@ -288,6 +341,7 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH
     if (attempt<G, WARP, MIX, S, SM>(p, nH, st, h, iso, cc, o, small)) {
         st = o;
         cc.valid = false;
+        cc.rvalid = false;
         t_left = (h == t_left) ? 0.0 : t_left - h;
         dt_tc = small ? 2.0 * h : h;
     } else {

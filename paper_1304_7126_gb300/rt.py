@@ -20,6 +20,7 @@ RT_OK, RT_EINVAL, RT_EDT, RT_ESUBCYCLE, RT_EQUEUE, RT_ECUDA, RT_ENOMEM, RT_ENONF
 RT_BC_OUTFLOW, RT_BC_REFLECT, RT_BC_PERIODIC = 0, 1, 2
 RT_GLF, RT_HLL = 0, 1
 RT_FP64, RT_MIXED, RT_MIXED32 = 0, 1, 2
+RT_REC_BY_BAND = -2
 RT_MAX_GROUPS = 8
 
 ERROR_NAMES = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_EDT", -3: "RT_ESUBCYCLE", -4: "RT_EQUEUE",
@@ -34,7 +35,7 @@ class rt_grid(C.Structure):
 class rt_options(C.Structure):
     _fields_ = [("X", C.c_double), ("isothermal", C.c_int), ("otsa", C.c_int), ("flux", C.c_int),
                 ("cfl", C.c_double), ("precision", C.c_int), ("a_exp", C.c_double),
-                ("max_subcycles", C.c_int), ("smooth", C.c_int)]
+                ("max_subcycles", C.c_int), ("smooth", C.c_int), ("rec_group", C.c_int * 3)]
 
 
 class RTError(RuntimeError):
@@ -151,6 +152,8 @@ def default_options(**kw) -> rt_options:
     o = rt_options()
     load().rt_default_options(C.byref(o))
     for k, v in kw.items():
+        if k == "rec_group":
+            v = (C.c_int * 3)(*[int(a) for a in v])
         setattr(o, k, v)
     return o
 
