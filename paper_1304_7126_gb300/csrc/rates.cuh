@@ -6,7 +6,8 @@
 //
 // Evaluation is split in two stages so that the same arithmetic can be done
 // by one thread or spread over the lanes of a warp:
-//   1. transcendentals of one temperature (struct Transc): ln T, sqrt T,
+//   1. transcendentals of one temperature (struct Transc; exp, log and
+//      log1p are the table-driven ones of fmath.cuh): ln T, sqrt T,
 //      1/T, and twelve exponentials exp(a ln T + b/T + c) - the Boltzmann
 //      factors exp(-T0/T), the power laws, and w = (lam/l0)^r of the four
 //      Hui & Gnedin fits A lam^p / (1 + w)^s - then log1p(w) and
@@ -21,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "dual.cuh"
+#include "fmath.cuh"
 
 namespace rtgb {
 
@@ -77,7 +79,7 @@ static __constant__ RateTable c_rate_tab[2] = {
 
 __device__ __forceinline__ void transc_level0(double T, Transc &t)
 {
-    t.lnT = log(T);
+    t.lnT = fm::log_t(T);
     t.sqrtT = sqrt(T);
     t.invT = 1.0 / T;
     t.u = 1.0 / (1.0 + t.sqrtT * 0.003162277660168379);
@@ -101,12 +103,12 @@ __device__ __forceinline__ void transc_serial(double T, int case_b, unsigned nee
     transc_level0(T, t);
 #pragma unroll
     for (int k = 0; k < NEXP; ++k)
-        if (need & (1u << k)) t.e[k] = exp(exp_arg(R.ea[k], t));
+        if (need & (1u << k)) t.e[k] = fm::exp_t(exp_arg(R.ea[k], t));
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
-            t.l[j] = log1p(t.e[E_W0 + j]);
-            t.v[j] = exp(hg_arg(R.hg[j], t.lnT, t.l[j]));
+            t.l[j] = fm::log1p_t(t.e[E_W0 + j]);
+            t.v[j] = fm::exp_t(hg_arg(R.hg[j], t.lnT, t.l[j]));
         }
     }
 }
@@ -119,11 +121,11 @@ __device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
     const int lane = threadIdx.x & 31;
     transc_level0(T, t);
     const int k = lane < NEXP ? lane : 0;
-    double ek = exp(exp_arg(R.ea[k], t));
+    double ek = fm::exp_t(exp_arg(R.ea[k], t));
     const int j = lane & 3;
     double wj = __shfl_sync(0xffffffffu, ek, E_W0 + j);
-    double lj = log1p(wj);
-    double vj = exp(hg_arg(R.hg[j], t.lnT, lj));
+    double lj = fm::log1p_t(wj);
+    double vj = fm::exp_t(hg_arg(R.hg[j], t.lnT, lj));
 #pragma unroll
     for (int q = 0; q < NEXP; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
 #pragma unroll

@@ -425,8 +425,7 @@ __device__ __forceinline__ void block_reduce2(double *red, double &a, double &b)
 }
 
 template <typename S, int FLUX>
-__global__ void __launch_bounds__(256)
-transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
+__device__ __forceinline__ void transport_kernel_body(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
                  const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
                  const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
                  int tiles_x, int tiles_y, int nblk)
@@ -450,6 +449,31 @@ transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N
         part_inbox[(long long)grp * nblk + tile] = inbox;
         part_out[(long long)grp * nblk + tile] = outflow * area_dt;
     }
+}
+
+// FP64: one CTA per SM fits (FP64-pipe bound).  FP32: capped at 80
+// registers so that three CTAs share an SM and hide the shared-memory and
+// table-lookup latencies (the FP32 kernel is latency-bound).
+template <typename S, int FLUX>
+__global__ void __launch_bounds__(256)
+transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
+                 const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
+                 const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
+                 int tiles_x, int tiles_y, int nblk)
+{
+    transport_kernel_body<S, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, part_inbox, part_out,
+                                   tiles_x, tiles_y, nblk);
+}
+
+template <int FLUX>
+__global__ void __launch_bounds__(256, 3)
+transport_kernel_f32(GridDev g, float c, float dtdx, double area_dt, const float *__restrict__ N0all,
+                     const float *__restrict__ F0all, float *__restrict__ N1all, float *__restrict__ F1all,
+                     const float *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
+                     int tiles_x, int tiles_y, int nblk)
+{
+    transport_kernel_body<float, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, part_inbox, part_out,
+                                       tiles_x, tiles_y, nblk);
 }
 
 // Batched boxes: CTA i works on item i (box, group, tile, z range) of a
@@ -503,8 +527,8 @@ void transport_init()
     int s8 = (int)sizeof(PlaneSmem<double, 32, 8>), s4 = (int)sizeof(PlaneSmem<float, 32, 8>);
     cudaFuncSetAttribute(transport_kernel<double, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
     cudaFuncSetAttribute(transport_kernel<double, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
-    cudaFuncSetAttribute(transport_kernel<float, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
-    cudaFuncSetAttribute(transport_kernel<float, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+    cudaFuncSetAttribute(transport_kernel_f32<RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+    cudaFuncSetAttribute(transport_kernel_f32<RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
     set_smem_attr_batch<double, 32, 8>();
     set_smem_attr_batch<double, 16, 16>();
     set_smem_attr_batch<float, 32, 8>();
@@ -523,12 +547,21 @@ static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double
     size_t smem = sizeof(PlaneSmem<S, 32, 8>);
     S dtdx = (S)(dt / g.dx);
     double area_dt = g.dx * g.dx * dt;
-    if (flux == RT_HLL)
-        transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
-                                                               p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
-    else
-        transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
-                                                               p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+    if constexpr (sizeof(S) == sizeof(float)) {
+        if (flux == RT_HLL)
+            transport_kernel_f32<RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                    p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+        else
+            transport_kernel_f32<RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                    p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+    } else {
+        if (flux == RT_HLL)
+            transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                   p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+        else
+            transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                   p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+    }
     return cudaGetLastError();
 }
 

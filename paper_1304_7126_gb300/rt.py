@@ -77,6 +77,7 @@ def load(build: bool = True):
     L.rt_last_error.restype = C.c_char_p
     L.rt_hll_table.argtypes = [C.c_int, C.c_int, dp]
     L.rt_version.argtypes = []
+    L.rt_fmath_eval.argtypes = [C.c_int, C.c_longlong, dp, dp, vp]
     L.rt_step_vjp.argtypes = [vp, C.c_double, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_run_vjp.argtypes = [vp, C.c_double, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_thermo_step_noalloc.argtypes = [C.c_longlong, C.c_int, C.POINTER(rt_options), C.c_double, dp, dp,
