@@ -1,4 +1,4 @@
-// Adjoint (vector-Jacobian product) of one RT step, FP64, GLF transport.
+// Adjoint (vector-Jacobian product) of one RT step, FP64, GLF or HLL transport.
 //
 // The forward step is U_k -> inject -> U_a -> transport -> U_b -> thermo ->
 // U_{k+1} (paper Sec. 3: Eq. (injnum), the Godunov update with the GLF
@@ -28,8 +28,11 @@
 // lambda_L and (J_R^T - c) mu/2 to lambda_R, J = dPhi_d/dU from the M1
 // closure (Sec. 2, Eqs. (edd2), (eddTens)).  Boundary ghosts are B U_c
 // (outflow: B = I; reflect: the normal flux negated) and carry no lambda'.
-// The realisability clamp of the forward update acts only at rounding level
-// for CFL <= 1 and is taken as the identity.
+// With HLL (Eq. (hll)) the face flux also depends on the cells' tabulated
+// wave speeds; its transpose adds their derivatives (transport_vjp_hll).
+// The realisability rescaling of F that ends the forward update is
+// transposed first (clamp_vjp); its N < 0 branch (never taken for CFL <= 1)
+// is taken as the identity.
 #include <cuda_runtime.h>
 
 #include "rt_internal.h"
@@ -293,6 +296,235 @@ transport_vjp_kernel(GridDev g, double c, double r, const double *__restrict__ N
     lFo[2 * g.stride + i] = acc[3];
 }
 
+// ---- HLL (Eq. (hll)) ----
+//
+// Face flux Fhat = (l+ Phi_L - l- Phi_R + l+ l- (U_R - U_L)) / (l+ - l-),
+// l+ = max(0, lmax_L, lmax_R), l- = min(0, lmin_L, lmin_R), the speeds c
+// times the bilinear table at (f, mu_d) of their cell.  Its transpose on a
+// co-flux m: (l+ J_L^T m - l+ l- m)/den to U_L, (-l- J_R^T m + l+ l- m)/den
+// to U_R, and through the speeds: d(Fhat.m)/dl+ = (Phi_L + l- dU - Fhat).m
+// / den, d(Fhat.m)/dl- = (-Phi_R + l+ dU + Fhat).m / den, times the
+// gradient of the selected cell's speed (the max/min picks one cell; the
+// bilinear table is differentiated inside its cell).  With no speed (both
+// zero: f = 1 beams along the face) the flux is the average of the two.
+
+struct HllSide {
+    double U[4], Phi[4];
+    double lo, hi;            // c * table speeds
+    double dlo[4], dhi[4];    // their gradients with respect to U
+};
+
+// speeds and their U-gradients of a state along direction d
+__device__ __forceinline__ void hll_side(const double U[4], int d, double c, const double *__restrict__ tab, HllSide &o)
+{
+    const double N = U[0];
+    const double F2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+    double f = 0.0, n[3] = {0.0, 0.0, 0.0}, mag = 0.0;
+    bool dir = false, clamped = false;
+    if (N > kClosureFloorN && F2 > 0.0) {
+        mag = sqrt(F2);
+        const double fr = mag / (c * N);
+        clamped = fr > 1.0;
+        f = clamped ? 1.0 : fr;
+        n[0] = U[1] / mag; n[1] = U[2] / mag; n[2] = U[3] / mag;
+        dir = true;
+    }
+    const double mu = n[d];
+    // the forward's bilinear lookup, with its slopes
+    const double fx = f * (double)(kHllNF - 1);
+    int k = (int)floor(fx);
+    k = k < 0 ? 0 : (k > kHllNF - 2 ? kHllNF - 2 : k);
+    const double wf = fx - (double)k;
+    const double mx = (mu + 1.0) * 0.5 * (double)(kHllNMU - 1);
+    int j = (int)floor(mx);
+    j = j < 0 ? 0 : (j > kHllNMU - 2 ? kHllNMU - 2 : j);
+    const double wm = mx - (double)j;
+    const double2 *t2 = reinterpret_cast<const double2 *>(tab);
+    const double2 A = __ldg(&t2[k * kHllNMU + j]), B = __ldg(&t2[k * kHllNMU + j + 1]);
+    const double2 Cc = __ldg(&t2[(k + 1) * kHllNMU + j]), D = __ldg(&t2[(k + 1) * kHllNMU + j + 1]);
+    const double lo0 = A.x + wm * (B.x - A.x), lo1 = Cc.x + wm * (D.x - Cc.x);
+    const double hi0 = A.y + wm * (B.y - A.y), hi1 = Cc.y + wm * (D.y - Cc.y);
+    o.lo = (lo0 + wf * (lo1 - lo0)) * c;
+    o.hi = (hi0 + wf * (hi1 - hi0)) * c;
+    // d/df and d/dmu of the table values, times c
+    const double sf = (double)(kHllNF - 1) * c, sm = 0.5 * (double)(kHllNMU - 1) * c;
+    const double dlo_df = sf * (lo1 - lo0), dhi_df = sf * (hi1 - hi0);
+    const double dlo_dmu = sm * ((1.0 - wf) * (B.x - A.x) + wf * (D.x - Cc.x));
+    const double dhi_dmu = sm * ((1.0 - wf) * (B.y - A.y) + wf * (D.y - Cc.y));
+    for (int q = 0; q < 4; ++q) o.dlo[q] = o.dhi[q] = 0.0;
+    if (dir) {
+        // f = |F|/(c N): df/dN = -f/N, df/dF = n/(c N) (0 where clamped);
+        // mu = F_d/|F|: dmu/dF = (e_d - mu n)/|F|
+        const double dfN = clamped ? 0.0 : -f / N;
+        const double dfF = clamped ? 0.0 : 1.0 / (c * N);
+        o.dlo[0] = dlo_df * dfN;
+        o.dhi[0] = dhi_df * dfN;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double dmu = ((q == d ? 1.0 : 0.0) - mu * n[q]) / mag;
+            o.dlo[1 + q] = dlo_df * dfF * n[q] + dlo_dmu * dmu;
+            o.dhi[1 + q] = dhi_df * dfF * n[q] + dhi_dmu * dmu;
+        }
+    }
+    // physical flux along d
+    double Fv[3] = {U[1], U[2], U[3]};
+    double P[3];
+    {
+        const double f2 = f * f;
+        const double chi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
+        const double cN = c * c * N;
+        const double ca = cN * 0.5 * (1.0 - chi), cb = cN * 0.5 * (3.0 * chi - 1.0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) P[q] = (q == d ? ca : 0.0) + cb * n[q] * n[d];
+    }
+    o.Phi[0] = Fv[d];
+    o.Phi[1] = P[0]; o.Phi[2] = P[1]; o.Phi[3] = P[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o.U[q] = U[q];
+}
+
+// Contribution of one HLL face (L, R) with co-flux m to the lambda of L
+// (want_L) and / or R; JLm, JRm: J_L^T m and J_R^T m where needed.
+__device__ __forceinline__ void hll_face_vjp(const HllSide &L, const HllSide &R, const double m[4],
+                                             const double JLm[4], const double JRm[4], bool want_L, bool want_R,
+                                             double cL[4], double cR[4])
+{
+    const double lp = fmax(0.0, fmax(L.hi, R.hi));
+    const double lm = fmin(0.0, fmin(L.lo, R.lo));
+    const double den = lp - lm;
+    if (!(den > 0.0)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cL[q] = want_L ? 0.5 * JLm[q] : 0.0;
+            cR[q] = want_R ? 0.5 * JRm[q] : 0.0;
+        }
+        return;
+    }
+    const double inv = 1.0 / den;
+    double gp = 0.0, gm = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double dU = R.U[q] - L.U[q];
+        const double Fh = (lp * L.Phi[q] - lm * R.Phi[q] + lp * lm * dU) * inv;
+        gp += (L.Phi[q] + lm * dU - Fh) * m[q];
+        gm += (-R.Phi[q] + lp * dU + Fh) * m[q];
+    }
+    gp *= inv;
+    gm *= inv;
+    // which cell's speed sets l+ and l- (none if the bound is 0)
+    const bool pL = lp > 0.0 && L.hi >= R.hi, pR = lp > 0.0 && !pL;
+    const bool mL = lm < 0.0 && L.lo <= R.lo, mR = lm < 0.0 && !mL;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        cL[q] = want_L ? (lp * JLm[q] - lp * lm * m[q]) * inv + (pL ? gp * L.dhi[q] : 0.0) + (mL ? gm * L.dlo[q] : 0.0)
+                       : 0.0;
+        cR[q] = want_R ? (-lm * JRm[q] + lp * lm * m[q]) * inv + (pR ? gp * R.dhi[q] : 0.0) + (mR ? gm * R.dlo[q] : 0.0)
+                       : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(128)
+transport_vjp_hll_kernel(GridDev g, double c, double r, const double *__restrict__ N, const double *__restrict__ F,
+                         const double *__restrict__ tab, const double *__restrict__ lN1,
+                         const double *__restrict__ lF1, double *__restrict__ lN0, double *__restrict__ lF0)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nc) return;
+    const long long go = (long long)blockIdx.y * g.stride;
+    const double *Ng = N + go, *Fg = F + 3 * go, *lNg = lN1 + go, *lFg = lF1 + 3 * go;
+    const int x = (int)(i % g.nx);
+    const int y = (int)((i / g.nx) % g.ny);
+    const int z = (int)(i / ((long long)g.nx * g.ny));
+    const int pos[3] = {x, y, z};
+    const int ext[3] = {g.nx, g.ny, g.nz};
+    const long long step[3] = {1, g.nx, (long long)g.nx * g.ny};
+    const double Uc[4] = {Ng[i], Fg[i], Fg[g.stride + i], Fg[2 * g.stride + i]};
+    const double lp[4] = {lNg[i], lFg[i], lFg[g.stride + i], lFg[2 * g.stride + i]};
+    double acc[4] = {lp[0], lp[1], lp[2], lp[3]};
+    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        HllSide S;
+        hll_side(Uc, d, c, tab, S);
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {   // 0: low face (c is R), 1: high face (c is L)
+            const int bcode = g.bc[2 * d + side];
+            const bool at_edge = side ? (pos[d] == ext[d] - 1) : (pos[d] == 0);
+            double m[4], Jc[4], cL[4], cR[4];
+            if (!at_edge || bcode == RT_BC_PERIODIC) {
+                long long nb;
+                if (!at_edge) nb = side ? i + step[d] : i - step[d];
+                else nb = side ? i - (long long)(ext[d] - 1) * step[d] : i + (long long)(ext[d] - 1) * step[d];
+                const double Un[4] = {Ng[nb], Fg[nb], Fg[g.stride + nb], Fg[2 * g.stride + nb]};
+                const double ln[4] = {lNg[nb], lFg[nb], lFg[g.stride + nb], lFg[2 * g.stride + nb]};
+                HllSide Sn;
+                hll_side(Un, d, c, tab, Sn);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) m[q] = side ? r * (ln[q] - lp[q]) : r * (lp[q] - ln[q]);
+                phi_vjp(Uc[0], Uc + 1, d, c, m, Jc);
+                if (side) hll_face_vjp(S, Sn, m, Jc, zero, true, false, cL, cR);
+                else hll_face_vjp(Sn, S, m, zero, Jc, false, true, cL, cR);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] += side ? cL[q] : cR[q];
+            } else {
+                // ghost B U_c (outflow: B = I; reflect: normal flux negated);
+                // it carries no lambda', and its side reaches c through B
+                double Ug[4] = {Uc[0], Uc[1], Uc[2], Uc[3]};
+                if (bcode == RT_BC_REFLECT) Ug[1 + d] = -Ug[1 + d];
+                HllSide Sg;
+                hll_side(Ug, d, c, tab, Sg);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) m[q] = side ? -r * lp[q] : r * lp[q];
+                double Jg[4];
+                phi_vjp(Uc[0], Uc + 1, d, c, m, Jc);
+                phi_vjp(Ug[0], Ug + 1, d, c, m, Jg);
+                if (side) hll_face_vjp(S, Sg, m, Jc, Jg, true, true, cL, cR);
+                else hll_face_vjp(Sg, S, m, Jg, Jc, true, true, cL, cR);
+                const double *self = side ? cL : cR, *gh = side ? cR : cL;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double gq = (bcode == RT_BC_REFLECT && q == 1 + d) ? -gh[q] : gh[q];
+                    acc[q] += self[q] + gq;
+                }
+            }
+        }
+    }
+    double *lNo = lN0 + go, *lFo = lF0 + 3 * go;
+    lNo[i] = acc[0];
+    lFo[i] = acc[1];
+    lFo[g.stride + i] = acc[2];
+    lFo[2 * g.stride + i] = acc[3];
+}
+
+// The forward update ends by rescaling F to c N where |F| came out above it
+// (rounding level for CFL <= 1, but it does happen where HLL keeps beams at
+// f = 1).  Its output is then exactly on |F| = c N, which is where it is
+// recognised here (|F|^2 >= (c N)^2 (1 - 1e-12)); the map F -> c N F/|F|
+// has the transpose lambda_N += c n.lambda_F, lambda_F -> (I - n n^T)
+// lambda_F, applied in place before the flux transpose.
+__global__ void clamp_vjp_kernel(long long n, double c, const double *__restrict__ N, const double *__restrict__ F,
+                                 double *lN, double *lF, long long nc)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // over G * nc
+    if (k >= n) return;
+    const long long g = k / nc, i = k % nc;
+    const double Nv = N[k];
+    const long long b = 3 * g * nc + i;
+    const double f0 = F[b], f1 = F[b + nc], f2 = F[b + 2 * nc];
+    const double F2 = f0 * f0 + f1 * f1 + f2 * f2;
+    const double cn = c * Nv;
+    if (!(Nv > kClosureFloorN) || !(F2 >= cn * cn * (1.0 - 1e-12))) return;
+    const double mag = sqrt(F2);
+    const double n0 = f0 / mag, n1 = f1 / mag, n2 = f2 / mag;
+    const double l0 = lF[b], l1 = lF[b + nc], l2 = lF[b + 2 * nc];
+    const double nl = n0 * l0 + n1 * l1 + n2 * l2;
+    lN[k] += c * nl;
+    lF[b] = l0 - n0 * nl;
+    lF[b + nc] = l1 - n1 * nl;
+    lF[b + 2 * nc] = l2 - n2 * nl;
+}
+
 // dJ/dL_{s,i} += lambda_a(N_i at the cell of source s) dt / V
 __global__ void inject_vjp_kernel(int nsrc, int G, long long nc, const long long *__restrict__ cells,
                                   const double *__restrict__ lN, double dt_over_V, double *g_L)
@@ -338,11 +570,23 @@ cudaError_t launch_thermo_vjp(const ThermoParams &tp, int G, const double *nH, c
 #undef RTGB_TVJP
 }
 
-cudaError_t launch_transport_vjp(const GridDev &g, int G, double cr, double dt, const double *N, const double *F,
-                                 const double *lN1, const double *lF1, double *lN0, double *lF0, cudaStream_t s)
+cudaError_t launch_transport_vjp(const GridDev &g, int G, int flux, double cr, double dt, const double *N,
+                                 const double *F, const double *hll_table, const double *lN1, const double *lF1,
+                                 double *lN0, double *lF0, cudaStream_t s)
 {
     dim3 grid((unsigned)((g.nc + 127) / 128), (unsigned)G);
-    transport_vjp_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, lN1, lF1, lN0, lF0);
+    if (flux == RT_HLL)
+        transport_vjp_hll_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, hll_table, lN1, lF1, lN0, lF0);
+    else
+        transport_vjp_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, lN1, lF1, lN0, lF0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clamp_vjp(int G, long long nc, double cr, const double *N, const double *F, double *lN, double *lF,
+                             cudaStream_t s)
+{
+    const long long n = (long long)G * nc;
+    clamp_vjp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, cr, N, F, lN, lF, nc);
     return cudaGetLastError();
 }
 

@@ -320,7 +320,9 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
     e = launch_thermo_vjp(tp, G, h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, NB, FB, lx, ly2, ly3, lT, lN, lF, lNb,
                           lFb, g_nH, sub_adj, h->status, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "thermo_vjp");
-    e = launch_transport_vjp(h->g, G, h->cr, dt, NA, FA, lNb, lFb, lN, lF, st);
+    e = launch_clamp_vjp(G, nc, h->cr, NB, FB, lNb, lFb, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "clamp_vjp");
+    e = launch_transport_vjp(h->g, G, h->opt.flux, h->cr, dt, NA, FA, h->hll, lNb, lFb, lN, lF, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "transport_vjp");
     e = launch_inject_vjp(h->nsrc_orig, G, nc, h->src_cell_orig, lN, dt / V, g_L, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "inject_vjp");
@@ -343,8 +345,8 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
 int vjp_args(rt_handle *h, double *dt, double *lx, double *ly2, double *ly3, double *lT, double *lN, double *lF,
              double *g_nH, double *g_L)
 {
-    if (h->opt.precision != RT_FP64 || h->opt.flux != RT_GLF || h->opt.smooth || !h->opt.otsa)
-        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64, flux RT_GLF, the OTSA and no smoothing");
+    if (h->opt.precision != RT_FP64 || h->opt.smooth || !h->opt.otsa)
+        return fail(h, RT_EINVAL, "the adjoint needs precision RT_FP64, the OTSA and no smoothing");
     if (!lx || !ly2 || !ly3 || !lT || !lN || !lF || !g_nH || (h->nsrc_orig > 0 && !g_L))
         return fail(h, RT_EINVAL, "null adjoint array");
     return check_dt(h, dt);

@@ -157,10 +157,16 @@ cudaError_t launch_thermo_vjp(const ThermoParams &tp, int G, const double *nH, c
                               const double *F, double *lx, double *ly2, double *ly3, double *lT,
                               const double *lN_in, const double *lF_in, double *lN_out, double *lF_out,
                               double *g_nH, int32_t *sub_out, unsigned *status, cudaStream_t s);
-// transport_vjp (GLF): lambda of the transported photons (lN1, lF1) -> lambda
-// of the photons before transport (lN0, lF0); N, F: the state before it.
-cudaError_t launch_transport_vjp(const GridDev &g, int G, double cr, double dt, const double *N, const double *F,
-                                 const double *lN1, const double *lF1, double *lN0, double *lF0, cudaStream_t s);
+// transport_vjp (GLF or HLL): lambda of the transported photons (lN1, lF1)
+// -> lambda of the photons before transport (lN0, lF0); N, F: the state
+// before it.
+cudaError_t launch_transport_vjp(const GridDev &g, int G, int flux, double cr, double dt, const double *N,
+                                 const double *F, const double *hll_table, const double *lN1, const double *lF1,
+                                 double *lN0, double *lF0, cudaStream_t s);
+// transpose of the |F| <= c N rescaling of the transport output N, F, in
+// place on lN, lF
+cudaError_t launch_clamp_vjp(int G, long long nc, double cr, const double *N, const double *F, double *lN, double *lF,
+                             cudaStream_t s);
 // g_L[s][i] += lN[i][cells[s]] dt / V for every source s (unmerged list)
 cudaError_t launch_inject_vjp(int nsrc, int G, long long nc, const long long *cells, const double *lN,
                               double dt_over_V, double *g_L, cudaStream_t s);
