@@ -26,7 +26,7 @@ SRC = os.path.join(HERE, "rt_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 GLF, HLL = 0, 1
-BC_OUTFLOW, BC_REFLECT, BC_PERIODIC = 0, 1, 2
+BC_OUTFLOW, BC_REFLECT, BC_PERIODIC, BC_INFLOW = 0, 1, 2, 3
 MAXG = 8
 
 RATE_NAMES = [
@@ -79,6 +79,7 @@ class OracleCfg(C.Structure):
         ("skip_thermo", C.c_int),
         ("smooth", C.c_int),
         ("rec_group", C.c_int * 3),
+        ("inflow", C.POINTER(C.c_double)),
     ]
 
 
@@ -154,7 +155,7 @@ class Problem:
     def __init__(self, shape, dx, G, cr, sigN, sigE, egy, X=1.0, isothermal=False,
                  otsa=True, flux=GLF, bc=(0, 0, 0, 0, 0, 0), a_exp=1.0,
                  max_subcycles=1_000_000, hll_table=None, nthreads=1, skip_thermo=False, smooth=False,
-                 rec_group=None):
+                 rec_group=None, inflow=None):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.G = int(G)
@@ -193,6 +194,11 @@ class Problem:
         rg = rec_group if rec_group is not None else [min(j, self.G - 1) for j in range(3)]
         for j in range(3):
             cfg.rec_group[j] = int(rg[j])
+        # faces with bc = BC_INFLOW hold the ghost state inflow[face][group]
+        # = (N, Fx, Fy, Fz)
+        self._inflow = (np.ascontiguousarray(inflow, dtype=np.float64).reshape(6, G, 4)
+                        if inflow is not None else None)
+        cfg.inflow = _dp(self._inflow) if self._inflow is not None else None
         self.cfg = cfg
 
     @property

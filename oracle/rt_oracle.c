@@ -320,11 +320,17 @@ static size_t cidx(const oracle_cfg *cfg, int i, int j, int k)
 
 /* Ghost state beyond a boundary face of direction d.  READING (no boundary
  * conditions are stated for the tests): outflow = zero-gradient copy,
- * reflect = copy with the normal flux component negated, periodic = wrap. */
+ * reflect = copy with the normal flux component negated, periodic = wrap,
+ * inflow = a given state (reading: the paper's fixed photon flux entering
+ * through a face, Sec. 6 test 3). */
 static void ghost_state(int bc, int d, const double Uin[4], const double Uwrap[4],
-                        double Ug[4])
+                        const double *Ufix, double Ug[4])
 {
-    if (bc == ORACLE_BC_PERIODIC) {
+    if (bc == ORACLE_BC_INFLOW) {
+        /* a face held at a given photon state (e.g. a plane-parallel flux
+         * entering the box), whatever the cells inside do */
+        for (int k = 0; k < 4; k++) Ug[k] = Ufix ? Ufix[k] : 0.0;
+    } else if (bc == ORACLE_BC_PERIODIC) {
         for (int k = 0; k < 4; k++) Ug[k] = Uwrap[k];
     } else {
         for (int k = 0; k < 4; k++) Ug[k] = Uin[k];
@@ -334,7 +340,7 @@ static void ghost_state(int bc, int d, const double Uin[4], const double Uwrap[4
 
 /* One transport step of one photon group in place.  N: [cells], F: [3][cells].
  * Returns the outflow (photons, outward positive) through the box faces. */
-static double transport_group(const oracle_cfg *cfg, double dt, double *N, double *F)
+static double transport_group(const oracle_cfg *cfg, double dt, double *N, double *F, int grp)
 {
     const int nx = cfg->nx, ny = cfg->ny, nz = cfg->nz;
     const size_t nc = (size_t)nx * ny * nz;
@@ -380,7 +386,9 @@ static double transport_group(const oracle_cfg *cfg, double dt, double *N, doubl
                             w[d] = lo ? nd - 1 : 0;
                             size_t cw = cidx(cfg, w[0], w[1], w[2]);
                             double Ug[4];
-                            ghost_state(bc, d, &U0[4 * cself], &U0[4 * cw], Ug);
+                            const int face = 2 * d + (lo ? 0 : 1);
+                            const double *fix = cfg->inflow ? cfg->inflow + 4 * ((size_t)face * cfg->G + grp) : NULL;
+                            ghost_state(bc, d, &U0[4 * cself], &U0[4 * cw], fix, Ug);
                             cell_quantities(cfg, Ug[0], Ug[1], Ug[2], Ug[3], &G);
                             if (lo) { L = &G; R = &Q[cself]; }
                             else    { L = &Q[cself]; R = &G; }
@@ -756,7 +764,7 @@ int oracle_step(const oracle_cfg *cfg, double dt, const double *nH, double *xHII
 
     /* 2. transport, every group independently */
     for (int i = 0; i < G; i++)
-        budget[4 * i + 2] = transport_group(cfg, dt, N + (size_t)i * nc, F + (size_t)3 * i * nc);
+        budget[4 * i + 2] = transport_group(cfg, dt, N + (size_t)i * nc, F + (size_t)3 * i * nc, i);
 
     /* 3. thermochemistry, each cell independently */
     if (!cfg->skip_thermo) {

@@ -9,7 +9,7 @@
 #define ORACLE_MAXG 8
 
 enum { ORACLE_GLF = 0, ORACLE_HLL = 1 };
-enum { ORACLE_BC_OUTFLOW = 0, ORACLE_BC_REFLECT = 1, ORACLE_BC_PERIODIC = 2 };
+enum { ORACLE_BC_OUTFLOW = 0, ORACLE_BC_REFLECT = 1, ORACLE_BC_PERIODIC = 2, ORACLE_BC_INFLOW = 3 };
 enum { ORACLE_OK = 0, ORACLE_EINVAL = -1, ORACLE_ESUBCYCLE = -3 };
 
 /* indices into the rate arrays filled by oracle_rates */
@@ -45,6 +45,7 @@ typedef struct {
     int smooth;             /* smoothed RT, Sec. 3.4 */
     int rec_group[3];       /* without OTSA: group that HII, HeII, HeIII
                                recombinations emit into (-1: none) */
+    const double *inflow;   /* [6][G][4] ghost (N, Fx, Fy, Fz) of inflow faces, or NULL (0) */
 } oracle_cfg;
 
 void oracle_rates(double T, double a_exp, int case_b, double *r, double *dr);
