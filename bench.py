@@ -34,10 +34,10 @@ UNIT = "cell-group updates/s"
 # measured by an FMA-chain probe on the same part.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # FP64 flops executed per thermochemistry attempt of the one-thread path:
-# ncu's smsp__sass_thread_inst_executed_op_d{fma x2, add, mul} of
-# thermo_pass1 on step 4 of cosmo128 (4.820e9) over the attempts that launch
-# made (2 104 447).
-FP64_FLOP_PER_ATTEMPT = 2290.0
+# ncu's smsp__sass_thread_inst_executed_op_d{fma x2, add, mul} over the ten
+# thermo_pass1 launches of the profiling pass of cosmo128 (3.017e10) over
+# the first-pass attempts of those steps (21 194 255).
+FP64_FLOP_PER_ATTEMPT = 1423.0
 PASS1_ATTEMPTS = 6
 DRAIN1_BUDGET = 192   # attempts a queued cell spends in the first lane-per-cell drain stage
 
@@ -283,6 +283,7 @@ def main():
     queued = 0
     queued_att = 0
     long_cells = 0
+    pass1_att = []
     sub = torch.empty(w.ncells, dtype=torch.int32, device="cuda")
     for _ in range(args.steps):
         sim.step(dt)
@@ -293,6 +294,7 @@ def main():
         queued += int(q.sum().item())
         queued_att += int((sub[q] - PASS1_ATTEMPTS).sum().item())
         long_cells += int((sub > PASS1_ATTEMPTS + DRAIN1_BUDGET).sum().item())
+        pass1_att.append(int(torch.clamp(sub, max=PASS1_ATTEMPTS).sum().item()))
     prof = sim.profile()
     sim.set_profiling(False)
     phases = {k: {"ms_total": round(v[0], 4), "launches": v[1],
@@ -508,6 +510,7 @@ def main():
                 "thermo_attempts": {"per_step": attempts / args.steps, "max_per_cell": att_max,
                                     "queued_cells_per_step": queued / args.steps,
                                     "cells_past_first_drain_per_step": long_cells / args.steps,
+                                    "first_pass_attempts_by_step": pass1_att,
                                     "queued_attempts_per_step": queued_att / args.steps}}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -51,7 +51,7 @@ extern "C" {
 
 #define RT_MAX_GROUPS 8
 
-enum { RT_BC_OUTFLOW = 0, RT_BC_REFLECT = 1, RT_BC_PERIODIC = 2 };
+enum { RT_BC_OUTFLOW = 0, RT_BC_REFLECT = 1, RT_BC_PERIODIC = 2, RT_BC_INFLOW = 3 };
 enum { RT_GLF = 0, RT_HLL = 1 };
 enum { RT_FP64 = 0, RT_MIXED = 1, RT_MIXED32 = 2 };
 #define RT_REC_BY_BAND -2
@@ -60,7 +60,9 @@ typedef struct rt_handle rt_handle;
 
 /* Uniform grid.  bc[] = boundary condition of the faces -x, +x, -y, +y, -z,
  * +z: outflow (zero-gradient ghost), reflect (ghost with the normal flux
- * component negated) or periodic. */
+ * component negated), periodic, or inflow (a ghost held at a given photon
+ * state, rt_set_inflow; zero until set; single-box handles only), e.g.
+ * the constant flux entering the box of the paper's Sec. 6 test 3. */
 typedef struct {
     int nx, ny, nz;
     double dx_cm;
@@ -137,6 +139,12 @@ int rt_get_state(rt_handle *h, double *nH, double *xHII, double *xHeII, double *
  * indices (x, y, z), L [n][G] photons/s, host pointers.  Sources sharing a
  * cell are merged (luminosities summed in the given order). */
 int rt_set_sources(rt_handle *h, int n, const int32_t *ijk, const double *L);
+
+/* Ghost state of an RT_BC_INFLOW face (0..5 = -x, +x, -y, +y, -z, +z):
+ * state [G][4] = (N photons/cm^3, Fx, Fy, Fz photons/cm^2/s) per group,
+ * host pointer, copied; |F| <= c_r N required.  RT_EINVAL if the face is
+ * not an inflow face or the state is not realisable. */
+int rt_set_inflow(rt_handle *h, int face, const double *state);
 
 /* Courant time step CFL dx / (3 c_r), Eq. (dt_courant). */
 int rt_courant_dt(const rt_handle *h, double *dt);

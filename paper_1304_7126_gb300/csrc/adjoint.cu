@@ -27,7 +27,8 @@
 // its co-flux mu = r (lambda'_R - lambda'_L) adds (J_L^T + c) mu/2 to
 // lambda_L and (J_R^T - c) mu/2 to lambda_R, J = dPhi_d/dU from the M1
 // closure (Sec. 2, Eqs. (edd2), (eddTens)).  Boundary ghosts are B U_c
-// (outflow: B = I; reflect: the normal flux negated) and carry no lambda'.
+// (outflow: B = I; reflect: the normal flux negated; inflow: a given state,
+// B = 0) and carry no lambda'.
 // With HLL (Eq. (hll)) the face flux also depends on the cells' tabulated
 // wave speeds; its transpose adds their derivatives (transport_vjp_hll).
 // The realisability rescaling of F that ends the forward update is
@@ -263,6 +264,7 @@ transport_vjp_kernel(GridDev g, double c, double r, const double *__restrict__ N
                     m[k] += 0.5 * mu[k];
                     acc[k] += side ? 0.5 * c * mu[k] : -0.5 * c * mu[k];
                 }
+                if (bcode == RT_BC_INFLOW) continue;   // a given ghost state: B = 0
                 // the ghost's side, through B (B^T = B)
                 const double sgn = side ? -0.5 * c : 0.5 * c;
                 if (bcode == RT_BC_REFLECT) {
@@ -425,7 +427,8 @@ __device__ __forceinline__ void hll_face_vjp(const HllSide &L, const HllSide &R,
 
 __global__ void __launch_bounds__(128)
 transport_vjp_hll_kernel(GridDev g, double c, double r, const double *__restrict__ N, const double *__restrict__ F,
-                         const double *__restrict__ tab, const double *__restrict__ lN1,
+                         const double *__restrict__ tab, const double *__restrict__ inflow,
+                         const double *__restrict__ lN1,
                          const double *__restrict__ lF1, double *__restrict__ lN0, double *__restrict__ lF0)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,6 +475,12 @@ transport_vjp_hll_kernel(GridDev g, double c, double r, const double *__restrict
                 // it carries no lambda', and its side reaches c through B
                 double Ug[4] = {Uc[0], Uc[1], Uc[2], Uc[3]};
                 if (bcode == RT_BC_REFLECT) Ug[1 + d] = -Ug[1 + d];
+                const bool fixed = bcode == RT_BC_INFLOW;   // a given ghost state: B = 0
+                if (fixed) {
+                    const int face = 2 * d + side;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) Ug[q] = inflow ? inflow[24 * blockIdx.y + 4 * face + q] : 0.0;
+                }
                 HllSide Sg;
                 hll_side(Ug, d, c, tab, Sg);
 #pragma unroll
@@ -484,7 +493,7 @@ transport_vjp_hll_kernel(GridDev g, double c, double r, const double *__restrict
                 const double *self = side ? cL : cR, *gh = side ? cR : cL;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const double gq = (bcode == RT_BC_REFLECT && q == 1 + d) ? -gh[q] : gh[q];
+                    const double gq = fixed ? 0.0 : ((bcode == RT_BC_REFLECT && q == 1 + d) ? -gh[q] : gh[q]);
                     acc[q] += self[q] + gq;
                 }
             }
@@ -571,12 +580,13 @@ cudaError_t launch_thermo_vjp(const ThermoParams &tp, int G, const double *nH, c
 }
 
 cudaError_t launch_transport_vjp(const GridDev &g, int G, int flux, double cr, double dt, const double *N,
-                                 const double *F, const double *hll_table, const double *lN1, const double *lF1,
-                                 double *lN0, double *lF0, cudaStream_t s)
+                                 const double *F, const double *hll_table, const double *inflow,
+                                 const double *lN1, const double *lF1, double *lN0, double *lF0, cudaStream_t s)
 {
     dim3 grid((unsigned)((g.nc + 127) / 128), (unsigned)G);
     if (flux == RT_HLL)
-        transport_vjp_hll_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, hll_table, lN1, lF1, lN0, lF0);
+        transport_vjp_hll_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, hll_table, inflow, lN1, lF1, lN0,
+                                                      lF0);
     else
         transport_vjp_kernel<<<grid, 128, 0, s>>>(g, cr, dt / g.dx, N, F, lN1, lF1, lN0, lF0);
     return cudaGetLastError();

@@ -33,6 +33,8 @@ struct rt_handle {
     float *Nf[2] = {nullptr, nullptr};   // RT_MIXED photon state
     float *Ff[2] = {nullptr, nullptr};
     void *Npre = nullptr, *Fpre = nullptr;   // smoothed RT: photon state before injection
+    double *inflow_d = nullptr;              // [G][6][4] ghost states of inflow faces
+    float *inflow_f = nullptr;
     bool mixed = false;
     int cur = 0;
     double *hll = nullptr;
@@ -122,7 +124,7 @@ void free_all(rt_handle *h)
     void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
                     h->Nf[0], h->Nf[1], h->Ff[0], h->Ff[1], h->hllf, h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
                     h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
-                    h->budget, h->status, h->src_cell, h->src_L, h->src_cell_orig, h->adj, h->adj_sub, h->Npre, h->Fpre,
+                    h->budget, h->status, h->src_cell, h->src_L, h->src_cell_orig, h->adj, h->adj_sub, h->Npre, h->Fpre, h->inflow_d, h->inflow_f,
                     h->adj_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -219,10 +221,10 @@ int enqueue_step(rt_handle *h, double dt, bool capturing = false)
     if (prof) { prof_pair(h, 1, &a, &b); cudaEventRecord(a, h->stream); }
     if (h->mixed)
         e = launch_transport_f32(h->g, h->G, h->opt.flux, h->cr, dt, h->Nf[h->cur], h->Ff[h->cur], h->Nf[nxt],
-                                 h->Ff[nxt], h->hllf, h->part, h->stream);
+                                 h->Ff[nxt], h->hllf, h->inflow_f, h->part, h->stream);
     else
         e = launch_transport(h->g, h->G, h->opt.flux, h->cr, dt, h->N[h->cur], h->F[h->cur], h->N[nxt],
-                             h->F[nxt], h->hll, h->part, h->stream);
+                             h->F[nxt], h->hll, h->inflow_d, h->part, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "transport");
     if (prof) cudaEventRecord(b, h->stream);
     h->cur = nxt;
@@ -313,7 +315,7 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
         e = launch_inject(h->nsrc, G, nc, h->src_cell, h->src_L, dt / V, NA, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "inject");
     }
-    e = launch_transport(h->g, G, h->opt.flux, h->cr, dt, NA, FA, NB, FB, h->hll, h->part, st);
+    e = launch_transport(h->g, G, h->opt.flux, h->cr, dt, NA, FA, NB, FB, h->hll, h->inflow_d, h->part, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "transport");
     ThermoParams tp = thermo_params(h, dt);
     int32_t *sub_adj = check ? h->adj_sub : nullptr;
@@ -322,7 +324,7 @@ int enqueue_vjp(rt_handle *h, double dt, double *lx, double *ly2, double *ly3, d
     if (e != cudaSuccess) return cuda_fail(h, e, "thermo_vjp");
     e = launch_clamp_vjp(G, nc, h->cr, NB, FB, lNb, lFb, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "clamp_vjp");
-    e = launch_transport_vjp(h->g, G, h->opt.flux, h->cr, dt, NA, FA, h->hll, lNb, lFb, lN, lF, st);
+    e = launch_transport_vjp(h->g, G, h->opt.flux, h->cr, dt, NA, FA, h->hll, h->inflow_d, lNb, lFb, lN, lF, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "transport_vjp");
     e = launch_inject_vjp(h->nsrc_orig, G, nc, h->src_cell_orig, lN, dt / V, g_L, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "inject_vjp");
@@ -391,7 +393,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     long long nc = (long long)grid->nx * grid->ny * grid->nz;
     if (nc >= (1LL << 31)) return RT_EINVAL;
     for (int i = 0; i < 6; ++i)
-        if (grid->bc[i] < RT_BC_OUTFLOW || grid->bc[i] > RT_BC_PERIODIC) return RT_EINVAL;
+        if (grid->bc[i] < RT_BC_OUTFLOW || grid->bc[i] > RT_BC_INFLOW) return RT_EINVAL;
     for (int d = 0; d < 3; ++d)   // periodic must be set on both faces of an axis
         if ((grid->bc[2 * d] == RT_BC_PERIODIC) != (grid->bc[2 * d + 1] == RT_BC_PERIODIC)) return RT_EINVAL;
     if (n_groups < 1 || n_groups > RT_MAX_GROUPS) return RT_EINVAL;
@@ -467,6 +469,12 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
                 cudaMemset(h->N[k], 0, G * nc * sizeof(double));
                 cudaMemset(h->F[k], 0, 3 * G * nc * sizeof(double));
             }
+        }
+        if ((rc = dalloc(h, &h->inflow_d, (size_t)24 * G))) goto bad;
+        cudaMemset(h->inflow_d, 0, 24 * G * sizeof(double));
+        if (h->mixed) {
+            if ((rc = dalloc(h, &h->inflow_f, (size_t)24 * G))) goto bad;
+            cudaMemset(h->inflow_f, 0, 24 * G * sizeof(float));
         }
         if (opt->smooth) {
             const size_t es = h->mixed ? sizeof(float) : sizeof(double);
@@ -691,6 +699,33 @@ int rt_set_sources(rt_handle *h, int n, const int32_t *ijk, const double *L)
         RT_CUDA(h, cudaMemcpy(h->src_cell_orig, oc.data(), n * sizeof(long long), cudaMemcpyHostToDevice));
     }
     h->nsrc_orig = n;
+    invalidate_graph(h);
+    return RT_OK;
+}
+
+int rt_set_inflow(rt_handle *h, int face, const double *state)
+{
+    if (!h) return RT_EINVAL;
+    if (face < 0 || face > 5 || !state) return fail(h, RT_EINVAL, "bad inflow face or null state");
+    if (h->g.bc[face] != RT_BC_INFLOW) return fail(h, RT_EINVAL, "face is not an RT_BC_INFLOW face");
+    const int G = h->G;
+    for (int g = 0; g < G; ++g) {
+        const double *u = state + 4 * g;
+        const double F2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+        const double cn = h->cr * u[0];
+        if (!std::isfinite(u[0]) || !std::isfinite(F2) || !(u[0] >= 0.0) || F2 > cn * cn * (1.0 + 2e-8) + 1e-290)
+            return fail(h, RT_EINVAL, "inflow state not realisable (needs N >= 0, |F| <= c_r N)");
+    }
+    RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::vector<double> buf((size_t)24 * G);
+    RT_CUDA(h, cudaMemcpy(buf.data(), h->inflow_d, buf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int g = 0; g < G; ++g)
+        for (int k = 0; k < 4; ++k) buf[(size_t)24 * g + 4 * face + k] = state[4 * g + k];
+    RT_CUDA(h, cudaMemcpy(h->inflow_d, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (h->inflow_f) {
+        std::vector<float> bf(buf.begin(), buf.end());
+        RT_CUDA(h, cudaMemcpy(h->inflow_f, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     invalidate_graph(h);
     return RT_OK;
 }

@@ -98,14 +98,15 @@ struct Partials {
 };
 
 // ---- launchers (defined in the .cu files) ----
-// transport: reads N0/F0, writes N1/F1 for all groups.
+// transport: reads N0/F0, writes N1/F1 for all groups.  inflow: NULL, or
+// the ghost states [G][6 faces][N, Fx, Fy, Fz] of RT_BC_INFLOW faces.
 cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
                              const double *N0, const double *F0, double *N1, double *F1,
-                             const double *hll_table, const Partials &p, cudaStream_t s);
+                             const double *hll_table, const double *inflow, const Partials &p, cudaStream_t s);
 // FP32 state (RT_MIXED): same scheme, compensated update.
 cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, double dt, const float *N0,
                                  const float *F0, float *N1, float *F1, const float *hll_table,
-                                 const Partials &p, cudaStream_t s);
+                                 const float *inflow, const Partials &p, cudaStream_t s);
 int transport_blocks_per_group(const GridDev &g);
 // Batched transport over items [item0, item0 + nitems) of one tile shape
 // (0: 32 x 8, 1: 16 x 16); N0/F0/N1/F1 are device arrays of per-class base
@@ -161,8 +162,8 @@ cudaError_t launch_thermo_vjp(const ThermoParams &tp, int G, const double *nH, c
 // -> lambda of the photons before transport (lN0, lF0); N, F: the state
 // before it.
 cudaError_t launch_transport_vjp(const GridDev &g, int G, int flux, double cr, double dt, const double *N,
-                                 const double *F, const double *hll_table, const double *lN1, const double *lF1,
-                                 double *lN0, double *lF0, cudaStream_t s);
+                                 const double *F, const double *hll_table, const double *inflow,
+                                 const double *lN1, const double *lF1, double *lN0, double *lF0, cudaStream_t s);
 // transpose of the |F| <= c N rescaling of the transport output N, F, in
 // place on lN, lF
 cudaError_t launch_clamp_vjp(int G, long long nc, double cr, const double *N, const double *F, double *lN, double *lF,

@@ -155,11 +155,26 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 
 // Load U at (x, y, z) where at most one coordinate may sit one cell outside
 // the box: that position is the boundary ghost (outflow: copy; reflect:
-// copy with the normal flux negated; periodic: wrap).
+// copy with the normal flux negated; periodic: wrap; inflow: the face's
+// given state).
+// inf: this group's inflow ghost states [6 faces][N, Fx, Fy, Fz], or NULL
 template <typename S>
-__device__ __forceinline__ void load_U(const GridDev &g, const S *__restrict__ N, const S *__restrict__ F, int x,
-                                       int y, int z, S &n, S &fx, S &fy, S &fz)
+__device__ __forceinline__ void load_U(const GridDev &g, const S *__restrict__ N, const S *__restrict__ F,
+                                       const S *__restrict__ inf, int x, int y, int z, S &n, S &fx, S &fy, S &fz)
 {
+    // a face held at a given state (RT_BC_INFLOW)
+    int face = -1;
+    if (x < 0) face = 0; else if (x >= g.nx) face = 1;
+    else if (y < 0) face = 2; else if (y >= g.ny) face = 3;
+    else if (z < 0) face = 4; else if (z >= g.nz) face = 5;
+    if (face >= 0 && g.bc[face] == RT_BC_INFLOW) {
+        if (inf) {
+            n = inf[4 * face]; fx = inf[4 * face + 1]; fy = inf[4 * face + 2]; fz = inf[4 * face + 3];
+        } else {
+            n = fx = fy = fz = (S)0;
+        }
+        return;
+    }
     int flip = -1;
     if (x < 0) {
         if (g.bc[0] == RT_BC_PERIODIC) x = g.nx - 1; else { x = 0; if (g.bc[0] == RT_BC_REFLECT) flip = 0; }
@@ -230,7 +245,8 @@ template <typename S, int FLUX, int TBX, int TBY>
 __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const GridDev &g, S c, S dtdx,
                                                const S *__restrict__ N0, const S *__restrict__ F0,
                                                S *__restrict__ N1, S *__restrict__ F1, const S *__restrict__ tab,
-                                               int x0, int y0, int z0, int z1, double &inbox, double &outflow)
+                                               const S *__restrict__ inf, int x0, int y0, int z0, int z1,
+                                               double &inbox, double &outflow)
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TBX + tx;
@@ -264,10 +280,10 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
     outflow = 0.0;
     if (active) {
         S n, fx, fy, fz;
-        load_U<S>(g, N0, F0, x, y, z0 - 1, n, fx, fy, fz);
+        load_U<S>(g, N0, F0, inf, x, y, z0 - 1, n, fx, fy, fz);
         CellQ<S> prev;
         closure<S, FLUX>(n, fx, fy, fz, c, tab, prev);
-        load_U<S>(g, N0, F0, x, y, z0, n, fx, fy, fz);
+        load_U<S>(g, N0, F0, inf, x, y, z0, n, fx, fy, fz);
         closure<S, FLUX>(n, fx, fy, fz, c, tab, cur);
         face_flux<S, FLUX, 2>(prev, cur, c, flo);
     }
@@ -275,21 +291,21 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
     for (int z = z0; z < z1; ++z) {
         if (active) {
             S n, fx, fy, fz;
-            load_U<S>(g, N0, F0, x, y, z + 1, n, fx, fy, fz);
+            load_U<S>(g, N0, F0, inf, x, y, z + 1, n, fx, fy, fz);
             closure<S, FLUX>(n, fx, fy, fz, c, tab, nxt);
             face_flux<S, FLUX, 2>(cur, nxt, c, fhi);
             put_plane<S, FLUX>(s, ty + 1, tx + 1, cur);
         } else if (ghost_slot) {
             S n, fx, fy, fz;
             CellQ<S> q;
-            load_U<S>(g, N0, F0, x, y, z, n, fx, fy, fz);
+            load_U<S>(g, N0, F0, inf, x, y, z, n, fx, fy, fz);
             closure<S, FLUX>(n, fx, fy, fz, c, tab, q);
             put_plane<S, FLUX>(s, ty + 1, tx + 1, q);
         }
         if (hvalid) {
             S n, fx, fy, fz;
             CellQ<S> q;
-            load_U<S>(g, N0, F0, hx, hy, z, n, fx, fy, fz);
+            load_U<S>(g, N0, F0, inf, hx, hy, z, n, fx, fy, fz);
             closure<S, FLUX>(n, fx, fy, fz, c, tab, q);
             put_plane<S, FLUX>(s, hr, hc, q);
         }
@@ -427,8 +443,8 @@ __device__ __forceinline__ void block_reduce2(double *red, double &a, double &b)
 template <typename S, int FLUX>
 __device__ __forceinline__ void transport_kernel_body(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
                  const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
-                 const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
-                 int tiles_x, int tiles_y, int nblk)
+                 const S *__restrict__ tab, const S *__restrict__ inflow, double *__restrict__ part_inbox,
+                 double *__restrict__ part_out, int tiles_x, int tiles_y, int nblk)
 {
     constexpr int TBX = 32, TBY = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -442,8 +458,8 @@ __device__ __forceinline__ void transport_kernel_body(GridDev g, S c, S dtdx, do
     double inbox, outflow;
     transport_tile<S, FLUX, TBX, TBY>(s, g, c, dtdx, N0all + (long long)grp * g.stride,
                                       F0all + 3LL * grp * g.stride, N1all + (long long)grp * g.stride,
-                                      F1all + 3LL * grp * g.stride, tab, tile_x * TBX, tile_y * TBY, z0,
-                                      min(z0 + TZC, g.nz), inbox, outflow);
+                                      F1all + 3LL * grp * g.stride, tab, inflow ? inflow + 24 * grp : nullptr,
+                                      tile_x * TBX, tile_y * TBY, z0, min(z0 + TZC, g.nz), inbox, outflow);
     block_reduce2<TBX * TBY>(&s.red[0][0], inbox, outflow);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         part_inbox[(long long)grp * nblk + tile] = inbox;
@@ -458,22 +474,23 @@ template <typename S, int FLUX>
 __global__ void __launch_bounds__(256)
 transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
                  const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
-                 const S *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
-                 int tiles_x, int tiles_y, int nblk)
+                 const S *__restrict__ tab, const S *__restrict__ inflow, double *__restrict__ part_inbox,
+                 double *__restrict__ part_out, int tiles_x, int tiles_y, int nblk)
 {
-    transport_kernel_body<S, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, part_inbox, part_out,
-                                   tiles_x, tiles_y, nblk);
+    transport_kernel_body<S, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, inflow, part_inbox,
+                                   part_out, tiles_x, tiles_y, nblk);
 }
 
 template <int FLUX>
 __global__ void __launch_bounds__(256, 3)
 transport_kernel_f32(GridDev g, float c, float dtdx, double area_dt, const float *__restrict__ N0all,
                      const float *__restrict__ F0all, float *__restrict__ N1all, float *__restrict__ F1all,
-                     const float *__restrict__ tab, double *__restrict__ part_inbox, double *__restrict__ part_out,
-                     int tiles_x, int tiles_y, int nblk)
+                     const float *__restrict__ tab, const float *__restrict__ inflow,
+                     double *__restrict__ part_inbox, double *__restrict__ part_out, int tiles_x, int tiles_y,
+                     int nblk)
 {
-    transport_kernel_body<float, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, part_inbox, part_out,
-                                       tiles_x, tiles_y, nblk);
+    transport_kernel_body<float, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, inflow, part_inbox,
+                                       part_out, tiles_x, tiles_y, nblk);
 }
 
 // Batched boxes: CTA i works on item i (box, group, tile, z range) of a
@@ -495,8 +512,8 @@ transport_batch_kernel(const BatchItem *__restrict__ items, const BatchBox *__re
     const long long fbase = 3LL * w.grp * b.g.stride + b.cell_off;
     double inbox, outflow;
     transport_tile<S, FLUX, TBX, TBY>(s, b.g, c, dtdx, N0cls[b.cls] + base, F0cls[b.cls] + fbase,
-                                      N1cls[b.cls] + base, F1cls[b.cls] + fbase, tab, w.x0, w.y0, w.z0, w.z1,
-                                      inbox, outflow);
+                                      N1cls[b.cls] + base, F1cls[b.cls] + fbase, tab, nullptr, w.x0, w.y0, w.z0,
+                                      w.z1, inbox, outflow);
     block_reduce2<TBX * TBY>(&s.red[0][0], inbox, outflow);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         part_inbox[it] = inbox;
@@ -537,7 +554,7 @@ void transport_init()
 
 template <typename S>
 static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double dt, const S *N0, const S *F0,
-                            S *N1, S *F1, const S *tab, const Partials &p, cudaStream_t st)
+                            S *N1, S *F1, const S *tab, const S *inflow, const Partials &p, cudaStream_t st)
 {
     int tiles_x = (g.nx + 31) / 32;
     int tiles_y = (g.ny + 7) / 8;
@@ -549,17 +566,17 @@ static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double
     double area_dt = g.dx * g.dx * dt;
     if constexpr (sizeof(S) == sizeof(float)) {
         if (flux == RT_HLL)
-            transport_kernel_f32<RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+            transport_kernel_f32<RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
                                                                     p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
         else
-            transport_kernel_f32<RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+            transport_kernel_f32<RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
                                                                     p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
     } else {
         if (flux == RT_HLL)
-            transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+            transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
                                                                    p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
         else
-            transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+            transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
                                                                    p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
     }
     return cudaGetLastError();
@@ -567,16 +584,16 @@ static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double
 
 cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, double dt,
                              const double *N0, const double *F0, double *N1, double *F1,
-                             const double *hll_table, const Partials &p, cudaStream_t st)
+                             const double *hll_table, const double *inflow, const Partials &p, cudaStream_t st)
 {
-    return launch_t<double>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, p, st);
+    return launch_t<double>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, inflow, p, st);
 }
 
 cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, double dt, const float *N0,
                                  const float *F0, float *N1, float *F1, const float *hll_table,
-                                 const Partials &p, cudaStream_t st)
+                                 const float *inflow, const Partials &p, cudaStream_t st)
 {
-    return launch_t<float>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, p, st);
+    return launch_t<float>(g, G, flux, cr, dt, N0, F0, N1, F1, hll_table, inflow, p, st);
 }
 
 template <typename S>

@@ -17,7 +17,7 @@ from . import _build
 
 RT_OK, RT_EINVAL, RT_EDT, RT_ESUBCYCLE, RT_EQUEUE, RT_ECUDA, RT_ENOMEM, RT_ENONFINITE = \
     0, -1, -2, -3, -4, -5, -6, -7
-RT_BC_OUTFLOW, RT_BC_REFLECT, RT_BC_PERIODIC = 0, 1, 2
+RT_BC_OUTFLOW, RT_BC_REFLECT, RT_BC_PERIODIC, RT_BC_INFLOW = 0, 1, 2, 3
 RT_GLF, RT_HLL = 0, 1
 RT_FP64, RT_MIXED, RT_MIXED32 = 0, 1, 2
 RT_REC_BY_BAND = -2
@@ -78,6 +78,7 @@ def load(build: bool = True):
     L.rt_hll_table.argtypes = [C.c_int, C.c_int, dp]
     L.rt_version.argtypes = []
     L.rt_fmath_eval.argtypes = [C.c_int, C.c_longlong, dp, dp, vp]
+    L.rt_set_inflow.argtypes = [vp, C.c_int, dp]
     L.rt_step_vjp.argtypes = [vp, C.c_double, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_run_vjp.argtypes = [vp, C.c_double, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_thermo_step_noalloc.argtypes = [C.c_longlong, C.c_int, C.POINTER(rt_options), C.c_double, dp, dp,
@@ -235,6 +236,11 @@ class RT:
         l = np.ascontiguousarray(L, dtype=np.float64).reshape(a.shape[0], self.G)
         self._check(self.L.rt_set_sources(self.h, a.shape[0], _ptr(a), _ptr(l)), "rt_set_sources")
 
+    def set_inflow(self, face: int, state):
+        """Ghost state [G][4] = (N, Fx, Fy, Fz) of an RT_BC_INFLOW face."""
+        a = np.ascontiguousarray(state, dtype=np.float64).reshape(self.G, 4)
+        self._check(self.L.rt_set_inflow(self.h, int(face), _ptr(a)), "rt_set_inflow")
+
     def courant_dt(self) -> float:
         d = C.c_double()
         self._check(self.L.rt_courant_dt(self.h, C.byref(d)), "rt_courant_dt")
@@ -297,6 +303,11 @@ class RT:
         r = cls(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, bc=w.bc, **o)
         r.set_state(w.state())
         r.set_sources(w.src_ijk, w.src_L)
+        inflow = w.extra.get("inflow") if w.extra else None
+        if inflow is not None:
+            for face in range(6):
+                if w.bc[face] == RT_BC_INFLOW:
+                    r.set_inflow(face, inflow[face])
         return r
 
 

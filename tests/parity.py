@@ -19,6 +19,8 @@ def rel_err(g, o):
 
 
 def oracle_problem(O, w, **kw):
+    if w.extra and w.extra.get("inflow") is not None and "inflow" not in kw:
+        kw["inflow"] = w.extra["inflow"]
     return O.Problem(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, X=w.X,
                      isothermal=w.isothermal, otsa=w.otsa, flux=w.flux, bc=w.bc, **kw)
 
