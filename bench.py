@@ -217,6 +217,7 @@ def main():
                          "outflow rate and absorption empty them within a step sub-cycle without end under the "
                          "10%% rule with its 1e-30 floor")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the adjoint")
+    ap.add_argument("--no-shadow", action="store_true", help="skip the dense-cloud shadow workload")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -455,6 +456,35 @@ def main():
                                 "workload": "256^3, 3 groups, seed 11, 64 sources of 1e52/s, HLL, c_r=c/10",
                                 "tolerance": {"x_abs": 1e-4, "T_rel": 1e-3, "N_rel": 1e-4}, **res}
         del fin, ref, init3
+
+    # ---- the dense-cloud shadow workload (Sec. 6 test 3 on a uniform 128^3
+    # grid): a constant flux entering through x = 0, HLL, FP64 ----
+    if not args.no_shadow:
+        from paper_1304_7126_gb300 import workloads as W
+        w6 = W.shadow(128)
+        k6 = min(args.steps, 200)
+        s6 = R.RT.from_workload(w6)
+        s6.set_stream(stream.cuda_stream)
+        dt6 = s6.courant_dt()
+        s6.run(dt6, 3)
+        init6 = {k: torch.from_numpy(v).cuda() for k, v in w6.state().items()}
+        s6.set_state(init6)
+        s6.sync()
+        barrier()
+        ev0.record(stream)
+        s6.run(dt6, k6)
+        ev1.record(stream)
+        ev1.synchronize()
+        s6.sync()
+        t6 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        sub6 = s6.subcycles()
+        variants["shadow128"] = {
+            "value": w6.ncells * w6.G * k6 * ws / t6, "ms_per_step": 1e3 * t6 / k6, "steps": k6,
+            "last_step_attempts": {"total": int(sub6.sum()), "max": int(sub6.max())},
+            "workload": "128^3, box 6.6 kpc, cloud r = 0.8 kpc (n_H 4e-2, 40 K) in n_H 2e-4, 8000 K, H only, "
+                        "3 groups, 1e6 photons/cm^2/s entering through x = 0, HLL, c_r = c/10, FP64"}
+        s6.close()
+        del init6
 
     # ---- adjoint: 64^3, 3 groups, 8 sources, GLF, FP64; forward with a checkpoint
     # every 20 steps, then the backward pass (recompute + hand-written VJPs) ----
