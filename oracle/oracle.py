@@ -237,6 +237,26 @@ class Problem:
             sub.ctypes.data_as(C.POINTER(C.c_int32)), _dp(mg))
         return st, budget, sub.reshape(self.shape), mg.reshape(self.shape)
 
+    def expand(self, state: dict, a_new: float):
+        """Change the expansion factor to a_new (Sec. 5, cosmological
+        settings).  The photon state is kept in the super-comoving
+        variables N~ = a^3 N, F~ = a^4 F / (H0 L) and the gas at constant
+        comoving density, so in physical units N scales by (a/a_new)^3, F by
+        (a/a_new)^4 and n_H by (a/a_new)^3; the physical cell width becomes
+        a_new times the comoving one, and the Compton term takes
+        T_gamma = 2.727 / a_new.  With a fixed between two changes, the
+        transport equations in those variables are the physical ones at
+        that cell width, so the steps themselves are unchanged.  (The
+        adiabatic cooling of the gas belongs to the hydrodynamics and is
+        not applied.)  state is modified in place."""
+        a_old = float(self.cfg.a_exp)
+        r = a_old / float(a_new)
+        state["N"] *= r ** 3
+        state["F"] *= r ** 4
+        state["nH"] *= r ** 3
+        self.cfg.dx = float(self.cfg.dx) / r
+        self.cfg.a_exp = float(a_new)
+
     def thermo_cell(self, dt: float, nH: float, s, N, F, fixed_photons=False, Ndot=None, Fdot=None):
         """Sub-cycle one cell over dt.  s = [x_HII, x_HeII, x_HeIII, T];
         N [G]; F [G][3]; Ndot [G], Fdot [G][3]: smoothed-RT rates (Sec. 3.4)
