@@ -146,6 +146,19 @@ int rt_set_sources(rt_handle *h, int n, const int32_t *ijk, const double *L);
  * not an inflow face or the state is not realisable. */
 int rt_set_inflow(rt_handle *h, int face, const double *state);
 
+/* Change the expansion factor to a (Sec. 5, cosmological settings).  The
+ * photons are kept in the super-comoving variables N~ = a^3 N,
+ * F~ = a^4 F / (H0 L) and the gas at constant comoving density, so the
+ * physical N, F and n_H held by the handle scale by (a_old/a)^3,
+ * (a_old/a)^4 and (a_old/a)^3; the physical cell width becomes
+ * dx * a / a_old and the Compton term takes T_gamma = 2.727 / a.  Between
+ * two changes the super-comoving transport equations are the physical
+ * ones at that cell width, so rt_step is unchanged (the Courant dt follows
+ * dx).  a_old is the previous value, initially rt_options.a_exp.  The
+ * adiabatic cooling of the gas is not applied (it belongs to the
+ * hydrodynamics).  Needs a state; enqueued on the handle's stream. */
+int rt_set_scale_factor(rt_handle *h, double a);
+
 /* Courant time step CFL dx / (3 c_r), Eq. (dt_courant). */
 int rt_courant_dt(const rt_handle *h, double *dt);
 

@@ -26,6 +26,14 @@ __global__ void inject_kernel(int nsrc, int G, long long nc, const long long *__
     }
 }
 
+// x[i] *= f for i < n (the dilution of a change of expansion factor)
+template <typename P>
+__global__ void scale_kernel(long long n, double f, P *x)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = (P)((double)x[i] * f);
+}
+
 template <typename A, typename B>
 __global__ void convert_kernel(long long n, const A *__restrict__ in, B *__restrict__ out)
 {
@@ -141,6 +149,19 @@ cudaError_t launch_reduce_N_f32(int G, long long nc, const float *N, const Parti
     reduce_N_kernel<float><<<grid, RB, 0, s>>>(nc, N, p.th_inbox);
     return cudaGetLastError();
 }
+
+template <typename P>
+static cudaError_t launch_scale_t(long long n, double f, P *x, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    scale_kernel<P><<<(unsigned)b, 256, 0, s>>>(n, f, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(long long n, double f, double *x, cudaStream_t s) { return launch_scale_t(n, f, x, s); }
+cudaError_t launch_scale_f32(long long n, double f, float *x, cudaStream_t s) { return launch_scale_t(n, f, x, s); }
 
 cudaError_t launch_convert_d2f(long long n, const double *in, float *out, cudaStream_t s)
 {

@@ -730,6 +730,31 @@ int rt_set_inflow(rt_handle *h, int face, const double *state)
     return RT_OK;
 }
 
+int rt_set_scale_factor(rt_handle *h, double a)
+{
+    if (!h) return RT_EINVAL;
+    if (!(a > 0.0) || !std::isfinite(a)) return fail(h, RT_EINVAL, "expansion factor must be > 0");
+    if (!h->state_set) return fail(h, RT_EINVAL, "rt_set_state has not been called");
+    const double r = h->opt.a_exp / a;
+    if (r == 1.0) return RT_OK;
+    const long long nc = h->g.nc;
+    const int G = h->G;
+    cudaError_t e;
+    if (h->mixed) {
+        e = launch_scale_f32((long long)G * nc, r * r * r, h->Nf[h->cur], h->stream);
+        if (e == cudaSuccess) e = launch_scale_f32(3LL * G * nc, r * r * r * r, h->Ff[h->cur], h->stream);
+    } else {
+        e = launch_scale((long long)G * nc, r * r * r, h->N[h->cur], h->stream);
+        if (e == cudaSuccess) e = launch_scale(3LL * G * nc, r * r * r * r, h->F[h->cur], h->stream);
+    }
+    if (e == cudaSuccess) e = launch_scale(nc, r * r * r, h->nH, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "scale");
+    h->g.dx /= r;
+    h->opt.a_exp = a;
+    invalidate_graph(h);
+    return RT_OK;
+}
+
 int rt_courant_dt(const rt_handle *h, double *dt)
 {
     if (!h || !dt) return RT_EINVAL;

@@ -146,6 +146,8 @@ cudaError_t launch_inject_f32(int nsrc, int G, long long nc, const long long *ce
                               double dt_over_V, float *N, cudaStream_t s);
 cudaError_t launch_reduce_N_f32(int G, long long nc, const float *N, const Partials &p, cudaStream_t s);
 cudaError_t launch_convert_d2f(long long n, const double *in, float *out, cudaStream_t s);
+cudaError_t launch_scale(long long n, double f, double *x, cudaStream_t s);        // x *= f
+cudaError_t launch_scale_f32(long long n, double f, float *x, cudaStream_t s);
 cudaError_t launch_convert_f2d(long long n, const float *in, double *out, cudaStream_t s);
 
 // ---- adjoint (adjoint.cu) ----

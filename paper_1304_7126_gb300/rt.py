@@ -79,6 +79,7 @@ def load(build: bool = True):
     L.rt_version.argtypes = []
     L.rt_fmath_eval.argtypes = [C.c_int, C.c_longlong, dp, dp, vp]
     L.rt_set_inflow.argtypes = [vp, C.c_int, dp]
+    L.rt_set_scale_factor.argtypes = [vp, C.c_double]
     L.rt_step_vjp.argtypes = [vp, C.c_double, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_run_vjp.argtypes = [vp, C.c_double, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_longlong)]
     L.rt_thermo_step_noalloc.argtypes = [C.c_longlong, C.c_int, C.POINTER(rt_options), C.c_double, dp, dp,
@@ -240,6 +241,10 @@ class RT:
         """Ghost state [G][4] = (N, Fx, Fy, Fz) of an RT_BC_INFLOW face."""
         a = np.ascontiguousarray(state, dtype=np.float64).reshape(self.G, 4)
         self._check(self.L.rt_set_inflow(self.h, int(face), _ptr(a)), "rt_set_inflow")
+
+    def set_scale_factor(self, a: float):
+        """rt_set_scale_factor: change the expansion factor to a."""
+        self._check(self.L.rt_set_scale_factor(self.h, float(a)), "rt_set_scale_factor")
 
     def courant_dt(self) -> float:
         d = C.c_double()
