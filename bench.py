@@ -178,25 +178,40 @@ def _config(w):
             "l2": "inputs larger than L2 (state %.0f MB)" % ((5 + 8 * w.G) * w.ncells * 8 / 1e6)}
 
 
+# kernels each profiled phase of one RT step launches (the thermochemistry
+# drain phase: two lane-per-cell drains and the warp-per-cell kernel)
+KERNELS_PER_PHASE = {"inject": 1, "transport": 1, "thermo_pass1": 1, "thermo_drain": 3, "reduce": 1, "finalize": 1}
+
+
 def cpu_baseline(w, seconds_hint=20.0):
     """The oracle on this host's cores: RT steps of the full workload from its
-    initial state (as many as fit the hint, at least one)."""
+    initial state (as many as fit the hint, at least one), with its cells
+    spread over all cores, then one step of the same on a single thread."""
     from oracle import oracle as O
     cores = os.cpu_count() or 1
-    p = O.Problem(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, X=w.X, isothermal=w.isothermal,
-                  otsa=w.otsa, flux=w.flux, bc=w.bc, nthreads=cores)
-    dt = O.courant_dt(w.cfl, w.dx, w.cr)
-    s = w.state()
-    n = 0
-    t0 = time.perf_counter()
-    while True:
-        p.step(s, dt, w.src_ijk, w.src_L)
-        n += 1
-        if time.perf_counter() - t0 > seconds_hint or n >= 3:
-            break
-    t = time.perf_counter() - t0
-    return {"value": w.ncells * w.G * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d RT step(s) of the same %s workload from its initial state" % (n, w.name)}
+
+    def timed(nthreads, max_steps):
+        p = O.Problem(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, X=w.X, isothermal=w.isothermal,
+                      otsa=w.otsa, flux=w.flux, bc=w.bc, nthreads=nthreads)
+        dt = O.courant_dt(w.cfl, w.dx, w.cr)
+        s = w.state()
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            p.step(s, dt, w.src_ijk, w.src_L)
+            n += 1
+            if time.perf_counter() - t0 > seconds_hint or n >= max_steps:
+                break
+        return n, time.perf_counter() - t0
+
+    n, t = timed(cores, 3)
+    out = {"value": w.ncells * w.G * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "first %d RT step(s) of the same %s workload from its initial state" % (n, w.name)}
+    if cores > 1:
+        n1, t1 = timed(1, 1)
+        out["single_thread"] = {"value": w.ncells * w.G * n1 / t1, "unit": UNIT, "cores": 1,
+                                "sample": "first RT step of the same workload, one thread"}
+    return out
 
 
 def main():
@@ -535,7 +550,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clocks, "phases": phases,
+                "gpu_launches": sum(KERNELS_PER_PHASE[k] * v[1] for k, v in prof.items()), "clocks": clocks,
+                "phases": phases,
                 "variants": variants,
                 "thermo_attempts": {"per_step": attempts / args.steps, "max_per_cell": att_max,
                                     "queued_cells_per_step": queued / args.steps,

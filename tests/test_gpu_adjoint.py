@@ -9,7 +9,8 @@ and the torch.autograd.Function on top) against finite differences.
   injection;
 * one full step (H+He, evolving T, sources): the same directional check
   over every field and n_H, the sub-cycle schedule identical in the +/- runs
-  and in the adjoint's recomputation;
+  and in the adjoint's recomputation; for HLL the photons of cells at a
+  face with tied wave speeds (a kink of the step) are left unperturbed;
 * several steps against the oracle's central-difference gradient of the
   neutral hydrogen mass (oracle/fd.py) with respect to n_H and the source
   luminosities;
@@ -136,11 +137,10 @@ def _evolved_cosmo(R, n, steps, seed=3, nsrc=2, flux=0):
     return w, sim, dt, sim.get_state()
 
 
-@pytest.mark.parametrize("flux", [0, pytest.param(1, marks=pytest.mark.xfail(
-    reason="HLL: 7e-5 (transport only) to 1e-3 (full step) off the central difference on an evolved state; "
-           "per-cell checks trace it to cells ~100x above the 1e-30 closure floor", strict=False))])
-def test_full_step_vjp_directional(R, flux):
+@pytest.mark.parametrize("flux", [0, 1])
+def test_full_step_vjp_directional(R, oracle_mod, flux):
     import torch
+    from parity import hll_tie_cells
     w, sim, dt, s0 = _evolved_cosmo(R, 10, 3, flux=flux)
     nc, G = w.ncells, w.G
     rng = np.random.default_rng(7)
@@ -152,6 +152,16 @@ def test_full_step_vjp_directional(R, flux):
     u = {"N": s0["N"] * rng.standard_normal(G * nc), "F": s0["F"] * rng.standard_normal(3 * G * nc) * 0.1,
          "xHII": np.minimum(s0["xHII"] - 1e-6, 1 - s0["xHII"]) * rng.standard_normal(nc),
          "T": s0["T"] * rng.standard_normal(nc), "nH": s0["nH"] * rng.standard_normal(nc)}
+    if flux == 1:
+        # HLL: at a face whose wave speeds tie (the photon front fills cells
+        # with equal F/N) the step is only one-sidedly differentiable and a
+        # central difference averages two slopes; move the photons of the
+        # other cells only.  The tied cells exist (the front has reached
+        # empty cells) but are few.
+        tie = hll_tie_cells(oracle_mod, w, s0)
+        assert 0 < tie.sum() < nc // 20
+        for k in ("N", "F"):
+            u[k] = u[k] * np.tile(~tie, u[k].size // nc)
 
     def J(eps):
         s = {k: a.copy() for k, a in s0.items()}
