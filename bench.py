@@ -105,6 +105,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest x over the ranks of the default process group (x itself
+    on one rank): the job's time is its slowest rank's."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_units(units_per_rank, ws):
+    """Cell-group updates of the whole job: every rank runs its own replica
+    of the workload (weak scaling, no exchange between ranks)."""
+    return units_per_rank * ws
+
+
 def workload(name):
     from paper_1304_7126_gb300 import workloads as W
     return {"cosmo128": W.cosmo128, "stromgren32": W.stromgren32, "cosmo256": W.cosmo256}[name]()
@@ -262,14 +280,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # warm-up (also captures the CUDA graph of a pair of steps)
     sim.run(dt, max(args.warmup, 3))
     sim.sync()
@@ -286,8 +296,8 @@ def main():
         ev1.synchronize()
     barrier()
     sim.sync()
-    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
-    units = w.ncells * w.G * args.steps * ws
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
+    units = job_units(w.ncells * w.G * args.steps, ws)
     value = units / t
     clocks = clk.summary()
 
@@ -359,7 +369,7 @@ def main():
             sim.get_state(cur_out)          # D2H of the step's result
             cur_in, cur_out = cur_out, cur_in
         barrier()
-        te = max_over_ranks(time.perf_counter() - t0)
+        te = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
         e2e = {"value": units / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "how": "per step: rt_set_state from pinned host buffers, rt_step, rt_get_state to pinned host"}
 
@@ -381,7 +391,7 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         simm.sync()
-        tm = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        tm = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
         simm.set_state(dev_init)
         simm.set_profiling(True)
         for _ in range(args.steps):
@@ -421,10 +431,10 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         bt.sync()
-        tb = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        tb = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
         cgb = sum(wb.ncells * wb.G for wb in boxes)
         variants["batched%d" % len(boxes)] = {
-            "value": cgb * kb * ws / tb, "ms_per_step": 1e3 * tb / kb, "steps": kb, "cell_groups": cgb,
+            "value": job_units(cgb * kb, ws) / tb, "ms_per_step": 1e3 * tb / kb, "steps": kb, "cell_groups": cgb,
             "cells": sum(wb.ncells for wb in boxes), "precision": "mixed (FP32 transport, FP64 thermochemistry)",
             "workload": "%d boxes, side in {16,24,32,48,64}, 1 or 3 groups, HLL, c_r=c/100" % len(boxes)}
         bt.close()
@@ -452,9 +462,9 @@ def main():
             ev1.record(stream)
             ev1.synchronize()
             s3.sync()
-            t3 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+            t3 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
             fin[name] = s3.get_state(device=True)
-            res[name] = {"value": cg3 * k3 * ws / t3, "ms_per_step": 1e3 * t3 / k3}
+            res[name] = {"value": job_units(cg3 * k3, ws) / t3, "ms_per_step": 1e3 * t3 / k3}
             s3.close()
         ref = fin["fp64"]
         nmax = float(ref["N"].abs().max())
@@ -491,10 +501,10 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         s6.sync()
-        t6 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        t6 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
         sub6 = s6.subcycles()
         variants["shadow128"] = {
-            "value": w6.ncells * w6.G * k6 * ws / t6, "ms_per_step": 1e3 * t6 / k6, "steps": k6,
+            "value": job_units(w6.ncells * w6.G * k6, ws) / t6, "ms_per_step": 1e3 * t6 / k6, "steps": k6,
             "last_step_attempts": {"total": int(sub6.sum()), "max": int(sub6.max())},
             "workload": "128^3, box 6.6 kpc, cloud r = 0.8 kpc (n_H 4e-2, 40 K) in n_H 2e-4, 8000 K, H only, "
                         "3 groups, 1e6 photons/cm^2/s entering through x = 0, HLL, c_r = c/10, FP64"}
@@ -529,10 +539,10 @@ def main():
         fwd_bwd(3)
         barrier()
         tf, tb, gnh, gl = fwd_bwd(k5)
-        tf, tb = max_over_ranks(tf), max_over_ranks(tb)
+        tf, tb = max_over_ranks(tf, ws, "cuda"), max_over_ranks(tb, ws, "cuda")
         cg5 = w5.ncells * w5.G
         variants["adjoint64"] = {
-            "value": cg5 * k5 * ws / (tf + tb), "unit": UNIT + " (forward + backward)", "steps": k5,
+            "value": job_units(cg5 * k5, ws) / (tf + tb), "unit": UNIT + " (forward + backward)", "steps": k5,
             "checkpoint_every": 20, "forward_s": tf, "backward_s": tb, "backward_over_forward": tb / tf,
             "grad_L_per_source": (gl * (Ld / Ld.sum(dim=1, keepdim=True))).sum(dim=1).tolist(),
             "grad_nH_abs_max": float(gnh.abs().max()),
