@@ -310,11 +310,13 @@ int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_options *opt
                            const double *nH, double *xHII, double *xHeII, double *xHeIII,
                            double *T, double *N, double *F, int32_t *subcycles, void *stream);
 
-/* The FP64 exp (fn 0), log (fn 1) and log1p (fn 2) that the library's
- * rate fits use (table-driven, Tang 1989/1990), applied to n values:
- * y[i] = f(x[i]); x, y device pointers, enqueued on `stream` (NULL: the
- * default stream), no synchronisation.  For accuracy checks against
- * CUDA's own functions.  RT_EINVAL for a bad fn or null arrays. */
+/* The exp (fn 0), log (fn 1), log1p (fn 2), reciprocal (fn 3) and square
+ * root (fn 4) that the library's FP64 rate fits use (double-float
+ * arithmetic on float pairs, table-driven exp and log after Tang
+ * 1989/1990), applied to n doubles: y[i] = f(x[i]); x, y device pointers,
+ * enqueued on `stream` (NULL: the default stream), no synchronisation.
+ * For accuracy checks against CUDA's own functions.  RT_EINVAL for a bad
+ * fn or null arrays. */
 int rt_fmath_eval(int fn, long long n, const double *x, double *y, void *stream);
 
 /* Library version (major * 10000 + minor * 100 + patch). */

@@ -1,19 +1,30 @@
-// rt_fmath_eval: the table-driven exp, log and log1p of fmath.cuh over a
-// device array, so that their accuracy can be checked against CUDA's own.
+// rt_fmath_eval: the double-float exp, log, log1p, reciprocal and square
+// root of dfmath.cuh (the ones the FP64 rate fits use) over a device array
+// of doubles, so that their accuracy can be checked against CUDA's own.
 #include <cuda_runtime.h>
 
-#include "fmath.cuh"
+#include "dfmath.cuh"
 #include "rt.h"
 
 namespace rtgb {
 namespace {
 
+__device__ double eval_one(int fn, double v)
+{
+    using namespace dfm;
+    switch (fn) {
+    case 0: return splittable(v) ? exp2d(split(v)) : exp(v);
+    case 1: return to_double(logd(v));
+    case 2: return (v >= 0.0 && !splittable(v)) ? log1p(v) : to_double(log1pd(v));
+    case 3: return (v > 0.0 && splittable(v)) ? to_double(rcp(split(v))) : 1.0 / v;
+    default: return (v > 0.0 && splittable(v)) ? to_double(sqrt2(split(v))) : sqrt(v);
+    }
+}
+
 __global__ void fmath_kernel(int fn, long long n, const double *__restrict__ x, double *__restrict__ y)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double v = x[i];
-        y[i] = fn == 0 ? fm::exp_t(v) : (fn == 1 ? fm::log_t(v) : fm::log1p_t(v));
-    }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = eval_one(fn, x[i]);
 }
 
 }  // namespace
@@ -21,7 +32,7 @@ __global__ void fmath_kernel(int fn, long long n, const double *__restrict__ x, 
 
 extern "C" int rt_fmath_eval(int fn, long long n, const double *x, double *y, void *stream)
 {
-    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return RT_EINVAL;
+    if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !y))) return RT_EINVAL;
     if (n == 0) return RT_OK;
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;

@@ -6,8 +6,9 @@
 //
 // Evaluation is split in two stages so that the same arithmetic can be done
 // by one thread or spread over the lanes of a warp:
-//   1. transcendentals of one temperature (struct Transc; exp, log and
-//      log1p are the table-driven ones of fmath.cuh): ln T, sqrt T,
+//   1. transcendentals of one temperature (struct Transc; exp, log, log1p,
+//      square root and reciprocal in the double-float arithmetic of
+//      dfmath.cuh, on the FP32 pipe): ln T, sqrt T,
 //      1/T, and twelve exponentials exp(a ln T + b/T + c) - the Boltzmann
 //      factors exp(-T0/T), the power laws, and w = (lam/l0)^r of the four
 //      Hui & Gnedin fits A lam^p / (1 + w)^s - then log1p(w) and
@@ -22,7 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "dual.cuh"
-#include "fmath.cuh"
+#include "dfmath.cuh"
 
 namespace rtgb {
 
@@ -77,22 +78,48 @@ static __constant__ RateTable c_rate_tab[2] = {
         1.26e-14, 0.75 }
 };
 
-__device__ __forceinline__ void transc_level0(double T, Transc &t)
+// Stage 1 in double-float arithmetic (dfmath.cuh): ln T, 1/T, sqrt T and u
+// as float pairs, each exponential's argument formed in pair arithmetic and
+// e^x returned as a double; the Transc values are the doubles of the pairs.
+constexpr double kUc = 0.003162277660168379;   // 1 / sqrt(1e5)
+constexpr float kUcHi = (float)kUc;
+constexpr float kUcLo = (float)(kUc - (double)kUcHi);
+
+__device__ __forceinline__ void transc_level0(double T, Transc &t, dfm::F2 &lnT, dfm::F2 &invT)
 {
-    t.lnT = fm::log_t(T);
-    t.sqrtT = sqrt(T);
-    t.invT = 1.0 / T;
-    t.u = 1.0 / (1.0 + t.sqrtT * 0.003162277660168379);
+    using namespace dfm;
+    if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^120 K
+        t.lnT = log(T);
+        t.sqrtT = sqrt(T);
+        t.invT = 1.0 / T;
+        t.u = 1.0 / (1.0 + t.sqrtT * kUc);
+        lnT = split_any(t.lnT);
+        invT = split_any(t.invT);
+        return;
+    }
+    const F2 T2 = split(T);
+    lnT = log2f2(T2);
+    invT = rcp(T2);
+    const F2 sq = sqrt2(T2);
+    const F2 u = rcp(add(mul(sq, F2{kUcHi, kUcLo}), 1.0f));
+    t.lnT = to_double(lnT);
+    t.sqrtT = to_double(sq);
+    t.invT = to_double(invT);
+    t.u = to_double(u);
 }
 
-__device__ __forceinline__ double exp_arg(const ExpArg &q, const Transc &t)
+// a ln T + b / T + c
+__device__ __forceinline__ dfm::F2 exp_arg(const ExpArg &q, dfm::F2 lnT, dfm::F2 invT)
 {
-    return fma(q.a, t.lnT, fma(q.b, t.invT, q.c));
+    using namespace dfm;
+    return add(add(split(q.c), mul(lnT, split(q.a))), mul(invT, split(q.b)));
 }
 
-__device__ __forceinline__ double hg_arg(const HGPar &h, double lnT, double l)
+// p (ln T1 - ln T) - s log1p(w)
+__device__ __forceinline__ dfm::F2 hg_arg(const HGPar &h, dfm::F2 lnT, dfm::F2 l)
 {
-    return h.p * (h.lnT1 - lnT) - h.s * l;
+    using namespace dfm;
+    return add(mul(add(split(h.lnT1), neg(lnT)), split(h.p)), neg(mul(l, split(h.s))));
 }
 
 // Stage 1 in one thread.  need: bit k of the exponentials E_*, bit NEXP + j
@@ -100,15 +127,17 @@ __device__ __forceinline__ double hg_arg(const HGPar &h, double lnT, double l)
 __device__ __forceinline__ void transc_serial(double T, int case_b, unsigned need, Transc &t)
 {
     const RateTable &R = c_rate_tab[case_b];
-    transc_level0(T, t);
+    dfm::F2 lnT, invT;
+    transc_level0(T, t, lnT, invT);
 #pragma unroll
     for (int k = 0; k < NEXP; ++k)
-        if (need & (1u << k)) t.e[k] = fm::exp_t(exp_arg(R.ea[k], t));
+        if (need & (1u << k)) t.e[k] = dfm::exp2d(exp_arg(R.ea[k], lnT, invT));
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
-            t.l[j] = fm::log1p_t(t.e[E_W0 + j]);
-            t.v[j] = fm::exp_t(hg_arg(R.hg[j], t.lnT, t.l[j]));
+            const dfm::F2 l = dfm::log1pd(t.e[E_W0 + j]);
+            t.l[j] = dfm::to_double(l);
+            t.v[j] = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
         }
     }
 }
@@ -119,13 +148,15 @@ __device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
 {
     const RateTable &R = c_rate_tab[case_b];
     const int lane = threadIdx.x & 31;
-    transc_level0(T, t);
+    dfm::F2 lnT, invT;
+    transc_level0(T, t, lnT, invT);
     const int k = lane < NEXP ? lane : 0;
-    double ek = fm::exp_t(exp_arg(R.ea[k], t));
+    double ek = dfm::exp2d(exp_arg(R.ea[k], lnT, invT));
     const int j = lane & 3;
     double wj = __shfl_sync(0xffffffffu, ek, E_W0 + j);
-    double lj = fm::log1p_t(wj);
-    double vj = fm::exp_t(hg_arg(R.hg[j], t.lnT, lj));
+    const dfm::F2 l = dfm::log1pd(wj);
+    double lj = dfm::to_double(l);
+    double vj = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
 #pragma unroll
     for (int q = 0; q < NEXP; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
 #pragma unroll
@@ -137,27 +168,46 @@ __device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
 
 // FP32 transcendentals (the mixed-precision thermochemistry): the same
 // arguments evaluated in single precision, stored widened into Transc so the
-// assembly below is shared.  Relative accuracy ~1e-7.
+// assembly below is shared (widened through integer operations: a float ->
+// double conversion would take the FP64 pipe; float subnormals, far below
+// any rate that matters, count as zero).  Relative accuracy ~1e-7.
+// a double rounded to the nearest float (ties away from zero) through
+// integer operations: a double -> float conversion would take the FP64
+// pipe.  Below the normal float range the result is 0, above it infinity
+// (NaN included).  Truncating instead biases the FP32 absorption
+// coefficients by half an ulp, which over a source cell's thousands of
+// sub-steps moved the mixed-precision results by 1e-4.
+__device__ __forceinline__ float narrow(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned long long a = (b & 0x7fffffffffffffffULL) + 0x10000000ULL;   // carry may raise the exponent
+    const int e = (int)(a >> 52);
+    if (e < 897) return __uint_as_float(sign);
+    if (e > 1150) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((a >> 29) & 0x7fffff));
+}
+
 __device__ __forceinline__ void transc_level0_f(double T, Transc &t, float &lnT, float &invT)
 {
-    float Tf = (float)T;
+    float Tf = narrow(T);
     lnT = logf(Tf);
     float sq = sqrtf(Tf);
     invT = 1.0f / Tf;
-    t.lnT = lnT;
-    t.sqrtT = sq;
-    t.invT = invT;
-    t.u = 1.0f / (1.0f + sq * 0.0031622776f);
+    t.lnT = dfm::widen(lnT);
+    t.sqrtT = dfm::widen(sq);
+    t.invT = dfm::widen(invT);
+    t.u = dfm::widen(1.0f / (1.0f + sq * 0.0031622776f));
 }
 
 __device__ __forceinline__ float exp_arg_f(const ExpArg &q, float lnT, float invT)
 {
-    return fmaf((float)q.a, lnT, fmaf((float)q.b, invT, (float)q.c));
+    return fmaf(narrow(q.a), lnT, fmaf(narrow(q.b), invT, narrow(q.c)));
 }
 
 __device__ __forceinline__ float hg_arg_f(const HGPar &h, float lnT, float l)
 {
-    return (float)h.p * ((float)h.lnT1 - lnT) - (float)h.s * l;
+    return narrow(h.p) * (narrow(h.lnT1) - lnT) - narrow(h.s) * l;
 }
 
 __device__ __forceinline__ void transc_serial_f(double T, int case_b, unsigned need, Transc &t)
@@ -165,15 +215,21 @@ __device__ __forceinline__ void transc_serial_f(double T, int case_b, unsigned n
     const RateTable &R = c_rate_tab[case_b];
     float lnT, invT;
     transc_level0_f(T, t, lnT, invT);
+    float ew[NHG] = {0.0f, 0.0f, 0.0f, 0.0f};   // w of the Hui & Gnedin fits, as floats
 #pragma unroll
-    for (int k = 0; k < NEXP; ++k)
-        if (need & (1u << k)) t.e[k] = expf(exp_arg_f(R.ea[k], lnT, invT));
+    for (int k = 0; k < NEXP; ++k) {
+        if (need & (1u << k)) {
+            const float e = expf(exp_arg_f(R.ea[k], lnT, invT));
+            t.e[k] = dfm::widen(e);
+            if (k >= E_W0) ew[k - E_W0] = e;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
-            float l = log1pf((float)t.e[E_W0 + j]);
-            t.l[j] = l;
-            t.v[j] = expf(hg_arg_f(R.hg[j], lnT, l));
+            float l = log1pf(ew[j]);
+            t.l[j] = dfm::widen(l);
+            t.v[j] = dfm::widen(expf(hg_arg_f(R.hg[j], lnT, l)));
         }
     }
 }
@@ -191,11 +247,11 @@ __device__ __forceinline__ void transc_warp_f(double T, int case_b, Transc &t)
     float lj = log1pf(wj);
     float vj = expf(hg_arg_f(R.hg[j], lnT, lj));
 #pragma unroll
-    for (int q = 0; q < NEXP; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
+    for (int q = 0; q < NEXP; ++q) t.e[q] = dfm::widen(__shfl_sync(0xffffffffu, ek, q));
 #pragma unroll
     for (int q = 0; q < NHG; ++q) {
-        t.l[q] = __shfl_sync(0xffffffffu, lj, q);
-        t.v[q] = __shfl_sync(0xffffffffu, vj, q);
+        t.l[q] = dfm::widen(__shfl_sync(0xffffffffu, lj, q));
+        t.v[q] = dfm::widen(__shfl_sync(0xffffffffu, vj, q));
     }
 }
 

@@ -184,9 +184,11 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             // absorption coefficient in FP32; the update itself in FP64, since
             // a cell may take thousands of sub-steps and FP32 roundings of
             // N would accumulate past the stated 1e-4
-            float Df = (float)cr * ((float)p.gc.sigN[i][0] * (float)nHI + (float)p.gc.sigN[i][1] * (float)nHeI +
-                                    (float)p.gc.sigN[i][2] * (float)nHeII);
-            double inv = 1.0 / (1.0 + h * (double)Df);
+            // (doubles narrowed and the float widened through integer
+            // operations, not FP64-pipe conversions)
+            float Df = narrow(cr) * (narrow(p.gc.sigN[i][0]) * narrow(nHI) + narrow(p.gc.sigN[i][1]) * narrow(nHeI) +
+                                     narrow(p.gc.sigN[i][2]) * narrow(nHeII));
+            double inv = 1.0 / (1.0 + h * dfm::widen(Df));
             if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
             else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
             else Nn = s.N[i] * inv;
