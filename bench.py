@@ -33,11 +33,15 @@ UNIT = "cell-group updates/s"
 # per clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s, matching the 1.25 TFLOP/s
 # measured by an FMA-chain probe on the same part.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# FP64 flops executed per thermochemistry attempt of the one-thread path:
-# ncu's smsp__sass_thread_inst_executed_op_d{fma x2, add, mul} over the ten
-# thermo_pass1 launches of the profiling pass of cosmo128 (3.017e10) over
-# the first-pass attempts of those steps (21 194 255).
-FP64_FLOP_PER_ATTEMPT = 1423.0
+# FP32: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+# Flops executed per thermochemistry attempt of the one-thread path: ncu's
+# smsp__sass_thread_inst_executed_op_{d,f}{fma x2, add, mul} over the ten
+# thermo_pass1 launches of the profiling pass of cosmo128 (FP64 1.518e10,
+# FP32 9.512e10) over the first-pass attempts of those steps (21 194 255).
+# The rate transcendentals run in double-float arithmetic on the FP32 pipe.
+FP64_FLOP_PER_ATTEMPT = 716.0
+FP32_FLOP_PER_ATTEMPT = 4488.0
 PASS1_ATTEMPTS = 6
 DRAIN1_BUDGET = 192   # attempts a queued cell spends in the first lane-per-cell drain stage
 
@@ -344,10 +348,14 @@ def main():
             att_per_launch = queued_att / args.steps
         fpa = FP64_FLOP_PER_ATTEMPT
         ach = fpa * att_per_launch / (ms_launch / 1e3) / 1e9
+        ach32 = FP32_FLOP_PER_ATTEMPT * att_per_launch / (ms_launch / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dominant + " (+ thermo_hard)",
                 "peak_kind": "derived FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz; 1.25 TFLOP/s measured)",
-                "flop_per_attempt": fpa, "attempts_per_launch": att_per_launch}
+                "flop_per_attempt": fpa, "attempts_per_launch": att_per_launch,
+                "fp32": {"achieved": ach32, "peak": FP32_PEAK_GFLOPS, "frac": ach32 / FP32_PEAK_GFLOPS,
+                         "flop_per_attempt": FP32_FLOP_PER_ATTEMPT,
+                         "peak_kind": "derived FP32 (152 SMs x 128 FMA/clk x 2.07 GHz)"}}
 
     # ---- end to end: host buffers through the C-ABI, copies in the timed region ----
     e2e = None
