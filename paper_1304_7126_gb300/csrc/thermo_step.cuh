@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "dual.cuh"
 #include "rates.cuh"
 #include "rt_internal.h"
@@ -55,15 +57,57 @@ __device__ __forceinline__ S mu_of(double X, const S &x, const S &y2, const S &y
     return 1.0 / mu_den(X, x, y2, y3);
 }
 
+
+// Comparisons, minima and maxima of doubles through their bit patterns, on
+// the integer pipe (a GB300 warp issues one FP64 instruction, compares and
+// min/max included, per ~64 cycles).  For doubles >= +0 the signed 64-bit
+// order of the bits is the order of the values, and every negative double
+// orders below them, so these are exact wherever at most one operand can be
+// negative; a NaN orders above +infinity.
+constexpr long long kInfBits = 0x7ff0000000000000LL;
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// max(x, c), min(x, c) for c >= +0 and any x (dual numbers: fmax, fmin)
+template <typename S, typename C>
+__device__ __forceinline__ S max0(const S &x, C c)
+{
+    if constexpr (std::is_same<S, double>::value && std::is_same<C, double>::value)
+        return __longlong_as_double(max(dbits(x), dbits(c)));
+    else
+        return fmax(x, c);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ S min0(const S &x, C c)
+{
+    if constexpr (std::is_same<S, double>::value && std::is_same<C, double>::value)
+        return __longlong_as_double(min(dbits(x), dbits(c)));
+    else
+        return fmin(x, c);
+}
+
+// 2 h and h / 2 of a positive normal h: the exponent moved by one (exact)
+__device__ __forceinline__ double twice(double h)
+{
+    return (dbits(h) >> 52) < 2046 ? __longlong_as_double(dbits(h) + (1LL << 52)) : 2.0 * h;
+}
+
+__device__ __forceinline__ double half(double h)
+{
+    return (dbits(h) >> 52) > 1 ? __longlong_as_double(dbits(h) - (1LL << 52)) : 0.5 * h;
+}
+
 // fl(a / b) > t and fl(a / b) < t (a >= 0, b > 0), decided exactly as the
 // rounded quotient would decide them: the product t b settles everything
-// outside a band of a few ulps around the threshold, where the quotient
-// itself is formed.  The 10% rule's decisions thus match a statement of it
-// that divides, including at exact ties (a sub-cycled cell whose photon
+// more than 8 ulps away from it (for doubles, by their bits; the rounding
+// of t b and of the quotient is within 2 ulps), and the quotient itself is
+// formed only inside that band (or for a NaN, which then compares false as
+// the quotient would).  The 10% rule's decisions thus match a statement of
+// it that divides, including at exact ties (a sub-cycled cell whose photon
 // density grows linearly from zero meets relative changes of exactly 1/10
-// and 1/20).
-// the quotient itself, kept out of line so that the compiler does not
-// evaluate it on the common path
+// and 1/20).  The quotient is kept out of line so that the compiler does
+// not evaluate it on the common path.
 template <typename S>
 __device__ __noinline__ bool quotient_gt(S a, S b, double t)
 {
@@ -80,8 +124,14 @@ template <typename S>
 __device__ __forceinline__ bool ratio_gt(const S &a, const S &b, double t)
 {
     const S tb = t * b;
-    if (a > tb * (1.0 + 1e-15)) return true;
-    if (a < tb * (1.0 - 1e-15)) return false;
+    if constexpr (std::is_same<S, double>::value) {
+        const long long ai = dbits(a), ti = dbits(tb);
+        if (ai > ti + 8 && ai <= kInfBits) return true;
+        if (ai < ti - 8) return false;
+    } else {
+        if (a > tb * (1.0 + 1e-15)) return true;
+        if (a < tb * (1.0 - 1e-15)) return false;
+    }
     return quotient_gt<S>(a, b, t);
 }
 
@@ -89,8 +139,14 @@ template <typename S>
 __device__ __forceinline__ bool ratio_lt(const S &a, const S &b, double t)
 {
     const S tb = t * b;
-    if (a < tb * (1.0 - 1e-15)) return true;
-    if (a > tb * (1.0 + 1e-15)) return false;
+    if constexpr (std::is_same<S, double>::value) {
+        const long long ai = dbits(a), ti = dbits(tb);
+        if (ai < ti - 8) return true;
+        if (ai > ti + 8 && ai <= kInfBits) return false;
+    } else {
+        if (a < tb * (1.0 - 1e-15)) return true;
+        if (a > tb * (1.0 + 1e-15)) return false;
+    }
     return quotient_lt<S>(a, b, t);
 }
 
@@ -192,7 +248,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
             else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
             else Nn = s.N[i] * inv;
-            double dN = fabs(Nn - s.N[i]), den = fmax(s.N[i], kFloorN);
+            double dN = fabs(Nn - s.N[i]), den = max0(s.N[i], kFloorN);
             if (ratio_gt(dN, den, 0.1)) return false;
             sm = sm && ratio_lt(dN, den, 0.05);
             o.Fs[i] = s.Fs[i] * inv;
@@ -206,7 +262,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
             else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
             else Nn = s.N[i] * inv;
-            S dN = fabs(Nn - s.N[i]), den = fmax(s.N[i], kFloorN);
+            S dN = fabs(Nn - s.N[i]), den = max0(s.N[i], kFloorN);
             if (ratio_gt(dN, den, 0.1)) return false;
             sm = sm && ratio_lt(dN, den, 0.05);
             o.Fs[i] = s.Fs[i] * inv;
@@ -269,9 +325,9 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     S J = dC - (C + Dd) - x * (dC + dD);
     S xdot = C - x * (C + Dd);
     S x1 = x + h * xdot / (1.0 - J * h);
-    x1 = fmin(fmax(x1, kXMin), 1.0);
+    x1 = min0(max0(x1, kXMin), 1.0);
     {
-        S xden = fmax(x, kXMin);
+        S xden = max0(x, kXMin);
         S dx = fabs(x1 - x);
         if (ratio_gt(dx, xden, 0.1)) return false;
         if (ratio_gt(fabs(xdot) * h, xden, 0.1)) return false;
@@ -312,12 +368,12 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         // conservation: lower the largest fraction (HeI largest: no change)
         if (y2n >= yI1 && y2n >= y3n) y2n = 1.0 - yI1 - y3n;
         else if (y3n >= yI1 && y3n > y2n) y3n = 1.0 - yI1 - y2n;
-        y2n = fmin(fmax(y2n, 0.0), 1.0);
-        y3n = fmin(fmax(y3n, 0.0), 1.0);
+        y2n = min0(max0(y2n, 0.0), 1.0);
+        y3n = min0(max0(y3n, 0.0), 1.0);
     }
     {
         S ne1 = x1 * nH + (y2n + 2.0 * y3n) * nHe;
-        S dne = fabs(ne1 - ne), den = fmax(ne, kNeFloor * nH);
+        S dne = fabs(ne1 - ne), den = max0(ne, S(kNeFloor * nH));
         if (ratio_gt(dne, den, 0.1)) return false;
         sm = sm && ratio_lt(dne, den, 0.05);
     }
@@ -325,7 +381,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     o.x = x1;
     o.y2 = y2n;
     o.y3 = y3n;
-    o.T = fmax(Tf, kTFloor);
+    o.T = max0(Tf, kTFloor);
     small = sm;
     return true;
 }
@@ -336,7 +392,8 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH
                                               double &t_left, double &dt_tc, int &att, const IsoRates<S> &iso,
                                               CoolCache<S> &cc)
 {
-    double h = (dt_tc < t_left) ? dt_tc : t_left;
+    // t_left, dt_tc > 0: compared through their bits
+    double h = (dbits(dt_tc) < dbits(t_left)) ? dt_tc : t_left;
     ++att;
     CellState<G, S> o;
     bool small = false;
@@ -344,12 +401,12 @@ __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH
         st = o;
         cc.valid = false;
         cc.rvalid = false;
-        t_left = (h == t_left) ? 0.0 : t_left - h;
-        dt_tc = small ? 2.0 * h : h;
+        t_left = (dbits(h) == dbits(t_left)) ? 0.0 : t_left - h;
+        dt_tc = small ? twice(h) : h;
     } else {
-        dt_tc = 0.5 * h;
+        dt_tc = half(h);
     }
-    return !(t_left > 0.0);
+    return dbits(t_left) <= 0;
 }
 
 }  // namespace thermo_detail
