@@ -96,6 +96,7 @@ thermo_vjp_kernel(ThermoParams p, const double *__restrict__ nH, const double *_
     }
     const Dual n(nH[c], j == G + 4 ? 1.0 : 0.0);
     IsoRates<Dual> iso;
+    cell_constants(p, n, iso);
     CoolCache<Dual> cc;
     cc.valid = false;
     cc.rvalid = false;

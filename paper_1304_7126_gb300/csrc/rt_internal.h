@@ -132,10 +132,23 @@ cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, bool rates32, con
                                 double *xHeII, double *xHeIII, double *T, float *N, float *F, float *Npre,
                                 float *Fpre, int32_t *subcycles, Queue q, unsigned *status, int n_sm,
                                 cudaStream_t s, cudaEvent_t *ev = nullptr);
-cudaError_t launch_thermo_mixed32(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
-                                  double *xHeIII, double *T, float *N, float *F, float *Npre, float *Fpre,
-                                  int32_t *subcycles, Queue q, unsigned *status, int n_sm, cudaStream_t s,
-                                  cudaEvent_t *ev = nullptr);
+
+// the kernels of one precision family for every group count (thermo_f64.cu,
+// thermo_f64_sm.cu, thermo_mix.cu, thermo_mix_sm.cu, thermo_mix32.cu,
+// thermo_mix32_sm.cu)
+#define RTGB_THERMO_DISPATCH(NAME, P)                                                                               \
+    cudaError_t NAME(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII, double *xHeIII, \
+                     double *T, P *N, P *F, P *Npre, P *Fpre, int32_t *subcycles, Queue q, unsigned *status,     \
+                     int n_sm, cudaStream_t s, cudaEvent_t *ev);
+RTGB_THERMO_DISPATCH(thermo_dispatch_f64, double)
+RTGB_THERMO_DISPATCH(thermo_dispatch_f64_sm, double)
+RTGB_THERMO_DISPATCH(thermo_dispatch_mix, float)
+RTGB_THERMO_DISPATCH(thermo_dispatch_mix_sm, float)
+RTGB_THERMO_DISPATCH(thermo_dispatch_mix32, float)
+RTGB_THERMO_DISPATCH(thermo_dispatch_mix32_sm, float)
+#undef RTGB_THERMO_DISPATCH
+
+
 
 cudaError_t launch_inject(int nsrc, int G, long long nc, const long long *cells,
                           const double *Lsum, double dt_over_V, double *N, cudaStream_t s);

@@ -32,13 +32,15 @@
 //                 the one-thread path, so results do not depend on which
 //                 kernel finished a cell.
 // Nothing waits on another thread; each kernel ends when its queue is empty.
+// The kernels live in thermo_kernels.cuh, instantiated per precision family
+// in thermo_f64.cu, thermo_mix.cu, thermo_mix32.cu and their smoothed-RT
+// counterparts (*_sm.cu); this file holds the launchers and the
+// allocation-free entry point.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "rt_internal.h"
-
-#include "thermo_kernels.cuh"
 
 namespace rtgb {
 
@@ -47,10 +49,29 @@ cudaError_t launch_thermo(const ThermoParams &tp, int G, const double *nH, doubl
                           int32_t *subcycles, Queue q, unsigned *status, int n_sm, cudaStream_t s, cudaEvent_t *ev)
 {
     if (Npre)
-        return dispatch_g<double, false, true>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, subcycles, q,
-                                               status, n_sm, s, ev);
-    return dispatch_g<double, false, false>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, nullptr, nullptr, subcycles, q,
-                                            status, n_sm, s, ev);
+        return thermo_dispatch_f64_sm(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, subcycles, q, status, n_sm,
+                                      s, ev);
+    return thermo_dispatch_f64(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, nullptr, nullptr, subcycles, q, status, n_sm, s,
+                               ev);
+}
+
+cudaError_t launch_thermo_mixed(const ThermoParams &tp, int G, bool rates32, const double *nH, double *xHII,
+                                double *xHeII, double *xHeIII, double *T, float *N, float *F, float *Npre,
+                                float *Fpre, int32_t *subcycles, Queue q, unsigned *status, int n_sm, cudaStream_t s,
+                                cudaEvent_t *ev)
+{
+    if (rates32) {
+        if (Npre)
+            return thermo_dispatch_mix32_sm(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, subcycles, q, status,
+                                            n_sm, s, ev);
+        return thermo_dispatch_mix32(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, nullptr, nullptr, subcycles, q, status,
+                                     n_sm, s, ev);
+    }
+    if (Npre)
+        return thermo_dispatch_mix_sm(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, subcycles, q, status, n_sm,
+                                      s, ev);
+    return thermo_dispatch_mix(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, nullptr, nullptr, subcycles, q, status, n_sm, s,
+                               ev);
 }
 
 }  // namespace rtgb

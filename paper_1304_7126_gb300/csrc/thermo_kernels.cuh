@@ -138,6 +138,7 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         CoolCache<> cc;
         load_cell<G, false, P, R32, SM>(p, c, true, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
         double n = nH[c];
+        cell_constants(p, n, iso);
         bool done = false;
         const int lim = p.pass1_attempts < p.max_sub ? p.pass1_attempts : p.max_sub;
         for (int k = 0; k < lim && !done; ++k)
@@ -213,6 +214,7 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             n = nH[c];
             used = 0;
             load_cell<G, false, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
+            cell_constants(p, n, iso);
             have = true;
         } else {
             have = false;
@@ -262,6 +264,7 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
         IsoRates<> iso;
         CoolCache<> cc;
         load_cell<G, true, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
+        cell_constants(p, n, iso);
         bool done = false;
         while (!done) {
             done = subcycle_once<G, true, R32, double, SM>(p, n, st, t_left, dt_tc, att, iso, cc);

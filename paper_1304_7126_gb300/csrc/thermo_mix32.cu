@@ -1,19 +1,16 @@
-// RT_MIXED32 thermochemistry launcher: FP32 photon state and rate
-// transcendentals, FP64 stiff updates (kernels in thermo_kernels.cuh).
+// Thermochemistry kernels of one precision family, RT_MIXED32 (FP32 photon state and rate transcendentals, FP64 stiff updates): the
+// instantiations of thermo_kernels.cuh for every group count, one family
+// per translation unit so that they compile in parallel.
 #include "thermo_kernels.cuh"
 
 namespace rtgb {
 
-cudaError_t launch_thermo_mixed32(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII,
-                                  double *xHeIII, double *T, float *N, float *F, float *Npre, float *Fpre,
-                                  int32_t *subcycles, Queue q, unsigned *status, int n_sm, cudaStream_t s,
-                                  cudaEvent_t *ev)
+cudaError_t thermo_dispatch_mix32(const ThermoParams &tp, int G, const double *nH, double *xHII, double *xHeII, double *xHeIII,
+               double *T, float *N, float *F, float *Npre, float *Fpre, int32_t *subcycles, Queue q, unsigned *status,
+               int n_sm, cudaStream_t s, cudaEvent_t *ev)
 {
-    if (Npre)
-        return dispatch_g<float, true, true>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, subcycles, q,
-                                             status, n_sm, s, ev);
-    return dispatch_g<float, true, false>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, nullptr, nullptr, subcycles, q,
-                                          status, n_sm, s, ev);
+    return dispatch_g<float, true, false>(tp, G, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, subcycles, q, status, n_sm, s,
+                                  ev);
 }
 
 }  // namespace rtgb

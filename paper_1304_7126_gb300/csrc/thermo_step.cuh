@@ -32,9 +32,10 @@ struct CellState {
 };
 
 template <typename S = double>
-struct IsoRates {     // rates at the fixed temperature of an isothermal cell
-    HRatesT<S> h;
+struct IsoRates {     // quantities of a cell fixed over its sub-steps
+    HRatesT<S> h;     // rates at the fixed temperature of an isothermal cell
     HeRatesT<S> he;
+    S nHe, K, nef;    // n_He, (gamma - 1) X / (k_B n_H), the n_e floor 1e-6 n_H
 };
 
 template <typename S = double>
@@ -43,6 +44,14 @@ struct CoolCache {    // quantities of the current state at t, kept over rejecte
     S rj[3];          // without the OTSA: (alpha^A_j - alpha^B_j) n_j n_e, j = HII, HeII, HeIII
     bool valid, rvalid;
 };
+
+template <typename S>
+__device__ __forceinline__ void cell_constants(const ThermoParams &p, const S &nH, IsoRates<S> &iso)
+{
+    iso.nHe = nH * p.he_ratio;
+    iso.K = p.kfac / nH;
+    iso.nef = kNeFloor * nH;
+}
 
 // 1/mu, mu the mean particle mass in m_H (App. A)
 template <typename S>
@@ -207,7 +216,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
                                         bool &small)
 {
     static_assert(!MIX || sizeof(S) == sizeof(double), "the mixed path is not differentiated");
-    const S nHe = nH * p.he_ratio;
+    const S nHe = iso.nHe;
     const S x = s.x, y2 = s.y2, y3 = s.y3;
     const S nHI = nH * (1.0 - x);
     const S nHII = nH * x;
@@ -295,7 +304,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         }
         S lam = heat - cc.L;
         S dlam = -mu * cc.dL;
-        S K = p.kfac / nH;
+        const S K = iso.K;
         S Tmu = s.T * mden;
         S dT = lam * K * h / (1.0 - dlam * K * h);
         Tmu1 = Tmu + dT;
@@ -373,7 +382,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     }
     {
         S ne1 = x1 * nH + (y2n + 2.0 * y3n) * nHe;
-        S dne = fabs(ne1 - ne), den = max0(ne, S(kNeFloor * nH));
+        S dne = fabs(ne1 - ne), den = max0(ne, iso.nef);
         if (ratio_gt(dne, den, 0.1)) return false;
         sm = sm && ratio_lt(dne, den, 0.05);
     }
