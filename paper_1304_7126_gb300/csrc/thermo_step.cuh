@@ -228,6 +228,16 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     bool sm = true;
     S gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
 
+    // cooling at T(t) and the state at t (step 2 below), first: it depends on
+    // nothing this sub-step computes, so its FP32-pipe transcendentals can
+    // overlap the FP64 photon update; kept over rejected attempts
+    if (!p.isothermal && !cc.valid) {
+        TranscT<S> t;
+        get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
+        cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+        cc.valid = true;
+    }
+
     // recombination photons without the OTSA, Eq. (cool_N_cr), at T(t) with
     // the backward abundances; group i gains C_i = sum_j [rec_g[j] == i] rj[j]
     if (p.emit && !cc.rvalid) {
@@ -295,13 +305,6 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     const S mu = 1.0 / mden;
     S Tmu1 = 0.0;
     if (!p.isothermal) {
-        if (!cc.valid) {
-            TranscT<S> t;
-            get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
-            cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L,
-                         cc.dL);
-            cc.valid = true;
-        }
         S lam = heat - cc.L;
         S dlam = -mu * cc.dL;
         const S K = iso.K;
