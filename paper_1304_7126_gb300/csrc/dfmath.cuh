@@ -25,7 +25,7 @@
 // i.e. 1e-14 to 1e-12 relative for the rate coefficients, far inside the
 // 1e-10 parity the FP64 path is held to.  Inputs outside the ranges the
 // rate fits produce (a double beyond 2^-60 .. 2^60 in magnitude) go to
-// CUDA's FP64 functions.
+// CUDA's FP64 functions (log1p of w < 2^-60 is w itself).
 #pragma once
 
 #include <cuda_runtime.h>
