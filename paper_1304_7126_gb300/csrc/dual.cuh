@@ -58,6 +58,17 @@ __device__ __forceinline__ Dual operator/(double a, const Dual &b)
     const double q = a / b.v;
     return Dual(q, -q * b.d / b.v);
 }
+// products and sums rounded as written (never fused into an FMA): the
+// value of a dual is then bit for bit the double computed the same way
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ Dual rmul(const Dual &a, const Dual &b)
+{
+    return Dual(__dmul_rn(a.v, b.v), a.v * b.d + a.d * b.v);
+}
+__device__ __forceinline__ Dual rmul(const Dual &a, double b) { return Dual(__dmul_rn(a.v, b), a.d * b); }
+__device__ __forceinline__ Dual radd(const Dual &a, const Dual &b) { return Dual(__dadd_rn(a.v, b.v), a.d + b.d); }
+
 __device__ __forceinline__ Dual &operator+=(Dual &a, const Dual &b) { a = a + b; return a; }
 __device__ __forceinline__ Dual &operator-=(Dual &a, const Dual &b) { a = a - b; return a; }
 __device__ __forceinline__ Dual &operator*=(Dual &a, const Dual &b) { a = a * b; return a; }

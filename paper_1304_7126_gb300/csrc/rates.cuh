@@ -361,56 +361,181 @@ __device__ __forceinline__ void recomb_alphas(const TranscT<S> &t, int case_b, S
 }
 
 // Primordial cooling magnitude L (Eq. (rate_cooling), positive = cooling)
-// and dL/dT for the given densities and electron density.
+// and dL/dT, as a sum of terms of one form,
+//     C n_s sqrt(T)^a u^b T^c X1 X2 A,
+// X1 an exponential e[i1] of the Transc (or the Hui & Gnedin value v[hg]),
+// X2 an optional second exponential, A the fit's amplitude where the rate
+// table holds it (it depends on the recombination case), n_s a density;
+// each term's T-derivative is the term times its log-derivative
+//     a/(2T) - b (1 - u)/(2T) + c/T + dln X1/dT + dln X2/dT,
+// dln e/dT = a_e/T - b_e/T^2 from the exponential's argument, and the Hui &
+// Gnedin log-derivative.  The terms (collisional ionisation and excitation,
+// recombination and dielectronic cooling, bremsstrahlung) are summed in a
+// fixed pairwise order; Compton cooling is added after.  All products and
+// sums are rounded as written (rmul, radd), so the one-thread sum and the
+// warp sum (lane k evaluates term k) give the same bits.
+enum { SP_HI = 0, SP_HII, SP_HEI, SP_HEII, SP_HEIII, SP_FF, NSP };   // SP_FF: n_HII + n_HeII + 4 n_HeIII
+
+struct CoolTerm {
+    double C;
+    int sq, uu, tt;   // powers (0 or 1) of sqrt T, u, T
+    int e1, e2, hg;   // exponentials e[e1], e[e2] and Hui & Gnedin fit hg (-1: none)
+    int amp;          // 1: times the table's amplitude of alpha_HeII
+    int sp;           // density factor SP_*
+    int he;           // a helium term
+};
+
+// (the paper's fits: Cen 1992 collisional ionisation and excitation, Hui &
+// Gnedin 1997 recombination cooling, Black 1981 dielectronic recombination,
+// bremsstrahlung; k_B T alpha_HeII for HeII recombination cooling)
+#define RTGB_COOL_TERMS(X)                                                           \
+    X(1.27e-21, 1, 1, 0, E_BETA_HI, -1, -1, 0, SP_HI, 0)                              \
+    X(7.5e-19, 0, 1, 0, E_PSI_HI, -1, -1, 0, SP_HI, 0)                                \
+    X(1.0, 0, 0, 1, -1, -1, HG_ETA_HII, 0, SP_HII, 0)                                 \
+    X(1.42e-27, 1, 0, 0, -1, -1, -1, 0, SP_FF, 0)                                     \
+    X(9.38e-22, 1, 1, 0, E_BETA_HEI, -1, -1, 0, SP_HEI, 1)                            \
+    X(4.95e-22, 1, 1, 0, E_BETA_HEII, -1, -1, 0, SP_HEII, 1)                          \
+    X(5.54e-17, 0, 1, 0, E_PSI_HEII, -1, -1, 0, SP_HEII, 1)                           \
+    X(1.380649e-16, 0, 0, 1, E_ALPHA_HEII, -1, -1, 1, SP_HEII, 1)                     \
+    X(1.24e-13, 0, 0, 0, E_OMEGA1, -1, -1, 0, SP_HEII, 1)                             \
+    X(0.3 * 1.24e-13, 0, 0, 0, E_OMEGA1, E_OMEGA2, -1, 0, SP_HEII, 1)                 \
+    X(1.0, 0, 0, 1, -1, -1, HG_ETA_HEIII, 0, SP_HEIII, 1)
+#define RTGB_COOL_ROW(C, a, b, c, e1, e2, hg, amp, sp, he) {C, a, b, c, e1, e2, hg, amp, sp, he},
+constexpr int kNCool = 11;
+// row k at compile time (the one-thread sum, unrolled)
+__device__ __forceinline__ constexpr CoolTerm cool_row(int k)
+{
+    constexpr CoolTerm rows[kNCool] = {RTGB_COOL_TERMS(RTGB_COOL_ROW)};
+    return rows[k];
+}
+// the same rows in device memory, indexed by lane (the warp sum)
+static __device__ const CoolTerm kCoolTermsDev[kNCool] = {RTGB_COOL_TERMS(RTGB_COOL_ROW)};
+#undef RTGB_COOL_ROW
+#undef RTGB_COOL_TERMS
+
+// a[i] through selects (registers, not local memory, for a lane-dependent
+// i; a plain a[i] once unrolled with a constant i)
+template <typename T, int N>
+__device__ __forceinline__ T pick(const T (&a)[N], int i)
+{
+    T r = a[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) r = (i == j) ? a[j] : r;
+    return r;
+}
+
+// dln e/dT of exp(a ln T + b/T + c)
+template <typename S>
+__device__ __forceinline__ S exp_dlog(const ExpArg &q, const S &x)
+{
+    return radd(rmul(x, q.a), rmul(rmul(x, x), -q.b));
+}
+
+// one term and its T-derivative
+template <typename S>
+__device__ __forceinline__ void cool_term(const CoolTerm &q, const RateTable &R, const TranscT<S> &t, const S &T,
+                                          const S (&n)[NSP], S &v, S &dv)
+{
+    const S x = t.invT;
+    S f = S(q.C);
+    S d = S(0.0);
+    if (q.sq) { f = rmul(f, t.sqrtT); d = radd(d, rmul(x, 0.5)); }
+    if (q.uu) { f = rmul(f, t.u); d = radd(d, rmul(rmul(radd(S(1.0), -t.u), -0.5), x)); }
+    if (q.tt) { f = rmul(f, T); d = radd(d, x); }
+    if (q.e1 >= 0) { f = rmul(f, pick(t.e, q.e1)); d = radd(d, exp_dlog(R.ea[q.e1], x)); }
+    if (q.e2 >= 0) { f = rmul(f, pick(t.e, q.e2)); d = radd(d, exp_dlog(R.ea[q.e2], x)); }
+    if (q.hg >= 0) {
+        const HGPar &h = R.hg[q.hg];
+        f = rmul(f, rmul(pick(t.v, q.hg), h.A));
+        const S w = pick(t.e, E_W0 + q.hg);
+        const S qw = w / radd(S(1.0), w);
+        d = radd(d, rmul(-x, radd(S(h.p), -rmul(qw, h.s * h.r))));
+    }
+    if (q.amp) f = rmul(f, R.A_aHeII);
+    v = rmul(f, pick(n, q.sp));
+    dv = rmul(v, d);
+}
+
+// the fixed pairwise order of a 16-lane butterfly (offsets 8, 4, 2, 1)
+template <typename S>
+__device__ __forceinline__ S tree_sum16(S a[16])
+{
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) {
+#pragma unroll
+        for (int i = 0; i < m; ++i) a[i] = radd(a[i], a[i + m]);
+    }
+    return a[0];
+}
+
+template <typename S>
+__device__ __forceinline__ void cool_densities(const S &nHI, const S &nHII, const S &nHeI, const S &nHeII,
+                                               const S &nHeIII, S n[NSP])
+{
+    n[SP_HI] = nHI;
+    n[SP_HII] = nHII;
+    n[SP_HEI] = nHeI;
+    n[SP_HEII] = nHeII;
+    n[SP_HEIII] = nHeIII;
+    n[SP_FF] = radd(radd(nHII, nHeII), rmul(nHeIII, 4.0));
+}
+
+template <typename S>
+__device__ __forceinline__ void cooling_close(double a_exp, const S &T, const S &ne, const S &Ls, const S &dLs, S &L,
+                                              S &dL)
+{
+    const double Tg = 2.727 / a_exp;
+    const double Tg4 = Tg * Tg * Tg * Tg;
+    const S vp = rmul(radd(T, S(-Tg)), 1.017e-37 * Tg4);   // Compton, T_gamma = 2.727 / a
+    L = rmul(ne, radd(Ls, vp));
+    dL = rmul(ne, radd(dLs, S(1.017e-37 * Tg4)));
+}
+
+// one thread
 template <typename S>
 __device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, double a_exp, bool helium, const S &T,
                                              const S &ne, const S &nHI, const S &nHII, const S &nHeI,
                                              const S &nHeII, const S &nHeIII, S &L, S &dL)
 {
     const RateTable &R = c_rate_tab[case_b];
-    const double kB = 1.380649e-16;
-    S v, dv;
-    cen_fit(1.27e-21, 157809.1, t.e[E_BETA_HI], t, v, dv);
-    S psi = 7.5e-19 * t.u * t.e[E_PSI_HI];
-    S dpsi = psi * (-0.5 * (1.0 - t.u) * t.invT + 118348.0 * t.invT * t.invT);
-    S Ls = (v + psi) * nHI;
-    S dLs = (dv + dpsi) * nHI;
-    S eta = R.hg[HG_ETA_HII].A * t.v[HG_ETA_HII];
-    S deta = eta * hg_dlog(R.hg[HG_ETA_HII], t, HG_ETA_HII);
-    Ls += T * eta * nHII;
-    dLs += (eta + T * deta) * nHII;
-    S th = 1.42e-27 * t.sqrtT;
-    S dth = 0.5 * th * t.invT;
-    Ls += th * (nHII + nHeII + 4.0 * nHeIII);
-    dLs += dth * (nHII + nHeII + 4.0 * nHeIII);
-    if (helium) {
-        cen_fit(9.38e-22, 285335.4, t.e[E_BETA_HEI], t, v, dv);
-        Ls += v * nHeI;
-        dLs += dv * nHeI;
-        S zs, dzs;
-        cen_fit(4.95e-22, 631515.0, t.e[E_BETA_HEII], t, zs, dzs);
-        S p2 = 5.54e-17 * t.u * t.e[E_PSI_HEII];
-        S dp2 = p2 * (-0.397 * t.invT - 0.5 * (1.0 - t.u) * t.invT + 473638.0 * t.invT * t.invT);
-        S a2 = R.A_aHeII * t.e[E_ALPHA_HEII];
-        S da2 = -a2 * R.p_aHeII * t.invT;
-        S et2 = kB * T * a2;
-        S det2 = kB * (a2 + T * da2);
-        S base = 1.24e-13 * t.e[E_OMEGA1];
-        S e7 = t.e[E_OMEGA2];
-        S om = base * (1.0 + 0.3 * e7);
-        S dom = om * (-1.5 * t.invT + 470000.0 * t.invT * t.invT) + base * 0.3 * e7 * 94000.0 * t.invT * t.invT;
-        Ls += (zs + p2 + et2 + om) * nHeII;
-        dLs += (dzs + dp2 + det2 + dom) * nHeII;
-        S e3h = R.hg[HG_ETA_HEIII].A * t.v[HG_ETA_HEIII];
-        S de3h = e3h * hg_dlog(R.hg[HG_ETA_HEIII], t, HG_ETA_HEIII);
-        Ls += T * e3h * nHeIII;
-        dLs += (e3h + T * de3h) * nHeIII;
+    S n[NSP];
+    cool_densities(nHI, nHII, nHeI, nHeII, nHeIII, n);
+    S a[16], b[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        a[k] = S(0.0);
+        b[k] = S(0.0);
     }
-    double Tg = 2.727 / a_exp;
-    double Tg4 = Tg * Tg * Tg * Tg;
-    S vp = 1.017e-37 * Tg4 * (T - Tg);
-    L = ne * (Ls + vp);
-    dL = ne * (dLs + 1.017e-37 * Tg4);
+#pragma unroll
+    for (int k = 0; k < kNCool; ++k) {
+        const CoolTerm q = cool_row(k);
+        if (helium || !q.he) cool_term(q, R, t, T, n, a[k], b[k]);
+    }
+    const S Ls = tree_sum16(a), dLs = tree_sum16(b);
+    cooling_close(a_exp, T, ne, Ls, dLs, L, dL);
+}
+
+// a full warp (all 32 lanes, the same arguments): lane k < 11 evaluates
+// term k, the sums run over shuffles in the same pairwise order
+__device__ __forceinline__ void cooling_warp(const Transc &t, int case_b, double a_exp, bool helium, double T,
+                                             double ne, double nHI, double nHII, double nHeI, double nHeII,
+                                             double nHeIII, double &L, double &dL)
+{
+    const RateTable &R = c_rate_tab[case_b];
+    double n[NSP];
+    cool_densities(nHI, nHII, nHeI, nHeII, nHeIII, n);
+    const int k = threadIdx.x & 15;
+    double v = 0.0, dv = 0.0;
+    if (k < kNCool) {
+        const CoolTerm q = kCoolTermsDev[k];
+        if (helium || !q.he) cool_term(q, R, t, T, n, v, dv);
+    }
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) {
+        v = radd(v, __shfl_xor_sync(0xffffffffu, v, m));
+        dv = radd(dv, __shfl_xor_sync(0xffffffffu, dv, m));
+    }
+    cooling_close(a_exp, T, ne, v, dv, L, dL);
 }
 
 }  // namespace rtgb

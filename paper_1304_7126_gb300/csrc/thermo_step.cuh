@@ -234,7 +234,10 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     if (!p.isothermal && !cc.valid) {
         TranscT<S> t;
         get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
-        cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+        if constexpr (WARP)   // lane k evaluates cooling term k
+            cooling_warp(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+        else
+            cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
         cc.valid = true;
     }
 
