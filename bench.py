@@ -40,6 +40,10 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 # thermo_pass1 launches of the profiling pass of cosmo128 (FP64 1.518e10,
 # FP32 9.512e10) over the first-pass attempts of those steps (21 194 255).
 # The rate transcendentals run in double-float arithmetic on the FP32 pipe.
+# (Counted before the 10% checks moved to the integer pipe and the cooling
+# became a sum of generic terms: those removed about two FP64 multiplies
+# per check and added a few per cooling term, so the count moved by a few
+# percent at most.)
 FP64_FLOP_PER_ATTEMPT = 716.0
 FP32_FLOP_PER_ATTEMPT = 4488.0
 PASS1_ATTEMPTS = 6
