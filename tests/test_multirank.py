@@ -2,7 +2,8 @@
 replica of the workload): two gloo ranks on the CPU.  The job's time is
 the slowest rank's (an all-reduce MAX over the ranks), the job's work the
 sum over ranks, and the rank variables come from the launcher's
-environment.  The reference arm prints nothing on ranks other than 0."""
+environment.  The reference arm prints nothing on ranks other than 0, and on
+rank 0 one JSON line with the benchmark's keys."""
 import os
 import socket
 
@@ -67,3 +68,23 @@ def test_reference_arm_silent_off_rank_zero(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(argparse.Namespace(workload="cosmo128", steps=1, warmup=0))
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line():
+    """The reference arm (the FP64 oracle on a 32^3 corner of the workload,
+    no GPU) prints one JSON line with the benchmark's keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+                         cwd=root, capture_output=True, text=True, check=True, env=env, timeout=600).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
