@@ -196,8 +196,12 @@ const char *rt_last_error(const rt_handle *h);
  * dJ/dL.  The thermochemistry is differentiated along the sub-cycle
  * schedule that the forward step takes (the schedule is piecewise constant
  * in the inputs, so this is the derivative wherever it exists), the
- * transport is the transposed GLF stencil.  Needs precision RT_FP64 and
- * flux RT_GLF (else RT_EINVAL) and a state set by rt_set_state.
+ * transport is the transposed GLF or HLL stencil of the handle's flux
+ * (with HLL, the derivative of the tabulated wave speeds included; where
+ * two cells' speeds tie exactly the step has a kink and the derivative is
+ * that of the branch max/min selects).  Needs precision RT_FP64, the OTSA
+ * and smooth = 0 (else RT_EINVAL), flux RT_GLF or RT_HLL, and a state
+ * set by rt_set_state.
  *
  * All arrays are CUDA device pointers on the handle's device, used on the
  * handle's stream, in the state layouts above:
@@ -227,6 +231,22 @@ int rt_run_vjp(rt_handle *h, double dt, int nsteps, double *lam_xHII, double *la
  * (lambda_min, lambda_max) at f = k/(nf-1), mu = -1 + 2j/(nmu-1).
  * Needs no GPU. */
 int rt_hll_table(int nf, int nmu, double *out);
+
+/* Routing of the thermochemistry (tuning and tests; no counterpart in the
+ * paper).  The sub-cycling of Sec. 3.3.1 runs in up to four kernels per
+ * step: a first pass (one thread per cell, pass1_attempts attempts), a
+ * lane-per-cell drain of the cells still sub-cycling (drain_budget more
+ * attempts each), a second such drain (drain2_budget) that runs only when
+ * more than drain2_min_cells cells are left for it, and a warp per cell
+ * for the rest.  Routing decides which kernel runs which attempts of a
+ * cell, never the arithmetic of an attempt: x_HII, x_HeII, x_HeIII, T, N
+ * and the attempt counts are identical for every routing, F may differ in
+ * its last bits (the flux scale prod 1/(1 + h D_i) of the attempts run so
+ * far is applied to F when a cell moves between kernels).  Values <= 0
+ * (drain2_min_cells < 0) restore the defaults 6, 192, 512 and eight cells
+ * per warp of the warp-per-cell kernel.  Takes effect at the next step. */
+int rt_set_thermo_routing(rt_handle *h, int pass1_attempts, int drain_budget, int drain2_budget,
+                          long long drain2_min_cells);
 
 /* Per-phase timing (diagnostics; not part of the RT method).  With enable
  * != 0, rt_step records CUDA events on the handle's stream around each of
@@ -303,8 +323,10 @@ int rt_batch_box_tiling(const rt_batch *b, int box, int *shape, int *planes);
  * RT_ECUDA if a CUDA call fails.
  * The first call on each device looks up the array's device address with
  * that device current (the device must be current when calling); make that
- * first call before any stream capture.  Every call uses the same array and
- * clears its counters first; calls that overlap on the GPU race on it. */
+ * first call before any stream capture.  After a device reset (a new
+ * primary context, hence a new copy of the array) the next call looks the
+ * address up again.  Every call uses the same array and clears its
+ * counters first; calls that overlap on the GPU race on it. */
 int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_options *opt, double c_r,
                            const double *sigN, const double *sigE, const double *egy, double dt,
                            const double *nH, double *xHII, double *xHeII, double *xHeIII,

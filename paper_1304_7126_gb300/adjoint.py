@@ -26,8 +26,8 @@ class RTRun(torch.autograd.Function):
     """final (xHII, xHeII, xHeIII, T, N, F) = RTRun.apply(sim, dt, nsteps,
     every, src_ijk, nH, L, xHII0, xHeII0, xHeIII0, T0, N0, F0).
 
-    sim: an rt.RT handle (precision RT_FP64, flux RT_GLF for the backward
-    pass); src_ijk: int array [n][3]; nH [cells], L [n][G] and the initial
+    sim: an rt.RT handle (precision RT_FP64, the OTSA and no smoothing for
+    the backward pass; flux RT_GLF or RT_HLL); src_ijk: int array [n][3]; nH [cells], L [n][G] and the initial
     state: CUDA float64 tensors in the library layout."""
 
     @staticmethod

@@ -267,7 +267,7 @@ ThermoParams class_params(const rt_batch *b, const ClassData &c, double dt)
     p.helium = (Y > 0.0) ? 1 : 0;
     p.case_b = 1;
     p.max_sub = b->opt.max_subcycles;
-    p.pass1_attempts = 6;
+    default_routing(p);
     p.gc = c.gc;
     return p;
 }

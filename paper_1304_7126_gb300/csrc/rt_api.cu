@@ -59,6 +59,7 @@ struct rt_handle {
     unsigned long long *adj_count = nullptr;
 
     bool state_set = false;
+    ThermoParams routing{};   // only the routing fields are used (rt_set_thermo_routing)
     cudaGraphExec_t graph = nullptr;
     double graph_dt = 0.0;
     int graph_cur0 = 0;     // ping-pong buffer the captured pair of steps starts from
@@ -156,7 +157,10 @@ ThermoParams thermo_params(const rt_handle *h, double dt)
     p.helium = (Y > 0.0) ? 1 : 0;
     p.case_b = h->opt.otsa ? 1 : 0;
     p.max_sub = h->opt.max_subcycles;
-    p.pass1_attempts = 6;
+    p.pass1_attempts = h->routing.pass1_attempts;
+    p.drain_budget = h->routing.drain_budget;
+    p.drain2_budget = h->routing.drain2_budget;
+    p.drain2_min = h->routing.drain2_min;
     p.emit = h->opt.otsa ? 0 : 1;
     for (int j = 0; j < 3; ++j) {
         int r = h->opt.rec_group[j];
@@ -406,7 +410,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
         if (opt->rec_group[j] != RT_REC_BY_BAND && (opt->rec_group[j] < -1 || opt->rec_group[j] >= n_groups))
             return RT_EINVAL;
     if (opt->precision != RT_FP64 && opt->precision != RT_MIXED && opt->precision != RT_MIXED32) return RT_EINVAL;
-    if (!(opt->a_exp > 0.0) || opt->max_subcycles < 1) return RT_EINVAL;
+    if (!(opt->a_exp > 0.0) || !std::isfinite(opt->a_exp) || opt->max_subcycles < 1) return RT_EINVAL;
     for (int i = 0; i < 3 * n_groups; ++i)
         if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0) || !std::isfinite(sigN[i]) || !std::isfinite(sigE[i]))
             return RT_EINVAL;
@@ -414,6 +418,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
         if (!(egy[i] > 0.0) || !std::isfinite(egy[i])) return RT_EINVAL;
 
     rt_handle *h = new rt_handle();
+    default_routing(h->routing);
     h->g.nx = grid->nx; h->g.ny = grid->ny; h->g.nz = grid->nz;
     h->g.nc = nc;
     h->g.stride = nc;
@@ -816,6 +821,20 @@ int rt_get_subcycles(rt_handle *h, int32_t *per_cell, int device_ptr)
     RT_CUDA(h, cudaMemcpy(per_cell, h->subcycles, h->g.nc * sizeof(int32_t),
                           device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     return rc;
+}
+
+int rt_set_thermo_routing(rt_handle *h, int pass1_attempts, int drain_budget, int drain2_budget,
+                          long long drain2_min_cells)
+{
+    if (!h) return RT_EINVAL;
+    ThermoParams d{};
+    default_routing(d);
+    h->routing.pass1_attempts = pass1_attempts > 0 ? pass1_attempts : d.pass1_attempts;
+    h->routing.drain_budget = drain_budget > 0 ? drain_budget : d.drain_budget;
+    h->routing.drain2_budget = drain2_budget > 0 ? drain2_budget : d.drain2_budget;
+    h->routing.drain2_min = drain2_min_cells >= 0 ? drain2_min_cells : d.drain2_min;
+    invalidate_graph(h);   // the captured launches carry the old routing
+    return RT_OK;
 }
 
 int rt_set_profiling(rt_handle *h, int enable)

@@ -65,10 +65,25 @@ struct ThermoParams {
     int case_b;
     int max_sub;
     int pass1_attempts;      // attempts before a cell is handed to the queue
+    int drain_budget;        // attempts a cell may spend in the first lane-per-cell drain
+    int drain2_budget;       // ... and in the second
+    long long drain2_min;    // the second drain runs only above this many queued cells
+                             // (< 0: eight per warp of the warp-per-cell kernel)
     int emit;                // no OTSA: recombination photons (Sec. 3.3.2)
     int rec_g[3];            // group receiving HII, HeII, HeIII recombination photons (-1: none)
     GroupConsts gc;
 };
+
+// Default routing of cells between the thermochemistry kernels.  Routing
+// decides only which kernel runs which attempts of a cell, never the
+// arithmetic of an attempt.
+inline void default_routing(ThermoParams &p)
+{
+    p.pass1_attempts = 6;
+    p.drain_budget = 192;
+    p.drain2_budget = 512;
+    p.drain2_min = -1;
+}
 
 // Device work queues of cells whose sub-cycling outlasted the first pass
 // (a) and the lane-per-cell drain (b); queue c, the input of the

@@ -22,7 +22,9 @@
 //   thermo_drain  persistent; every lane takes queue-A items one at a time,
 //                 one attempt per loop iteration, and fetches the next item
 //                 as soon as its cell completes; a cell that needs more than
-//                 kDrainBudget attempts here moves to queue B;
+//                 ThermoParams::drain_budget attempts here moves to queue B
+//                 (a second stage with its own budget runs when queue B is
+//                 long);
 //   thermo_hard   persistent; one warp per queue-B cell.  On GB300 a lone
 //                 FP64 dependent chain is slow (64 cycles per FMA, ~1000 per
 //                 exp), so the lanes of the warp evaluate the cell's
@@ -36,8 +38,10 @@
 // in thermo_f64.cu, thermo_mix.cu, thermo_mix32.cu and their smoothed-RT
 // counterparts (*_sm.cu); this file holds the launchers and the
 // allocation-free entry point.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "rt_internal.h"
@@ -100,6 +104,7 @@ constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * kNoAllocQueueBytes;
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 unsigned char *g_noalloc_addr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};   // context id the address belongs to
 
 }  // namespace
 
@@ -107,18 +112,53 @@ static __device__ __align__(256) unsigned char g_thermo_scratch[kNoAllocBytes];
 
 namespace {
 
+// Id of the current context (the driver's cuCtxGetCurrent and cuCtxGetId,
+// reached through the runtime so the library needs no link to the driver
+// library).  A device reset replaces the primary context, and with it the
+// module that holds g_thermo_scratch; the id tells the two apart.
+cudaError_t current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess) return e;
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return cudaErrorNotSupported;
+        get_current = reinterpret_cast<GetCurrent>(a);
+        get_id = reinterpret_cast<GetId>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorUnknown;
+    return cudaSuccess;
+}
+
 // Device address of g_thermo_scratch on the current device, looked up once
-// per device.  In host code the symbol names a host-side shadow, so only
-// this address may be handed to kernels.
+// per device and context (again after a device reset).  In host code the
+// symbol names a host-side shadow, so only this address may be handed to
+// kernels.
 cudaError_t noalloc_scratch(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    unsigned long long ctx = 0;
+    cudaError_t e = current_context_id(&ctx);
+    if (e != cudaSuccess || !g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
+        // (the lookup also creates the primary context if there is none yet)
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_thermo_scratch);
+        e = cudaGetSymbolAddress(&p, g_thermo_scratch);
+        if (e != cudaSuccess) return e;
+        e = current_context_id(&ctx);
         if (e != cudaSuccess) return e;
         g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_addr[dev];
     return cudaSuccess;
@@ -137,12 +177,17 @@ extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_o
     if (ncells < 1 || ncells > kNoAllocMaxCells) return RT_EINVAL;
     if (n_groups < 1 || n_groups > RT_MAX_GROUPS || !opt || !sigN || !sigE || !egy) return RT_EINVAL;
     if (!nH || !xHII || !xHeII || !xHeIII || !T || !N || !F || !subcycles) return RT_EINVAL;
-    if (!(c_r > 0.0) || !(dt > 0.0) || !(opt->X > 0.0 && opt->X <= 1.0)) return RT_EINVAL;
+    // the option and constant checks of rt_create, and a finite dt > 0
+    if (!(c_r > 0.0) || !std::isfinite(c_r) || !(dt > 0.0) || !std::isfinite(dt)) return RT_EINVAL;
+    if (!(opt->X > 0.0 && opt->X <= 1.0)) return RT_EINVAL;
     if (opt->otsa != 1 || opt->smooth != 0 || opt->precision != RT_FP64 || opt->max_subcycles < 1 ||
-        !(opt->a_exp > 0.0))
+        !(opt->a_exp > 0.0) || !std::isfinite(opt->a_exp))
         return RT_EINVAL;
     for (int i = 0; i < 3 * n_groups; ++i)
-        if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0)) return RT_EINVAL;
+        if (!(sigN[i] >= 0.0) || !(sigE[i] >= 0.0) || !std::isfinite(sigN[i]) || !std::isfinite(sigE[i]))
+            return RT_EINVAL;
+    for (int i = 0; i < n_groups; ++i)
+        if (!(egy[i] > 0.0) || !std::isfinite(egy[i])) return RT_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0, n_sm = 1;
     if (cudaGetDevice(&dev) != cudaSuccess) return RT_ECUDA;
@@ -163,7 +208,7 @@ extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_o
     tp.helium = (Y > 0.0) ? 1 : 0;
     tp.case_b = 1;
     tp.max_sub = opt->max_subcycles;
-    tp.pass1_attempts = 6;
+    default_routing(tp);
     for (int i = 0; i < n_groups; ++i) {
         for (int j = 0; j < 3; ++j) {
             tp.gc.sigN[i][j] = sigN[3 * i + j];

@@ -25,8 +25,6 @@ namespace {
 using namespace thermo_detail;
 
 constexpr int kPass1Block = 128;
-constexpr int kDrainBudget = 192;   // attempts a cell may spend in the first drain stage
-constexpr int kDrain2Budget = 512;  // ... and in the second
 
 // first: the cell's first load in this RT step (thermo_pass1)
 template <int G, bool WARP, typename P, bool R32, bool SM>
@@ -308,7 +306,7 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     if (hgrid > hneed) hgrid = hneed;
     if (hgrid < 1) hgrid = 1;
     if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
-    DrainStage d1{q.a, q.b, 0, 2, kDrainBudget, 0};
+    DrainStage d1{q.a, q.b, 0, 2, tp.drain_budget, 0};
     thermo_drain<G, P, R32, SM><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, sub,
                                                               q, d1, status);
     e = cudaGetLastError();
@@ -316,7 +314,7 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     // many more long sub-cyclers than the warp-per-cell kernel has warps:
     // they share the FP64 pipes anyway, so a lane per cell does more per
     // cycle; up to twice its warps, the warps keep each cell's path short
-    DrainStage d2{q.b, q.a, 2, 4, kDrain2Budget, 8 * hgrid};
+    DrainStage d2{q.b, q.a, 2, 4, tp.drain2_budget, tp.drain2_min < 0 ? 8 * hgrid : tp.drain2_min};
     thermo_drain<G, P, R32, SM><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, sub,
                                                               q, d2, status);
     e = cudaGetLastError();

@@ -109,9 +109,10 @@ def load(build: bool = True):
         getattr(L, name).restype = C.c_int
     L.rt_set_profiling.argtypes = [vp, C.c_int]
     L.rt_get_profile.argtypes = [vp, dp, dp]
+    L.rt_set_thermo_routing.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_longlong]
     for name in ("rt_create", "rt_set_stream", "rt_set_state", "rt_get_state", "rt_set_sources",
                  "rt_courant_dt", "rt_step", "rt_run", "rt_get_budget", "rt_get_subcycles", "rt_sync",
-                 "rt_hll_table", "rt_version", "rt_set_profiling", "rt_get_profile"):
+                 "rt_hll_table", "rt_version", "rt_set_profiling", "rt_get_profile", "rt_set_thermo_routing"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -266,6 +267,13 @@ class RT:
         s = np.zeros(self.ncells, dtype=np.int32)
         self._check(self.L.rt_get_subcycles(self.h, _ptr(s), 0), "rt_get_subcycles")
         return s.reshape(self.shape)
+
+    def set_thermo_routing(self, pass1_attempts=0, drain_budget=0, drain2_budget=0, drain2_min_cells=-1):
+        """rt_set_thermo_routing: which kernel runs which attempts of a cell
+        (never the arithmetic); 0 / -1 restore the defaults."""
+        self._check(self.L.rt_set_thermo_routing(self.h, int(pass1_attempts), int(drain_budget),
+                                                 int(drain2_budget), int(drain2_min_cells)),
+                    "rt_set_thermo_routing")
 
     PHASES = ("inject", "transport", "thermo_pass1", "thermo_drain", "reduce", "finalize")
 

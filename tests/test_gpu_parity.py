@@ -8,7 +8,7 @@ against their local scale c_r N (a component can be ~0 while |F| is not)."""
 import numpy as np
 import pytest
 
-from parity import compare, oracle_problem, rel_err
+from parity import compare, flux_err, oracle_problem, rel_err
 
 pytestmark = pytest.mark.gpu
 C_LIGHT = 2.99792458e10
@@ -74,10 +74,37 @@ def test_transport_parity(oracle_mod, R, flux, shape, bc):
     assert np.allclose(bud[:, 0], b[:, 0], rtol=1e-12)
 
 
+def _compare_off_ties(got, ref, mg, w, tol, tie_margin=1e-9):
+    """Every field of every cell whose 10%/5% decisions all had an oracle
+    margin of at least tie_margin (relative distance of the decisive ratio
+    from its threshold) within tol of the oracle, by the parity metric (the
+    scale of each field is taken over all cells).  Returns the fraction of
+    cells compared."""
+    keep = mg.reshape(-1) >= tie_margin
+    kG = np.tile(keep, w.G)
+    for k in ("xHII", "xHeII", "xHeIII", "T"):
+        o = ref[k]
+        sc = max(np.max(np.abs(o)), 1e-300)
+        e = np.abs(got[k] - o)[keep] / np.maximum(np.abs(o)[keep], 1e-6 * sc)
+        assert e.size == 0 or e.max() < tol, (k, float(e.max()))
+    oN = ref["N"]
+    sc = max(np.max(np.abs(oN)), 1e-300)
+    e = np.abs(got["N"] - oN)[kG] / np.maximum(np.abs(oN)[kG], 1e-6 * sc)
+    assert e.size == 0 or e.max() < tol, ("N", float(e.max()))
+    assert flux_err(got["F"].reshape(w.G, 3, -1)[:, :, keep], ref["F"].reshape(w.G, 3, -1)[:, :, keep],
+                    ref["N"].reshape(w.G, -1)[:, keep], w.cr, w.G) < tol
+    return float(keep.mean())
+
+
 @pytest.mark.parametrize("flux", [1, 0])
 @pytest.mark.parametrize("n,nx,ny", [(16, None, None), (18, 37, 11)])
 def test_full_step_parity_cosmo(oracle_mod, R, flux, n, nx, ny):
-    """H+He, evolving T, 3 groups, sources at the densest cells."""
+    """H+He, evolving T, 3 groups, sources at the densest cells.  Both sides
+    start every step from the oracle's state, so a tie in one step cannot
+    hide the steps after it: per step, attempt counts may differ only in
+    cells with a 10%/5% decision within 1e-9 of its threshold (oracle
+    margin), every other cell matches to 1e-10, and at least 99% of the
+    cells are compared."""
     from paper_1304_7126_gb300 import workloads as W
     w = W.small_cosmo(n, seed=3, nsrc=4, flux=flux, nx=nx, ny=ny)
     sim = R.RT.from_workload(w)
@@ -85,18 +112,84 @@ def test_full_step_parity_cosmo(oracle_mod, R, flux, n, nx, ny):
     ref = w.state()
     dt = sim.courant_dt()
     for step in range(8):
+        sim.set_state(ref)
         sim.step(dt)
         st, b, sub_o, mg = p.step(ref, dt, w.src_ijk, w.src_L)
         assert st == 0
-        sub_g = sim.subcycles()
-        differ = sub_g != sub_o
+        sub_g = sim.subcycles().reshape(-1)
+        differ = sub_g != sub_o.reshape(-1)
         # a schedule may only differ where a 10%/5% decision was a rounding tie
-        assert np.all(mg[differ] < 1e-9), (step, int(differ.sum()))
-        got = sim.get_state()
-        if not differ.any():
-            e = compare(got, ref, cr=w.cr, G=w.G)
-            assert max(e.values()) < 1e-10, (step, e)
+        assert np.all(mg.reshape(-1)[differ] < 1e-9), (step, int(differ.sum()))
+        frac = _compare_off_ties(sim.get_state(), ref, mg, w, 1e-10)
+        assert frac >= 0.99, (step, frac)
     assert sub_o.max() > 1
+
+
+def test_full_step_parity_cosmo128(oracle_mod, R):
+    """The benchmark workload itself (128^3, 3 groups, H+He, evolving T,
+    HLL, 16 sources of 1e52 photons/s): two RT steps from its initial state,
+    the GPU restarted from the oracle's state before the second, against the
+    oracle on all host cores; the same per-cell attempt counts outside
+    oracle-reported ties and 1e-10 on every other cell, which must be at
+    least 99% of them.  The source cells take hundreds of attempts, so all
+    four thermochemistry kernels run."""
+    import os
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.cosmo128()
+    sim = R.RT.from_workload(w)
+    p = oracle_problem(oracle_mod, w, nthreads=os.cpu_count() or 4)
+    ref = w.state()
+    dt = sim.courant_dt()
+    for step in range(2):
+        sim.set_state(ref)
+        sim.step(dt)
+        st, b, sub_o, mg = p.step(ref, dt, w.src_ijk, w.src_L)
+        assert st == 0
+        sub_g = sim.subcycles().reshape(-1)
+        differ = sub_g != sub_o.reshape(-1)
+        assert np.all(mg.reshape(-1)[differ] < 1e-9), (step, int(differ.sum()))
+        frac = _compare_off_ties(sim.get_state(), ref, mg, w, 1e-10)
+        print("cosmo128 step", step, "max attempts", int(sub_o.max()), "cells compared", frac)
+        assert frac >= 0.99, (step, frac)
+    assert sub_o.max() > 200
+
+
+@pytest.mark.parametrize("flux", [1, 0])
+def test_routing_reaches_every_kernel(oracle_mod, R, flux):
+    """The cells of a small box routed through all four thermochemistry
+    kernels (one first-pass attempt, two attempts in the first drain, three
+    in the second, which is forced to run, then a warp per cell): against
+    the oracle as above, and against the default routing, which must give
+    identical bits for x_HII, x_HeII, x_HeIII, T, N and the attempt counts
+    (routing never changes the arithmetic) and F within 1e-14 (the flux
+    scale is applied when a cell changes kernel)."""
+    from paper_1304_7126_gb300 import workloads as W
+    w = W.small_cosmo(16, seed=3, nsrc=4, flux=flux, nx=21, ny=13)
+    forced = R.RT.from_workload(w)
+    forced.set_thermo_routing(1, 2, 3, 0)
+    plain = R.RT.from_workload(w)
+    p = oracle_problem(oracle_mod, w, nthreads=4)
+    ref = w.state()
+    dt = forced.courant_dt()
+    for step in range(4):
+        forced.set_state(ref)
+        plain.set_state(ref)
+        forced.step(dt)
+        plain.step(dt)
+        st, b, sub_o, mg = p.step(ref, dt, w.src_ijk, w.src_L)
+        assert st == 0
+        sub_f = forced.subcycles().reshape(-1)
+        assert np.sum(sub_f > 6) > 0, "some cells must reach the warp-per-cell kernel"
+        differ = sub_f != sub_o.reshape(-1)
+        assert np.all(mg.reshape(-1)[differ] < 1e-9), (step, int(differ.sum()))
+        gf = forced.get_state()
+        frac = _compare_off_ties(gf, ref, mg, w, 1e-10)
+        assert frac >= 0.99, (step, frac)
+        gp = plain.get_state()
+        assert np.array_equal(sub_f, plain.subcycles().reshape(-1)), step
+        for k in ("N", "xHII", "xHeII", "xHeIII", "T"):
+            assert np.array_equal(gf[k], gp[k]), (step, k)
+        assert flux_err(gf["F"], gp["F"], gp["N"], w.cr, w.G) < 1e-14, step
 
 
 def test_stromgren_parity_and_front(oracle_mod, R):
