@@ -110,6 +110,9 @@ def test_transport_step_vs_50_digits(oracle_mod, flux):
     d = rng.standard_normal((G, 3, nc))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     F = cr * N[:, None, :] * rng.uniform(0.0, 0.9, size=(G, 1, nc)) * d
+    # every cell far above the closure floor (1e-30 photons/cm^3): the floor
+    # reading leaves such a state alone, so this is also the step without it
+    assert N.min() > 1e-20
     s = O.new_state(shape, G, 1e-3, 1e-6, 1e4)
     s["N"], s["F"] = N.reshape(-1).copy(), F.reshape(-1).copy()
     dt = O.courant_dt(0.8, dx, cr)

@@ -90,3 +90,39 @@ def test_lookup_interpolates(oracle_mod):
         lo, hi = oracle_mod.hll_lookup(t, f, mu)
         elo, ehi = H.eigen_extremes(f, mu)
         assert abs(lo - elo) < 2e-4 and abs(hi - ehi) < 2e-4
+
+
+def test_closure_floor(oracle_mod):
+    """The closure-floor reading (Sec. 2, Eq. (Udir) gives f = |F|/(c N) and
+    n = F/|F|, undefined for N = 0; the oracle takes f := 0, n := 0 for
+    N <= 1e-30 photons/cm^3, the isotropic D = I/3).  Above the floor the
+    closure is the printed one whatever the scale of N; at or below it a
+    cell is isotropic whatever its F."""
+    c = 3e9
+    chi = lambda f: (3 + 4 * f * f) / (5 + 2 * np.sqrt(4 - 3 * f * f))  # noqa: E731
+    d = np.array([0.6, -0.48, 0.64])
+    for N in (2e-30, 1e-20, 1e-3, 1e4):
+        F = 0.5 * c * N * d
+        D, f, n = oracle_mod.eddington(c, N, F)
+        assert f == pytest.approx(0.5, rel=1e-14)
+        np.testing.assert_allclose(n, d, rtol=1e-14)
+        a, b = 0.5 * (1 - chi(0.5)), 0.5 * (3 * chi(0.5) - 1)
+        np.testing.assert_allclose(D, a * np.eye(3) + b * np.outer(d, d), rtol=1e-14, atol=1e-16)
+    for N in (1e-30, 5e-31, 1e-300, 0.0):
+        for scale in (0.5, 1.0, 1e10):   # the flux of such a cell does not matter
+            D, f, n = oracle_mod.eddington(c, N, scale * c * max(N, 1e-30) * d)
+            assert f == 0.0 and np.all(n == 0.0)
+            np.testing.assert_allclose(D, np.eye(3) / 3.0, rtol=1e-15, atol=0.0)
+
+
+def test_dark_cell_is_isotropic_in_hll(oracle_mod):
+    """A cell at the floor gets the f = 0 wave speeds +-1/sqrt(3) in every
+    direction, as an empty cell does."""
+    from oracle import hll_table
+    tab = hll_table.table()
+    for N in (0.0, 1e-31):
+        _, f, n = oracle_mod.eddington(3e9, N, np.array([1e-22, 0.0, 0.0]))
+        for mu in n:
+            lo, hi = oracle_mod.hll_lookup(tab, f, mu)
+            assert lo == pytest.approx(-1 / np.sqrt(3), rel=1e-12)
+            assert hi == pytest.approx(1 / np.sqrt(3), rel=1e-12)
