@@ -83,26 +83,31 @@ class OracleCfg(C.Structure):
     ]
 
 
+def bind(L):
+    """Declare the oracle's C signatures on a loaded library (the oracle, or
+    its op-counting build, which exports the same functions)."""
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    L.oracle_rates.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp]
+    L.oracle_chi.argtypes = [C.c_double]
+    L.oracle_chi.restype = C.c_double
+    L.oracle_eddington.argtypes = [C.c_double, C.c_double, dp, dp, dp, dp]
+    L.oracle_hll_lookup.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp]
+    L.oracle_thermo_cell.argtypes = [C.POINTER(OracleCfg), C.c_double, C.c_double,
+                                     dp, dp, dp, dp, dp, C.c_int, C.POINTER(C.c_int), dp, dp]
+    L.oracle_courant_dt.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.oracle_courant_dt.restype = C.c_double
+    L.oracle_step.argtypes = [C.POINTER(OracleCfg), C.c_double, dp, dp, dp, dp, dp, dp, dp,
+                              C.c_int, ip, dp, dp, ip, dp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(LIB)
-            dp = C.POINTER(C.c_double)
-            ip = C.POINTER(C.c_int32)
-            L.oracle_rates.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp]
-            L.oracle_chi.argtypes = [C.c_double]
-            L.oracle_chi.restype = C.c_double
-            L.oracle_eddington.argtypes = [C.c_double, C.c_double, dp, dp, dp, dp]
-            L.oracle_hll_lookup.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp]
-            L.oracle_thermo_cell.argtypes = [C.POINTER(OracleCfg), C.c_double, C.c_double,
-                                             dp, dp, dp, dp, dp, C.c_int, C.POINTER(C.c_int), dp, dp]
-            L.oracle_courant_dt.argtypes = [C.c_double, C.c_double, C.c_double]
-            L.oracle_courant_dt.restype = C.c_double
-            L.oracle_step.argtypes = [C.POINTER(OracleCfg), C.c_double, dp, dp, dp, dp, dp, dp, dp,
-                                      C.c_int, ip, dp, dp, ip, dp]
-            _lib = L
+            _lib = bind(C.CDLL(LIB))
         return _lib
 
 

@@ -12,7 +12,7 @@ rate names are the LaTeX macros of the paper with their species subscript.
 The test test_oracle_rate_constants.py reads the JSON; rerun this script
 only to regenerate it:
 
-    python tests/golden/extract_rate_constants.py /root/reference/PAPER.md
+    python tests/golden/extract_rate_constants.py <path of the paper's LaTeX source>
 """
 import json
 import os
@@ -82,6 +82,8 @@ def main(path):
 
 
 if __name__ == "__main__":
-    fits = main(sys.argv[1] if len(sys.argv) > 1 else "/root/reference/PAPER.md")
+    if len(sys.argv) != 2:
+        raise SystemExit(__doc__)
+    fits = main(sys.argv[1])
     for k, v in fits.items():
         print(k, v["numbers"])
