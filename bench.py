@@ -29,25 +29,53 @@ METRIC = "cell-group RT updates/s (transport+thermochem)"
 UNIT = "cell-group updates/s"
 
 # Denominators.  HBM: the measured copy bandwidth of this GB300 pool
-# (MEASURED_PEAKS.json when present).  FP64: 152 SMs x 2 FP64 FMA per SM
-# per clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s, matching the 1.25 TFLOP/s
-# measured by an FMA-chain probe on the same part.
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# FP32: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz.
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
-# Flops executed per thermochemistry attempt of the one-thread path: ncu's
-# smsp__sass_thread_inst_executed_op_{d,f}{fma x2, add, mul} over the ten
-# thermo_pass1 launches of the profiling pass of cosmo128 (FP64 1.518e10,
-# FP32 9.512e10) over the first-pass attempts of those steps (21 194 255).
-# The rate transcendentals run in double-float arithmetic on the FP32 pipe.
-# (Counted before the 10% checks moved to the integer pipe and the cooling
-# became a sum of generic terms: those removed about two FP64 multiplies
-# per check and added a few per cooling term, so the count moved by a few
-# percent at most.)
-FP64_FLOP_PER_ATTEMPT = 716.0
-FP32_FLOP_PER_ATTEMPT = 4488.0
+# (MEASURED_PEAKS.json when present).  FP64 and FP32: cuBLAS DGEMM and SGEMM
+# (TF32 off) measured in the same run (measure_fp_peaks), the library's own
+# best FMA throughput on this part.
+# Algorithmic work per unit: the op-counting build of the oracle
+# (oracle/make_counts.py writes tests/golden/op_counts.json): FP64 flops per
+# thermochemistry attempt and per transport cell-group, as the oracle states
+# the method.  Transport bytes: N, F read and written once per cell-group.
 PASS1_ATTEMPTS = 6
-DRAIN1_BUDGET = 192   # attempts a queued cell spends in the first lane-per-cell drain stage
+DRAIN1_BUDGET = 192
+# DRAM bytes (read + write) per launch of the dominant phase's kernels, from
+# an ncu capture of the current kernels (profiles/); None until captured
+TRAFFIC = {}   # attempts a queued cell spends in the first lane-per-cell drain stage
+
+
+def _op_counts():
+    d = json.load(open(os.path.join(ROOT, "tests", "golden", "op_counts.json")))
+    return d["thermo_per_attempt"], d["transport_per_cell_group"]
+
+
+def measure_fp_peaks():
+    """FP64 and FP32 FMA throughput of this GPU: cuBLAS DGEMM (4096^3) and
+    SGEMM with TF32 off (8192^3) through torch.matmul, best of 5 (CUDA
+    events), in GFLOP/s."""
+    import torch
+    out = {}
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dtype, n in (("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dtype, device="cuda")
+            b = torch.randn(n, n, dtype=dtype, device="cuda")
+            c = torch.matmul(a, b)
+            best = None
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                t = e0.elapsed_time(e1) / 1e3
+                best = t if best is None else min(best, t)
+            out[name + "_gflops"] = 2.0 * n ** 3 / best / 1e9
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    out["how"] = "cuBLAS DGEMM 4096^3 and SGEMM 8192^3 (TF32 off) via torch.matmul, best of 5"
+    return out
 
 
 def _peaks():
@@ -137,61 +165,42 @@ def workload(name):
 
 
 def run_reference(args):
-    """FP64 CPU oracle on a bounded sample: one RT step of a 32^3 sub-box of
-    the workload's density field (with the sources that fall inside it) per
-    benchmark step, on all host cores."""
+    """The FP64 CPU oracle on this host's cores, on the GPU arm's workload and
+    metric: after min(W, 1) untimed warm-up step, K RT steps of the full
+    workload from its initial state (stopping early, with the steps done
+    reported, if they take more than four minutes)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import oracle as O
     w = workload(args.workload)
-    sub = _subbox(w, 32)
     cores = os.cpu_count() or 1
-    p = O.Problem(sub.shape, sub.dx, sub.G, sub.cr, sub.sigN, sub.sigE, sub.egy, X=sub.X,
-                  isothermal=sub.isothermal, otsa=sub.otsa, flux=sub.flux, bc=sub.bc, nthreads=cores)
-    dt = O.courant_dt(sub.cfl, sub.dx, sub.cr)
-    s = sub.state()
-    for _ in range(args.warmup):
-        p.step(s, dt, sub.src_ijk, sub.src_L)
-    s = sub.state()
+    p = O.Problem(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, X=w.X,
+                  isothermal=w.isothermal, otsa=w.otsa, flux=w.flux, bc=w.bc, nthreads=cores)
+    dt = O.courant_dt(w.cfl, w.dx, w.cr)
+    s = w.state()
+    for _ in range(min(args.warmup, 1)):
+        p.step(s, dt, w.src_ijk, w.src_L)
+    s = w.state()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        p.step(s, dt, sub.src_ijk, sub.src_L)
+    n = 0
+    while n < args.steps:
+        st, _, _, _ = p.step(s, dt, w.src_ijk, w.src_L)
+        assert st == 0
+        n += 1
+        if time.perf_counter() - t0 > 240.0:
+            break
     t = time.perf_counter() - t0
-    val = sub.ncells * sub.G * args.steps / t
-    sample = "one oracle RT step per benchmark step on a 32^3 sub-box (corner of the %s field, %d sources)" % (
-        w.name, len(sub.src_ijk))
+    val = w.ncells * w.G * n / t
+    sample = "RT steps 1-%d of the full %s workload from its initial state (%d requested)" % (n, w.name, args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(w),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_info()["cpu"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def _subbox(w, m):
-    """The m^3 corner of a workload (same cell size and physics)."""
-    from paper_1304_7126_gb300 import workloads as W
-    nz, ny, nx = w.shape
-    m = min(m, nz, ny, nx)
-    nH = w.nH.reshape(w.shape)[:m, :m, :m].copy()
-    s = W.Workload(name=w.name + "_sub%d" % m, shape=(m, m, m), dx=w.dx, G=w.G, cr=w.cr, sigN=w.sigN,
-                   sigE=w.sigE, egy=w.egy, X=w.X, isothermal=w.isothermal, otsa=w.otsa, flux=w.flux,
-                   bc=w.bc, steps=w.steps, cfl=w.cfl)
-    nc = m ** 3
-    s.nH = nH.reshape(-1)
-    s.xHII = w.xHII.reshape(w.shape)[:m, :m, :m].reshape(-1).copy()
-    s.xHeII = np.zeros(nc)
-    s.xHeIII = np.zeros(nc)
-    s.T = w.T.reshape(w.shape)[:m, :m, :m].reshape(-1).copy()
-    inside = np.all(w.src_ijk < m, axis=1)
-    if inside.any():
-        s.src_ijk, s.src_L = w.src_ijk[inside], w.src_L[inside]
-    else:   # keep the sample's photo-ionisation work: move the brightest source in
-        s.src_ijk = W.densest_cells(nH, 1)
-        s.src_L = w.src_L[:1]
-    return s
 
 
 def _config(w):
@@ -209,34 +218,87 @@ def _config(w):
 KERNELS_PER_PHASE = {"inject": 1, "transport": 1, "thermo_pass1": 1, "thermo_drain": 3, "reduce": 1, "finalize": 1}
 
 
-def cpu_baseline(w, seconds_hint=20.0):
-    """The oracle on this host's cores: RT steps of the full workload from its
-    initial state (as many as fit the hint, at least one), with its cells
-    spread over all cores, then one step of the same on a single thread."""
+def oracle_rate(w, nthreads, max_steps, seconds=30.0, boxes=None):
+    """The oracle on this host: RT steps of workload w from its initial state
+    (at least one, at most max_steps, stopping once `seconds` have passed),
+    its cells spread over nthreads cores (OpenMP over cells, the oracle's only
+    parallelism).  boxes: a list of workloads run one step each instead
+    (batched boxes; stops likewise).  Returns (cell-group updates/s, steps)."""
     from oracle import oracle as O
-    cores = os.cpu_count() or 1
-
-    def timed(nthreads, max_steps):
-        p = O.Problem(w.shape, w.dx, w.G, w.cr, w.sigN, w.sigE, w.egy, X=w.X, isothermal=w.isothermal,
-                      otsa=w.otsa, flux=w.flux, bc=w.bc, nthreads=nthreads)
-        dt = O.courant_dt(w.cfl, w.dx, w.cr)
-        s = w.state()
-        n = 0
-        t0 = time.perf_counter()
+    t0 = time.perf_counter()
+    units, n = 0, 0
+    for wb in (boxes if boxes is not None else [w]):
+        p = O.Problem(wb.shape, wb.dx, wb.G, wb.cr, wb.sigN, wb.sigE, wb.egy, X=wb.X, isothermal=wb.isothermal,
+                      otsa=wb.otsa, flux=wb.flux, bc=wb.bc, nthreads=nthreads,
+                      inflow=(wb.extra or {}).get("inflow"))
+        dt = O.courant_dt(wb.cfl, wb.dx, wb.cr)
+        s = wb.state()
+        k = 0
         while True:
-            p.step(s, dt, w.src_ijk, w.src_L)
-            n += 1
-            if time.perf_counter() - t0 > seconds_hint or n >= max_steps:
+            st, _, _, _ = p.step(s, dt, wb.src_ijk, wb.src_L)
+            assert st == 0
+            k += 1
+            units += wb.ncells * wb.G
+            if k >= (1 if boxes is not None else max_steps) or time.perf_counter() - t0 > seconds:
                 break
-        return n, time.perf_counter() - t0
+        n += k
+        if time.perf_counter() - t0 > seconds:
+            break
+    return units / (time.perf_counter() - t0), n
 
-    n, t = timed(cores, 3)
-    out = {"value": w.ncells * w.G * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": "first %d RT step(s) of the same %s workload from its initial state" % (n, w.name)}
+
+def cpu_info():
+    """Core count and CPU model (lscpu's model name, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cores": os.cpu_count() or 1, "cpu": model}
+
+
+def cpu_baseline(w, steps, seconds=40.0):
+    """The oracle on this host's cores over the same window as the GPU arm:
+    RT steps of the same workload from its initial state (all K, unless that
+    takes more than `seconds`), cells spread over all cores; then its first
+    step on a single thread."""
+    cores = os.cpu_count() or 1
+    v, n = oracle_rate(w, cores, steps, seconds)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "RT steps 1-%d of the same %s workload from its initial state (the GPU arm times steps 1-%d)"
+                     % (n, w.name, steps), "cpu": cpu_info()["cpu"]}
     if cores > 1:
-        n1, t1 = timed(1, 1)
-        out["single_thread"] = {"value": w.ncells * w.G * n1 / t1, "unit": UNIT, "cores": 1,
+        v1, n1 = oracle_rate(w, 1, 1, 0.0)
+        out["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
                                 "sample": "first RT step of the same workload, one thread"}
+    return out
+
+
+def variant_cpu_baseline(w, all_steps, one_steps, boxes=None, seconds=15.0):
+    """Single-thread and all-core oracle timings of a variant's workload
+    (bounded samples, as cpu_baseline)."""
+    cores = os.cpu_count() or 1
+    v, n = oracle_rate(w, cores, all_steps, seconds, boxes=boxes)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": ("%d boxes, one RT step each" % n) if boxes is not None else
+           "RT steps 1-%d from the initial state" % n}
+    if cores > 1:
+        v1, n1 = oracle_rate(w, 1, one_steps, seconds, boxes=boxes)
+        out["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                "sample": ("%d boxes, one RT step each" % n1) if boxes is not None else
+                                "RT steps 1-%d from the initial state" % n1}
     return out
 
 
@@ -259,6 +321,7 @@ def main():
                          "10%% rule with its 1e-30 floor")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the adjoint")
     ap.add_argument("--no-shadow", action="store_true", help="skip the dense-cloud shadow workload")
+    ap.add_argument("--no-stromgren", action="store_true", help="skip the 32^3 Stromgren-sphere workload")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -336,30 +399,50 @@ def main():
     dominant = max(prof, key=lambda k: prof[k][0])
     ms_launch = prof[dominant][0] / max(prof[dominant][1], 1)
     cg = w.ncells * w.G
+    th_ops, tr_ops = _op_counts()
+    fp_peaks = measure_fp_peaks()
+    fp64_peak = fp_peaks["fp64_gflops"]
+    # FP64 transport: HBM-bound by its bytes (64 B per cell-group), FP64-bound
+    # by its flops (the oracle's count per cell-group); both fractions
+    tr_ms = prof["transport"][0] / max(prof["transport"][1], 1)
+    tr_bytes = 64.0 * cg
+    tr_fpc = tr_ops["hll" if w.flux == R.RT_HLL else "glf"]["flop"]
+    tr_flop = tr_fpc * cg
+    tr_gbs = tr_bytes / (tr_ms / 1e3) / 1e9
+    tr_gfl = tr_flop / (tr_ms / 1e3) / 1e9
+    roof_ms = 1e3 * max(tr_bytes / (hbm_peak * 1e9), tr_flop / (fp64_peak * 1e9))
+    transport_roof = {
+        "kernel": "transport_kernel<double>", "ms_per_launch": tr_ms,
+        "bound": "fp64" if tr_flop / fp64_peak > tr_bytes / hbm_peak else "hbm",
+        "roof_ms_per_launch": roof_ms, "frac_of_roof": roof_ms / tr_ms,
+        "hbm": {"achieved": tr_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": tr_gbs / hbm_peak,
+                "algorithmic_bytes_per_launch": tr_bytes, "peak_kind": peak_kind},
+        "fp64": {"achieved": tr_gfl, "peak": fp64_peak, "unit": "GFLOP/s", "frac": tr_gfl / fp64_peak,
+                 "flop_per_cell_group": tr_fpc, "algorithmic_flop_per_launch": tr_flop,
+                 "peak_kind": "measured (cuBLAS DGEMM)"}}
     if dominant == "transport":
-        alg = 64.0 * cg   # FP64: N, F read and written once per cell-group
-        ach = alg / (ms_launch / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+        roof = {"bound": "hbm", "achieved": tr_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": tr_gbs / hbm_peak,
                 "traffic": None, "kernel": "transport", "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": alg}
+                "algorithmic_bytes_per_launch": tr_bytes}
     else:
-        # thermochemistry is FP64-ALU bound: flops per attempt x attempts the
-        # phase made (first pass: up to PASS1_ATTEMPTS per cell; queue
-        # drains: the rest)
+        # thermochemistry: FP64-ALU work = algorithmic flops per attempt x
+        # the attempts the phase made (first pass: up to PASS1_ATTEMPTS per
+        # cell; queue drains: the rest)
         if dominant == "thermo_pass1":
             att_per_launch = (attempts - queued_att) / args.steps
         else:
             att_per_launch = queued_att / args.steps
-        fpa = FP64_FLOP_PER_ATTEMPT
+        fpa = th_ops["flop"]
         ach = fpa * att_per_launch / (ms_launch / 1e3) / 1e9
-        ach32 = FP32_FLOP_PER_ATTEMPT * att_per_launch / (ms_launch / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None, "kernel": dominant + " (+ thermo_hard)",
-                "peak_kind": "derived FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz; 1.25 TFLOP/s measured)",
-                "flop_per_attempt": fpa, "attempts_per_launch": att_per_launch,
-                "fp32": {"achieved": ach32, "peak": FP32_PEAK_GFLOPS, "frac": ach32 / FP32_PEAK_GFLOPS,
-                         "flop_per_attempt": FP32_FLOP_PER_ATTEMPT,
-                         "peak_kind": "derived FP32 (152 SMs x 128 FMA/clk x 2.07 GHz)"}}
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s",
+                "frac": ach / fp64_peak, "traffic": TRAFFIC.get(dominant),
+                "kernel": dominant + " (two lane-per-cell drains + warp-per-cell thermo_hard)"
+                if dominant == "thermo_drain" else dominant,
+                "peak_kind": "measured (cuBLAS DGEMM, FP64)",
+                "flop_per_attempt": fpa, "transcendental_calls_per_attempt":
+                    th_ops["exp"] + th_ops["log"] + th_ops["pow"],
+                "attempts_per_launch": att_per_launch,
+                "ms_per_launch": ms_launch}
 
     # ---- end to end: host buffers through the C-ABI, copies in the timed region ----
     e2e = None
@@ -428,29 +511,79 @@ def main():
         from paper_1304_7126_gb300 import workloads as W
         boxes = W.batched(args.batched_boxes)
         kb = min(args.steps, 100)
-        bt = R.RTBatch.from_workloads(boxes, precision=R.RT_MIXED)
-        bt.set_stream(stream.cuda_stream)
-        dtb = bt.courant_dt()
-        bt.autotune(1)
-        bt.run(dtb, max(args.warmup, 3))
-        bt.sync()
-        for i, wb in enumerate(boxes):
-            bt.set_box_state(i, wb.state())
-        bt.sync()
+        cgb = sum(wb.ncells * wb.G for wb in boxes)
+        bres = {}
+        for bname, bprec in (("mixed", R.RT_MIXED), ("fp64", R.RT_FP64)):
+            bt = R.RTBatch.from_workloads(boxes, precision=bprec)
+            bt.set_stream(stream.cuda_stream)
+            dtb = bt.courant_dt()
+            bt.autotune(1)
+            bt.run(dtb, max(args.warmup, 3))
+            bt.sync()
+            for i, wb in enumerate(boxes):
+                bt.set_box_state(i, wb.state())
+            bt.sync()
+            barrier()
+            ev0.record(stream)
+            bt.run(dtb, kb)
+            ev1.record(stream)
+            ev1.synchronize()
+            bt.sync()
+            tb = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
+            bres[bname] = {"value": job_units(cgb * kb, ws) / tb, "ms_per_step": 1e3 * tb / kb}
+            bt.close()
+        # the plain FP64 path, one single-box handle per box, on the first 16
+        # boxes (one after another, kb steps each)
+        t_single, cg_single = 0.0, 0
+        for wb in boxes[:16]:
+            sb = R.RT.from_workload(wb)
+            sb.set_stream(stream.cuda_stream)
+            dts = sb.courant_dt()
+            sb.step(dts)
+            sb.set_state(wb.state())
+            sb.sync()
+            ev0.record(stream)
+            sb.run(dts, kb)
+            ev1.record(stream)
+            ev1.synchronize()
+            sb.sync()
+            t_single += ev0.elapsed_time(ev1) / 1e3
+            cg_single += wb.ncells * wb.G * kb
+            sb.close()
+        variants["batched%d" % len(boxes)] = {
+            "value": bres["mixed"]["value"], "ms_per_step": bres["mixed"]["ms_per_step"], "steps": kb,
+            "cell_groups": cgb, "cells": sum(wb.ncells for wb in boxes),
+            "precision": "mixed (FP32 transport, FP64 thermochemistry)",
+            "fp64_same_boxes": dict(bres["fp64"], precision="FP64 batch, same boxes and steps"),
+            "speedup_vs_fp64": bres["mixed"]["value"] / bres["fp64"]["value"],
+            "single_box_fp64_first16": {"value": cg_single / t_single, "boxes": 16,
+                                        "how": "one FP64 single-box handle per box, boxes run one after another"},
+            "workload": "%d boxes, side in {16,24,32,48,64}, 1 or 3 groups, HLL, c_r=c/100" % len(boxes)}
+        del boxes
+
+    # ---- the 32^3 Stromgren sphere (isothermal, one group, GLF, FP64), 500 steps ----
+    if not args.no_stromgren:
+        from paper_1304_7126_gb300 import workloads as W
+        w1 = W.stromgren32(32)
+        k1 = 500
+        s1 = R.RT.from_workload(w1)
+        s1.set_stream(stream.cuda_stream)
+        dt1 = s1.courant_dt()
+        s1.run(dt1, 3)
+        s1.set_state(w1.state())
+        s1.sync()
         barrier()
         ev0.record(stream)
-        bt.run(dtb, kb)
+        s1.run(dt1, k1)
         ev1.record(stream)
         ev1.synchronize()
-        bt.sync()
-        tb = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
-        cgb = sum(wb.ncells * wb.G for wb in boxes)
-        variants["batched%d" % len(boxes)] = {
-            "value": job_units(cgb * kb, ws) / tb, "ms_per_step": 1e3 * tb / kb, "steps": kb, "cell_groups": cgb,
-            "cells": sum(wb.ncells for wb in boxes), "precision": "mixed (FP32 transport, FP64 thermochemistry)",
-            "workload": "%d boxes, side in {16,24,32,48,64}, 1 or 3 groups, HLL, c_r=c/100" % len(boxes)}
-        bt.close()
-        del boxes
+        s1.sync()
+        t1 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, "cuda")
+        variants["stromgren32"] = {
+            "value": job_units(w1.ncells * w1.G * k1, ws) / t1, "ms_per_step": 1e3 * t1 / k1, "steps": k1,
+            "workload": "32^3 Stromgren sphere, box 6.6 kpc, n_H 1e-3, T 1e4 K fixed, 1 group, corner source, "
+                        "GLF, c_r = c/100, FP64"}
+        s1.close()
 
     # ---- 256^3 (seed 11, 64 sources): FP64, RT_MIXED and RT_MIXED32 from the
     # same state, per-field error of the reduced-precision states against FP64 ----
@@ -563,7 +696,15 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        cpu = cpu_baseline(w, args.steps)
+        from paper_1304_7126_gb300 import workloads as W
+        vcpu = {"stromgren32": (W.stromgren32(32), 500, 500, None),
+                "cosmo256": (W.cosmo256(), 2, 1, None),
+                "batched%d" % args.batched_boxes: (None, 1, 1, W.batched(16)),
+                "adjoint64": (W.adjoint64(), 10, 2, None)}
+        for name, (wv, na, n1, bx) in vcpu.items():
+            if name in variants:
+                variants[name]["cpu_baseline"] = variant_cpu_baseline(wv, na, n1, boxes=bx)
 
     if rank == 0:
         cfg = _config(w)
@@ -571,7 +712,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": cfg, "roofline": roof, "transport_roofline": transport_roof, "fp_peaks": fp_peaks,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(KERNELS_PER_PHASE[k] * v[1] for k, v in prof.items()), "clocks": clocks,
                 "phases": phases,
                 "variants": variants,

@@ -176,6 +176,11 @@ cudaError_t launch_thermo_vjp_g(const ThermoParams &tp, const double *nH, const 
 // (v is the flux part of v here).  f is clamped to 1 in the closure, so
 // where the clamp acts the terms through df vanish; below the N floor or at
 // F = 0 the closure is isotropic (f = 0, a = 1/3, b = 0).
+// b is taken in a form free of cancellation: with q = sqrt(4 - 3 f^2),
+// 3 chi - 1 = f^2 (6/(2 + q) + 12)/(5 + 2 q), so b = f^2 B(f) with
+// B = (3/(2 + q) + 6)/(5 + 2 q), and c^2 N b / |F| = c f B.  Written as
+// 0.5 (3 chi - 1), b is rounding noise of ~1e-17 for f << 1e-8, and that
+// noise divided by |F| = c N f grew without bound as f -> 0.
 __device__ __forceinline__ void phi_vjp(double N, const double F[3], int d, double c, const double v[4],
                                         double out[4])
 {
@@ -195,7 +200,8 @@ __device__ __forceinline__ void phi_vjp(double N, const double F[3], int d, doub
     const double den = 5.0 + 2.0 * q;
     const double chi = (3.0 + 4.0 * f2) / den;
     const double dchi = (8.0 * f * den + 6.0 * f * (3.0 + 4.0 * f2) / q) / (den * den);
-    const double a = 0.5 * (1.0 - chi), b = 0.5 * (3.0 * chi - 1.0);
+    const double B = (3.0 / (2.0 + q) + 6.0) / den;
+    const double a = 0.5 * (1.0 - chi), b = f2 * B;
     const double da = -0.5 * dchi, db = 1.5 * dchi;
     const double vn = v[1] * n[0] + v[2] * n[1] + v[3] * n[2];
     const double vd = v[1 + d], nd = n[d];
@@ -207,7 +213,9 @@ __device__ __forceinline__ void phi_vjp(double N, const double F[3], int d, doub
     out[1 + d] = v[0];
     if (dir) {
         const double k1 = clamped ? 0.0 : c * (da * vd + db * vn * nd);
-        const double K = c2 * N * b / mag;
+        // c^2 N b / |F| = c b / (|F| / (c N)): c f B unclamped; clamped
+        // (f = 1 < |F| / (c N)), c b(1) c N / |F|
+        const double K = clamped ? c * b * (c * N / mag) : c * f * B;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             out[1 + k] += k1 * n[k] + K * (nd * (v[1 + k] - vn * n[k]) + vn * ((k == d ? 1.0 : 0.0) - nd * n[k]));

@@ -71,8 +71,8 @@ def test_reference_arm_silent_off_rank_zero(monkeypatch, capsys):
 
 
 def test_reference_arm_json_line():
-    """The reference arm (the FP64 oracle on a 32^3 corner of the workload,
-    no GPU) prints one JSON line with the benchmark's keys."""
+    """The reference arm (the FP64 oracle on the full workload, no GPU)
+    prints one JSON line with the benchmark's keys."""
     import json
     import subprocess
     import sys
