@@ -332,10 +332,12 @@ int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_options *opt
                            const double *nH, double *xHII, double *xHeII, double *xHeIII,
                            double *T, double *N, double *F, int32_t *subcycles, void *stream);
 
-/* The exp (fn 0), log (fn 1), log1p (fn 2), reciprocal (fn 3) and square
- * root (fn 4) that the library's FP64 rate fits use (double-float
- * arithmetic on float pairs, table-driven exp and log after Tang
- * 1989/1990), applied to n doubles: y[i] = f(x[i]); x, y device pointers,
+/* The exp (fn 0), log (fn 1), log1p (fn 2), reciprocal (fn 3), square
+ * root (fn 4), softplus ln(1 + e^x) (fn 5) and its derivative 1/(1 + e^-x)
+ * (fn 6) that the library's FP64 rate fits use (double-float arithmetic on
+ * float pairs, table-driven exp and log after Tang 1989/1990, piecewise
+ * interpolating polynomials for softplus), applied to n doubles:
+ * y[i] = f(x[i]); x, y device pointers,
  * enqueued on `stream` (NULL: the default stream), no synchronisation.
  * For accuracy checks against CUDA's own functions.  RT_EINVAL for a bad
  * fn or null arrays. */

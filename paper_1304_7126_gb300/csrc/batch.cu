@@ -269,6 +269,7 @@ ThermoParams class_params(const rt_batch *b, const ClassData &c, double dt)
     p.max_sub = b->opt.max_subcycles;
     default_routing(p);
     p.gc = c.gc;
+    derive_group_terms(p);
     return p;
 }
 

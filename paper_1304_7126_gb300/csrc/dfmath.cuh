@@ -258,5 +258,45 @@ static __device__ __noinline__ F2 log1pd(double w)
     return add(lv, __fdividef(t.lo, v.hi));   // + c / v
 }
 
+// ln(1 + e^z) of a pair z, with its derivative 1/(1 + e^-z) as a double.
+// On [-16, 16): the interpolating polynomials of kDfSoftplusTab (degree 9
+// in t = z - middle of a 1/4-wide interval, |t| <= 1/8); the terms of
+// degree 5 and up are below 2^-24 of the value, so they are summed in
+// FP32, the rest in pair arithmetic (absolute error ~1e-14 at |z| ~ 16,
+// that of the pair coefficients).  Outside (temperatures far beyond the
+// fits' range) from e^z and log1p.
+__device__ __forceinline__ F2 softplus2(F2 z, double &sig)
+{
+    if (z.hi >= (float)kDfSpLo && z.hi < -(float)kDfSpLo) {
+        int k = (int)__fmul_rn(__fadd_rn(z.hi, -(float)kDfSpLo), (float)kDfSpPer);
+        k = k < kDfSpN - 1 ? k : kDfSpN - 1;
+        const float mid = (float)kDfSpLo + ((float)k + 0.5f) / (float)kDfSpPer;   // exact
+        const F2 t = add(z, -mid);
+        const float th = t.hi;
+        const float2 *c = kDfSoftplusTab[k];
+        float r = __ldg(&c[9].x), q = 9.0f * r;
+        r = __fmaf_rn(r, th, __ldg(&c[8].x));
+        q = __fmaf_rn(q, th, 8.0f * __ldg(&c[8].x));
+        r = __fmaf_rn(r, th, __ldg(&c[7].x));
+        q = __fmaf_rn(q, th, 7.0f * __ldg(&c[7].x));
+        r = __fmaf_rn(r, th, __ldg(&c[6].x));
+        q = __fmaf_rn(q, th, 6.0f * __ldg(&c[6].x));
+        r = __fmaf_rn(r, th, __ldg(&c[5].x));
+        q = __fmaf_rn(q, th, 5.0f * __ldg(&c[5].x));
+        F2 P{r, 0.0f}, D{q, 0.0f};
+#pragma unroll
+        for (int n = 4; n >= 0; --n) {
+            const float2 cn = __ldg(&c[n]);
+            P = add(F2{cn.x, cn.y}, mul(P, t));
+            if (n >= 1) D = add(mul(F2{cn.x, cn.y}, (float)n), mul(D, t));
+        }
+        sig = to_double(D);
+        return P;
+    }
+    const double w = exp2d(z);
+    sig = w / (1.0 + w);
+    return log1pd(w);
+}
+
 }  // namespace dfm
 }  // namespace rtgb

@@ -68,6 +68,16 @@ __device__ __forceinline__ Dual rmul(const Dual &a, const Dual &b)
 }
 __device__ __forceinline__ Dual rmul(const Dual &a, double b) { return Dual(__dmul_rn(a.v, b), a.d * b); }
 __device__ __forceinline__ Dual radd(const Dual &a, const Dual &b) { return Dual(__dadd_rn(a.v, b.v), a.d + b.d); }
+// a b + c with one rounding, as written
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ Dual rfma(double a, const Dual &b, const Dual &c)
+{
+    return Dual(__fma_rn(a, b.v, c.v), a * b.d + c.d);
+}
+__device__ __forceinline__ Dual rfma(const Dual &a, const Dual &b, const Dual &c)
+{
+    return Dual(__fma_rn(a.v, b.v, c.v), a.d * b.v + a.v * b.d + c.d);
+}
 
 __device__ __forceinline__ Dual &operator+=(Dual &a, const Dual &b) { a = a + b; return a; }
 __device__ __forceinline__ Dual &operator-=(Dual &a, const Dual &b) { a = a - b; return a; }

@@ -1,6 +1,7 @@
-// rt_fmath_eval: the double-float exp, log, log1p, reciprocal and square
-// root of dfmath.cuh (the ones the FP64 rate fits use) over a device array
-// of doubles, so that their accuracy can be checked against CUDA's own.
+// rt_fmath_eval: the double-float exp, log, log1p, reciprocal, square root,
+// and softplus with its derivative of dfmath.cuh (the ones the FP64
+// thermochemistry uses) over a device array of doubles, so
+// that their accuracy can be checked against CUDA's own.
 #include <cuda_runtime.h>
 
 #include "dfmath.cuh"
@@ -17,7 +18,16 @@ __device__ double eval_one(int fn, double v)
     case 1: return to_double(logd(v));
     case 2: return (v >= 0.0 && !splittable(v)) ? log1p(v) : to_double(log1pd(v));
     case 3: return (v > 0.0 && splittable(v)) ? to_double(rcp(split(v))) : 1.0 / v;
-    default: return (v > 0.0 && splittable(v)) ? to_double(sqrt2(split(v))) : sqrt(v);
+    case 4: return (v > 0.0 && splittable(v)) ? to_double(sqrt2(split(v))) : sqrt(v);
+    case 5: {   // ln(1 + e^v)
+        double sg;
+        return to_double(softplus2(split_any(v), sg));
+    }
+    default: {   // 1 / (1 + e^-v)
+        double sg;
+        softplus2(split_any(v), sg);
+        return sg;
+    }
     }
 }
 
@@ -32,7 +42,7 @@ __global__ void fmath_kernel(int fn, long long n, const double *__restrict__ x, 
 
 extern "C" int rt_fmath_eval(int fn, long long n, const double *x, double *y, void *stream)
 {
-    if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !y))) return RT_EINVAL;
+    if (fn < 0 || fn > 6 || n < 0 || (n > 0 && (!x || !y))) return RT_EINVAL;
     if (n == 0) return RT_OK;
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;

@@ -27,6 +27,12 @@
 
 namespace rtgb {
 
+// Quotients of the thermochemistry (IEEE division; a double-float quotient
+// refined by an FP64 residual step was tried and its longer dependent chain
+// made every attempt slower)
+template <typename S>
+__device__ __forceinline__ S qdiv(const S &a, const S &b) { return a / b; }
+
 // exp arguments: exp(fma(a, ln T, fma(b, 1/T, c)))
 enum {
     E_BETA_HI = 0,   // exp(-157809.1/T): beta_HI, zeta_HI
@@ -37,7 +43,8 @@ enum {
     E_OMEGA1,        // T^-1.5 exp(-470000/T)
     E_OMEGA2,        // exp(-94000/T)
     E_ALPHA_HEII,    // (570670/T)^p
-    E_W0,            // w of the Hui & Gnedin fits HG_*
+    E_W0,            // w = exp(z) of the Hui & Gnedin fits HG_* (their z = ln w
+                     // are the arguments E_W0.. of the table; w itself is not formed)
     NEXP = E_W0 + 4
 };
 enum { HG_ALPHA_HII = 0, HG_ALPHA_HEIII, HG_ETA_HII, HG_ETA_HEIII, NHG };
@@ -59,7 +66,8 @@ template <typename S>
 struct TranscT {
     S lnT, sqrtT, invT, u;   // u = 1 / (1 + sqrt(T / 1e5))
     S e[NEXP];
-    S l[NHG];                 // log1p(w)
+    S l[NHG];                 // log1p(w) = softplus(z), z = ln w
+    S s[NHG];                 // w / (1 + w), the derivative of softplus at z
     S v[NHG];                 // exp(p ln lam - s log1p(w))
 };
 using Transc = TranscT<double>;
@@ -67,16 +75,25 @@ using Transc = TranscT<double>;
 // Rate tables: exp(a ln T + b/T + c) arguments and the Hui &
 // Gnedin parameters, case A then case B; the logarithms are of the fits'
 // temperature constants and pivots.
-static __constant__ RateTable c_rate_tab[2] = {
-    { // case A
-        {{0.0, -157809.1, 0.0}, {0.0, -285335.4, 0.0}, {0.0, -631515.0, 0.0}, {0.0, -118348.0, 0.0}, {-0.397, -473638.0, 0.0}, {-1.5, -470000.0, 0.0}, {0.0, -94000.0, 0.0}, {-0.654, 0.0, 8.668486417830579}, {-0.47, 0.0, 6.2568105714688285}, {-0.47, 0.0, 6.908582567206}, {-0.502, 0.0, 6.664858835981581}, {-0.502, 0.0, 7.361006797385964}},
-        {{1.269e-13, 12.662275226919286, 1.503, 0.47, 1.923}, {2.538e-13, 14.049024154019651, 1.503, 0.47, 1.923}, {1.778e-29, 12.662275226919286, 1.965, 0.502, 2.697}, {1.4224e-28, 14.049024154019651, 1.965, 0.502, 2.697}},
-        3e-14, 0.654 },
-    { // case B
-        {{0.0, -157809.1, 0.0}, {0.0, -285335.4, 0.0}, {0.0, -631515.0, 0.0}, {0.0, -118348.0, 0.0}, {-0.397, -473638.0, 0.0}, {-1.5, -470000.0, 0.0}, {0.0, -94000.0, 0.0}, {-0.75, 0.0, 9.940924791090113}, {-0.407, 0.0, 4.743307143753357}, {-0.407, 0.0, 5.307713957083206}, {-0.376, 0.0, 4.456105724024312}, {-0.376, 0.0, 4.977523320614049}},
-        {{2.753e-14, 12.662275226919286, 1.5, 0.407, 2.242}, {5.506e-14, 14.049024154019651, 1.5, 0.407, 2.242}, {3.435e-30, 12.662275226919286, 1.97, 0.376, 3.72}, {2.748e-29, 14.049024154019651, 1.97, 0.376, 3.72}},
-        1.26e-14, 0.75 }
-};
+#define RTGB_RATE_TAB_INIT {\
+    { /* case A */ \
+        {{0.0, -157809.1, 0.0}, {0.0, -285335.4, 0.0}, {0.0, -631515.0, 0.0}, {0.0, -118348.0, 0.0}, {-0.397, -473638.0, 0.0}, {-1.5, -470000.0, 0.0}, {0.0, -94000.0, 0.0}, {-0.654, 0.0, 8.668486417830579}, {-0.47, 0.0, 6.2568105714688285}, {-0.47, 0.0, 6.908582567206}, {-0.502, 0.0, 6.664858835981581}, {-0.502, 0.0, 7.361006797385964}},\
+        {{1.269e-13, 12.662275226919286, 1.503, 0.47, 1.923}, {2.538e-13, 14.049024154019651, 1.503, 0.47, 1.923}, {1.778e-29, 12.662275226919286, 1.965, 0.502, 2.697}, {1.4224e-28, 14.049024154019651, 1.965, 0.502, 2.697}},\
+        3e-14, 0.654 },\
+    { /* case B */ \
+        {{0.0, -157809.1, 0.0}, {0.0, -285335.4, 0.0}, {0.0, -631515.0, 0.0}, {0.0, -118348.0, 0.0}, {-0.397, -473638.0, 0.0}, {-1.5, -470000.0, 0.0}, {0.0, -94000.0, 0.0}, {-0.75, 0.0, 9.940924791090113}, {-0.407, 0.0, 4.743307143753357}, {-0.407, 0.0, 5.307713957083206}, {-0.376, 0.0, 4.456105724024312}, {-0.376, 0.0, 4.977523320614049}},\
+        {{2.753e-14, 12.662275226919286, 1.5, 0.407, 2.242}, {5.506e-14, 14.049024154019651, 1.5, 0.407, 2.242}, {3.435e-30, 12.662275226919286, 1.97, 0.376, 3.72}, {2.748e-29, 14.049024154019651, 1.97, 0.376, 3.72}},\
+        1.26e-14, 0.75 }\
+}
+// uniform reads (an index the same in every lane): the constant cache
+static __constant__ RateTable c_rate_tab[2] = RTGB_RATE_TAB_INIT;
+// lane-indexed reads (lane k evaluates term k): global memory through the
+// L1 cache, which serves different addresses of a warp in one request where
+// the constant cache would serialise them
+static __device__ const RateTable g_rate_tab[2] = RTGB_RATE_TAB_INIT;
+// compile-time copy, for the derived constants of the cooling terms
+constexpr RateTable kRateTabCx[2] = RTGB_RATE_TAB_INIT;
+#undef RTGB_RATE_TAB_INIT
 
 // Stage 1 in double-float arithmetic (dfmath.cuh): ln T, 1/T, sqrt T and u
 // as float pairs, each exponential's argument formed in pair arithmetic and
@@ -123,46 +140,54 @@ __device__ __forceinline__ dfm::F2 hg_arg(const HGPar &h, dfm::F2 lnT, dfm::F2 l
 }
 
 // Stage 1 in one thread.  need: bit k of the exponentials E_*, bit NEXP + j
-// of the Hui & Gnedin fits j.
+// of the Hui & Gnedin fits j.  A Hui & Gnedin fit A lam^p / (1 + w)^s with
+// w = (lam/l0)^r is exp(p ln lam - s softplus(z)), z = r ln(lam/l0): one
+// polynomial for ln(1 + e^z) (dfm::softplus2) instead of an exp and a log1p.
 __device__ __forceinline__ void transc_serial(double T, int case_b, unsigned need, Transc &t)
 {
     const RateTable &R = c_rate_tab[case_b];
     dfm::F2 lnT, invT;
     transc_level0(T, t, lnT, invT);
 #pragma unroll
-    for (int k = 0; k < NEXP; ++k)
+    for (int k = 0; k < E_W0; ++k)
         if (need & (1u << k)) t.e[k] = dfm::exp2d(exp_arg(R.ea[k], lnT, invT));
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
-            const dfm::F2 l = dfm::log1pd(t.e[E_W0 + j]);
+            double sg;
+            const dfm::F2 l = dfm::softplus2(exp_arg(R.ea[E_W0 + j], lnT, invT), sg);
             t.l[j] = dfm::to_double(l);
+            t.s[j] = sg;
             t.v[j] = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
         }
     }
 }
 
 // Stage 1 spread over a full warp (all 32 lanes must call it with the same
-// T); every lane ends with the complete, identical Transc.
+// T); every lane ends with the complete, identical Transc.  Lanes 0..7
+// evaluate the exponentials, lanes 8..11 the Hui & Gnedin fits.
 __device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
 {
-    const RateTable &R = c_rate_tab[case_b];
+    const RateTable &R = g_rate_tab[case_b];
     const int lane = threadIdx.x & 31;
     dfm::F2 lnT, invT;
     transc_level0(T, t, lnT, invT);
-    const int k = lane < NEXP ? lane : 0;
-    double ek = dfm::exp2d(exp_arg(R.ea[k], lnT, invT));
-    const int j = lane & 3;
-    double wj = __shfl_sync(0xffffffffu, ek, E_W0 + j);
-    const dfm::F2 l = dfm::log1pd(wj);
-    double lj = dfm::to_double(l);
-    double vj = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
+    double ek, lj = 0.0, sj = 0.0;
+    if (lane < E_W0) {
+        ek = dfm::exp2d(exp_arg(R.ea[lane], lnT, invT));
+    } else {
+        const int j = (lane - E_W0) & 3;
+        const dfm::F2 l = dfm::softplus2(exp_arg(R.ea[E_W0 + j], lnT, invT), sj);
+        lj = dfm::to_double(l);
+        ek = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
+    }
 #pragma unroll
-    for (int q = 0; q < NEXP; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
+    for (int q = 0; q < E_W0; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
 #pragma unroll
     for (int q = 0; q < NHG; ++q) {
-        t.l[q] = __shfl_sync(0xffffffffu, lj, q);
-        t.v[q] = __shfl_sync(0xffffffffu, vj, q);
+        t.l[q] = __shfl_sync(0xffffffffu, lj, E_W0 + q);
+        t.s[q] = __shfl_sync(0xffffffffu, sj, E_W0 + q);
+        t.v[q] = __shfl_sync(0xffffffffu, ek, E_W0 + q);
     }
 }
 
@@ -215,20 +240,16 @@ __device__ __forceinline__ void transc_serial_f(double T, int case_b, unsigned n
     const RateTable &R = c_rate_tab[case_b];
     float lnT, invT;
     transc_level0_f(T, t, lnT, invT);
-    float ew[NHG] = {0.0f, 0.0f, 0.0f, 0.0f};   // w of the Hui & Gnedin fits, as floats
 #pragma unroll
-    for (int k = 0; k < NEXP; ++k) {
-        if (need & (1u << k)) {
-            const float e = expf(exp_arg_f(R.ea[k], lnT, invT));
-            t.e[k] = dfm::widen(e);
-            if (k >= E_W0) ew[k - E_W0] = e;
-        }
-    }
+    for (int k = 0; k < E_W0; ++k)
+        if (need & (1u << k)) t.e[k] = dfm::widen(expf(exp_arg_f(R.ea[k], lnT, invT)));
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
-            float l = log1pf(ew[j]);
+            const float w = expf(exp_arg_f(R.ea[E_W0 + j], lnT, invT));
+            const float l = log1pf(w);
             t.l[j] = dfm::widen(l);
+            t.s[j] = dfm::widen(w / (1.0f + w));
             t.v[j] = dfm::widen(expf(hg_arg_f(R.hg[j], lnT, l)));
         }
     }
@@ -236,29 +257,34 @@ __device__ __forceinline__ void transc_serial_f(double T, int case_b, unsigned n
 
 __device__ __forceinline__ void transc_warp_f(double T, int case_b, Transc &t)
 {
-    const RateTable &R = c_rate_tab[case_b];
+    const RateTable &R = g_rate_tab[case_b];
     const int lane = threadIdx.x & 31;
     float lnT, invT;
     transc_level0_f(T, t, lnT, invT);
-    const int k = lane < NEXP ? lane : 0;
-    float ek = expf(exp_arg_f(R.ea[k], lnT, invT));
-    const int j = lane & 3;
-    float wj = __shfl_sync(0xffffffffu, ek, E_W0 + j);
-    float lj = log1pf(wj);
-    float vj = expf(hg_arg_f(R.hg[j], lnT, lj));
+    float ek, lj = 0.0f, sj = 0.0f;
+    if (lane < E_W0) {
+        ek = expf(exp_arg_f(R.ea[lane], lnT, invT));
+    } else {
+        const int j = (lane - E_W0) & 3;
+        const float w = expf(exp_arg_f(R.ea[E_W0 + j], lnT, invT));
+        lj = log1pf(w);
+        sj = w / (1.0f + w);
+        ek = expf(hg_arg_f(R.hg[j], lnT, lj));
+    }
 #pragma unroll
-    for (int q = 0; q < NEXP; ++q) t.e[q] = dfm::widen(__shfl_sync(0xffffffffu, ek, q));
+    for (int q = 0; q < E_W0; ++q) t.e[q] = dfm::widen(__shfl_sync(0xffffffffu, ek, q));
 #pragma unroll
     for (int q = 0; q < NHG; ++q) {
-        t.l[q] = dfm::widen(__shfl_sync(0xffffffffu, lj, q));
-        t.v[q] = dfm::widen(__shfl_sync(0xffffffffu, vj, q));
+        t.l[q] = dfm::widen(__shfl_sync(0xffffffffu, lj, E_W0 + q));
+        t.s[q] = dfm::widen(__shfl_sync(0xffffffffu, sj, E_W0 + q));
+        t.v[q] = dfm::widen(__shfl_sync(0xffffffffu, ek, E_W0 + q));
     }
 }
 
 // Stage 1 for a dual temperature: values from transc_serial (so they are
 // the bits of the double path), derivatives by the chain rule:
 // d lnT = dT/T, d sqrtT = sqrtT dT/(2T), d(1/T) = -dT/T^2, du = -u^2 k d sqrtT,
-// d exp(a lnT + b/T + c) = e (a d lnT + b d(1/T)), d log1p(w) = dw/(1 + w),
+// d exp(a lnT + b/T + c) = e (a d lnT + b d(1/T)), d softplus(z) = sigma dz,
 // d exp(p (lnT1 - lnT) - s l) = v (-p d lnT - s dl).
 __device__ __forceinline__ void transc_dual(const Dual &T, int case_b, unsigned need, TranscT<Dual> &t)
 {
@@ -273,14 +299,17 @@ __device__ __forceinline__ void transc_dual(const Dual &T, int case_b, unsigned 
     t.invT = Dual(p.invT, dinv);
     t.u = Dual(p.u, -p.u * p.u * 0.003162277660168379 * dsq);
 #pragma unroll
-    for (int k = 0; k < NEXP; ++k)
+    for (int k = 0; k < E_W0; ++k)
         if (need & (1u << k)) t.e[k] = Dual(p.e[k], p.e[k] * (R.ea[k].a * dln + R.ea[k].b * dinv));
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
-            const double w = p.e[E_W0 + j];
-            const double dl = t.e[E_W0 + j].d / (1.0 + w);
+            // z = a lnT + b/T + c; d softplus(z) = sigma dz, d sigma = sigma (1 - sigma) dz
+            const double dz = R.ea[E_W0 + j].a * dln + R.ea[E_W0 + j].b * dinv;
+            const double sg = p.s[j];
+            const double dl = sg * dz;
             t.l[j] = Dual(p.l[j], dl);
+            t.s[j] = Dual(sg, sg * (1.0 - sg) * dz);
             t.v[j] = Dual(p.v[j], p.v[j] * (-R.hg[j].p * dln - R.hg[j].s * dl));
         }
     }
@@ -290,8 +319,7 @@ __device__ __forceinline__ void transc_dual(const Dual &T, int case_b, unsigned 
 template <typename S>
 __device__ __forceinline__ S hg_dlog(const HGPar &h, const TranscT<S> &t, int j)
 {
-    S w = t.e[E_W0 + j];
-    return -t.invT * (h.p - h.s * h.r * w / (1.0 + w));
+    return -t.invT * (h.p - h.s * h.r * t.s[j]);
 }
 
 // bits of Transc needed by each consumer
@@ -403,7 +431,7 @@ struct CoolTerm {
 #define RTGB_COOL_ROW(C, a, b, c, e1, e2, hg, amp, sp, he) {C, a, b, c, e1, e2, hg, amp, sp, he},
 constexpr int kNCool = 11;
 // row k at compile time (the one-thread sum, unrolled)
-__device__ __forceinline__ constexpr CoolTerm cool_row(int k)
+__host__ __device__ __forceinline__ constexpr CoolTerm cool_row(int k)
 {
     constexpr CoolTerm rows[kNCool] = {RTGB_COOL_TERMS(RTGB_COOL_ROW)};
     return rows[k];
@@ -431,29 +459,58 @@ __device__ __forceinline__ S exp_dlog(const ExpArg &q, const S &x)
     return radd(rmul(x, q.a), rmul(rmul(x, x), -q.b));
 }
 
-// one term and its T-derivative
+// Per recombination case and term, the constants of the term and of its
+// log-derivative, folded at compile time:
+//   value  = Cc n_s sqrtT^sq u^uu T^tt X1 X2 v^hg, Cc = C (A_hg)^hg (A_aHeII)^amp
+//   dln/dT = invT [K0 + U (1 - u) - Kb invT + SR sigma]
+// with K0 = sq/2 + tt + a1 + a2 - hg p, U = -uu/2, Kb = b1 + b2,
+// SR = hg s r (X_k = exp(a_k ln T + b_k / T + c_k), sigma = w/(1 + w) of
+// the Hui & Gnedin fit: d ln v/dT = -(p - s r sigma)/T).
+struct CoolK {
+    double Cc, K0, U, Kb, SR;
+};
+struct CoolKTab {
+    CoolK k[2][kNCool];
+};
+constexpr CoolKTab make_cool_k()
+{
+    CoolKTab t{};
+    for (int cb = 0; cb < 2; ++cb) {
+        const RateTable &R = kRateTabCx[cb];
+        for (int k = 0; k < kNCool; ++k) {
+            const CoolTerm q = cool_row(k);
+            double Cc = q.C, K0 = 0.5 * q.sq + q.tt, Kb = 0.0, SR = 0.0;
+            if (q.e1 >= 0) { K0 += R.ea[q.e1].a; Kb += R.ea[q.e1].b; }
+            if (q.e2 >= 0) { K0 += R.ea[q.e2].a; Kb += R.ea[q.e2].b; }
+            if (q.hg >= 0) { Cc *= R.hg[q.hg].A; K0 -= R.hg[q.hg].p; SR = R.hg[q.hg].s * R.hg[q.hg].r; }
+            if (q.amp) Cc *= R.A_aHeII;
+            t.k[cb][k] = CoolK{Cc, K0, -0.5 * q.uu, Kb, SR};
+        }
+    }
+    return t;
+}
+static __device__ const CoolKTab g_cool_k = make_cool_k();
+
+// One term and its T-derivative; q the row, kc its constants.  A factor the
+// row lacks multiplies by 1 and a missing part of the log-derivative adds
+// 0 (both exact), so the one-thread sum (q known at compile time) and the
+// warp sum (q indexed by lane) give the same bits.
 template <typename S>
-__device__ __forceinline__ void cool_term(const CoolTerm &q, const RateTable &R, const TranscT<S> &t, const S &T,
+__device__ __forceinline__ void cool_term(const CoolTerm &q, const CoolK &kc, const TranscT<S> &t, const S &T,
                                           const S (&n)[NSP], S &v, S &dv)
 {
     const S x = t.invT;
-    S f = S(q.C);
-    S d = S(0.0);
-    if (q.sq) { f = rmul(f, t.sqrtT); d = radd(d, rmul(x, 0.5)); }
-    if (q.uu) { f = rmul(f, t.u); d = radd(d, rmul(rmul(radd(S(1.0), -t.u), -0.5), x)); }
-    if (q.tt) { f = rmul(f, T); d = radd(d, x); }
-    if (q.e1 >= 0) { f = rmul(f, pick(t.e, q.e1)); d = radd(d, exp_dlog(R.ea[q.e1], x)); }
-    if (q.e2 >= 0) { f = rmul(f, pick(t.e, q.e2)); d = radd(d, exp_dlog(R.ea[q.e2], x)); }
-    if (q.hg >= 0) {
-        const HGPar &h = R.hg[q.hg];
-        f = rmul(f, rmul(pick(t.v, q.hg), h.A));
-        const S w = pick(t.e, E_W0 + q.hg);
-        const S qw = w / radd(S(1.0), w);
-        d = radd(d, rmul(-x, radd(S(h.p), -rmul(qw, h.s * h.r))));
-    }
-    if (q.amp) f = rmul(f, R.A_aHeII);
-    v = rmul(f, pick(n, q.sp));
-    dv = rmul(v, d);
+    const int e1 = q.e1 >= 0 ? q.e1 : 0, e2 = q.e2 >= 0 ? q.e2 : 0, hg = q.hg >= 0 ? q.hg : 0;
+    const S one(1.0);
+    const S a = rmul(q.sq ? t.sqrtT : one, q.uu ? t.u : one);
+    const S b = rmul(q.tt ? T : one, q.e1 >= 0 ? pick(t.e, e1) : one);
+    const S c = rmul(q.e2 >= 0 ? pick(t.e, e2) : one, q.hg >= 0 ? pick(t.v, hg) : one);
+    const S f = rmul(rmul(rmul(a, b), rmul(c, pick(n, q.sp))), kc.Cc);
+    const S sg = q.hg >= 0 ? pick(t.s, hg) : S(0.0);
+    const S d = rfma(kc.U, radd(one, -t.u), S(kc.K0));
+    const S d2 = rfma(kc.SR, sg, rfma(-kc.Kb, x, d));
+    v = f;
+    dv = rmul(f, rmul(d2, x));
 }
 
 // the fixed pairwise order of a 16-lane butterfly (offsets 8, 4, 2, 1)
@@ -480,24 +537,23 @@ __device__ __forceinline__ void cool_densities(const S &nHI, const S &nHII, cons
     n[SP_FF] = radd(radd(nHII, nHeII), rmul(nHeIII, 4.0));
 }
 
+// + Compton, varpi = comp (T - T_gamma), comp = 1.017e-37 T_gamma^4 and
+// T_gamma = 2.727/a (ThermoParams::comp, ::tg); both sums times n_e
 template <typename S>
-__device__ __forceinline__ void cooling_close(double a_exp, const S &T, const S &ne, const S &Ls, const S &dLs, S &L,
-                                              S &dL)
+__device__ __forceinline__ void cooling_close(double comp, double tg, const S &T, const S &ne, const S &Ls,
+                                              const S &dLs, S &L, S &dL)
 {
-    const double Tg = 2.727 / a_exp;
-    const double Tg4 = Tg * Tg * Tg * Tg;
-    const S vp = rmul(radd(T, S(-Tg)), 1.017e-37 * Tg4);   // Compton, T_gamma = 2.727 / a
+    const S vp = rmul(radd(T, S(-tg)), comp);
     L = rmul(ne, radd(Ls, vp));
-    dL = rmul(ne, radd(dLs, S(1.017e-37 * Tg4)));
+    dL = rmul(ne, radd(dLs, S(comp)));
 }
 
 // one thread
 template <typename S>
-__device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, double a_exp, bool helium, const S &T,
-                                             const S &ne, const S &nHI, const S &nHII, const S &nHeI,
+__device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, double comp, double tg, bool helium,
+                                             const S &T, const S &ne, const S &nHI, const S &nHII, const S &nHeI,
                                              const S &nHeII, const S &nHeIII, S &L, S &dL)
 {
-    const RateTable &R = c_rate_tab[case_b];
     S n[NSP];
     cool_densities(nHI, nHII, nHeI, nHeII, nHeIII, n);
     S a[16], b[16];
@@ -509,33 +565,32 @@ __device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, do
 #pragma unroll
     for (int k = 0; k < kNCool; ++k) {
         const CoolTerm q = cool_row(k);
-        if (helium || !q.he) cool_term(q, R, t, T, n, a[k], b[k]);
+        if (helium || !q.he) cool_term(q, g_cool_k.k[case_b][k], t, T, n, a[k], b[k]);
     }
     const S Ls = tree_sum16(a), dLs = tree_sum16(b);
-    cooling_close(a_exp, T, ne, Ls, dLs, L, dL);
+    cooling_close(comp, tg, T, ne, Ls, dLs, L, dL);
 }
 
 // a full warp (all 32 lanes, the same arguments): lane k < 11 evaluates
 // term k, the sums run over shuffles in the same pairwise order
-__device__ __forceinline__ void cooling_warp(const Transc &t, int case_b, double a_exp, bool helium, double T,
-                                             double ne, double nHI, double nHII, double nHeI, double nHeII,
-                                             double nHeIII, double &L, double &dL)
+__device__ __forceinline__ void cooling_warp(const Transc &t, int case_b, double comp, double tg, bool helium,
+                                             double T, double ne, double nHI, double nHII, double nHeI,
+                                             double nHeII, double nHeIII, double &L, double &dL)
 {
-    const RateTable &R = c_rate_tab[case_b];
     double n[NSP];
     cool_densities(nHI, nHII, nHeI, nHeII, nHeIII, n);
     const int k = threadIdx.x & 15;
-    double v = 0.0, dv = 0.0;
-    if (k < kNCool) {
-        const CoolTerm q = kCoolTermsDev[k];
-        if (helium || !q.he) cool_term(q, R, t, T, n, v, dv);
-    }
+    const int kk = k < kNCool ? k : 0;
+    const CoolTerm q = kCoolTermsDev[kk];
+    double v, dv;
+    cool_term(q, g_cool_k.k[case_b][kk], t, T, n, v, dv);
+    if (k >= kNCool || (!helium && q.he)) v = dv = 0.0;
 #pragma unroll
     for (int m = 8; m >= 1; m >>= 1) {
         v = radd(v, __shfl_xor_sync(0xffffffffu, v, m));
         dv = radd(dv, __shfl_xor_sync(0xffffffffu, dv, m));
     }
-    cooling_close(a_exp, T, ne, v, dv, L, dL);
+    cooling_close(comp, tg, T, ne, v, dv, L, dL);
 }
 
 }  // namespace rtgb

@@ -167,6 +167,7 @@ ThermoParams thermo_params(const rt_handle *h, double dt)
         p.rec_g[j] = (r == RT_REC_BY_BAND) ? std::min(j, h->G - 1) : r;
     }
     p.gc = h->gc;
+    derive_group_terms(p);
     return p;
 }
 

@@ -72,7 +72,30 @@ struct ThermoParams {
     int emit;                // no OTSA: recombination photons (Sec. 3.3.2)
     int rec_g[3];            // group receiving HII, HeII, HeIII recombination photons (-1: none)
     GroupConsts gc;
+    // derived per-group terms of the photon update (derive_group_terms):
+    double crs[kMaxG][3];    // c_r sigma^N_ij, the absorption coefficient per absorber
+    double hq[kMaxG][3];     // egy_i sigma^E_ij - eps_j sigma^N_ij, photoheating per absorber
+    double tg;               // T_gamma = 2.727 / a, the Compton temperature
+    double comp;             // 1.017e-37 T_gamma^4, Compton exchange per (T - T_gamma) n_e
 };
+
+// Fill ThermoParams::crs and ::hq from cr and gc (the photoheating term of
+// Eq. (PHeat2): each absorbed photon of group i heats by its mean energy
+// minus the ionisation energy eps_j of the absorber, 13.60, 24.59, 54.42 eV),
+// and the Compton constants from a_exp.  Call after setting cr, gc, a_exp.
+inline void derive_group_terms(ThermoParams &p)
+{
+    const double ev = 1.602176634e-12;
+    const double eps[3] = {13.60 * ev, 24.59 * ev, 54.42 * ev};
+    for (int i = 0; i < kMaxG; ++i)
+        for (int j = 0; j < 3; ++j) {
+            p.crs[i][j] = p.cr * p.gc.sigN[i][j];
+            p.hq[i][j] = p.gc.egy[i] * p.gc.sigE[i][j] - eps[j] * p.gc.sigN[i][j];
+        }
+    // Compton cooling/heating of the rate appendix, varpi = 1.017e-37 T_g^4 (T - T_g)
+    p.tg = 2.727 / p.a_exp;
+    p.comp = 1.017e-37 * (p.tg * p.tg * p.tg * p.tg);
+}
 
 // Default routing of cells between the thermochemistry kernels.  Routing
 // decides only which kernel runs which attempts of a cell, never the

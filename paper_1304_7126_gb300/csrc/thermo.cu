@@ -216,6 +216,7 @@ extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_o
         }
         tp.gc.egy[i] = egy[i];
     }
+    derive_group_terms(tp);
     Queue q{};
     q.counters = reinterpret_cast<unsigned long long *>(base);
     unsigned *status = reinterpret_cast<unsigned *>(base + 8 * kQueueCounters);

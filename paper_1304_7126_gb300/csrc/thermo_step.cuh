@@ -63,7 +63,7 @@ __device__ __forceinline__ S mu_den(double X, const S &x, const S &y2, const S &
 template <typename S>
 __device__ __forceinline__ S mu_of(double X, const S &x, const S &y2, const S &y3)
 {
-    return 1.0 / mu_den(X, x, y2, y3);
+    return qdiv(S(1.0), mu_den(X, x, y2, y3));
 }
 
 
@@ -201,6 +201,65 @@ __device__ __noinline__ void recomb_rates(S T, S nHII, S nHeII, S nHeIII, S ne, 
     rj[2] = (aA[2] - aB[2]) * nHeIII * ne;
 }
 
+// Photon update of one group, Eq. (SIE photons): N_i' = (N_i + h C_i)/(1 + h D_i)
+// (C_i = 0 under the OTSA; smoothed RT adds the rate Ndot_i), F_i scaled by
+// 1/(1 + h D_i), D_i = c_r sum_j sigma^N_ij n_j with the backward absorber
+// densities; with the group's 10% and 5% checks on N_i and its terms of the
+// photo-ionisation rates sigma^N_ij c_r N_i' (t0..t2) and of the
+// photoheating c_r N_i' sum_j n_j (egy_i sigma^E_ij - eps_j sigma^N_ij)
+// (tq).  Products and sums are rounded as written.
+template <typename S>
+struct PhotonTerms {
+    S Nn, Fs, Fb, t0, t1, t2, tq;
+    bool ok, small;
+};
+
+template <bool MIX, bool SM, typename S>
+__device__ __forceinline__ void photon_group(const ThermoParams &p, int i, const S &N, const S &Fs, const S &Nd,
+                                             const S &Fb, const S &Crec, const S &nHI, const S &nHeI,
+                                             const S &nHeII, double h, PhotonTerms<S> &o)
+{
+    S inv;
+    if constexpr (MIX) {
+        // absorption coefficient in FP32; the update itself in FP64, since
+        // a cell may take thousands of sub-steps and FP32 roundings of N
+        // would accumulate past the stated 1e-4 (doubles narrowed and the
+        // float widened through integer operations, not FP64-pipe
+        // conversions)
+        const float Df = __fadd_rn(__fadd_rn(__fmul_rn(narrow(p.crs[i][0]), narrow(nHI)),
+                                             __fmul_rn(narrow(p.crs[i][1]), narrow(nHeI))),
+                                   __fmul_rn(narrow(p.crs[i][2]), narrow(nHeII)));
+        inv = qdiv(1.0, rfma(h, dfm::widen(Df), 1.0));
+    } else {
+        const S D = rfma(p.crs[i][2], nHeII, rfma(p.crs[i][1], nHeI, rmul(nHI, p.crs[i][0])));
+        inv = qdiv(S(1.0), rfma(h, D, S(1.0)));
+    }
+    // smoothed RT: N + h Ndot rounded step by step, so a cell growing
+    // linearly from zero meets its relative changes 1/k exactly
+    S Nn;
+    if constexpr (SM) Nn = rmul(radd(N, rmul(Nd + Crec, h)), inv);
+    else if (p.emit) Nn = rmul(rfma(h, Crec, N), inv);
+    else Nn = rmul(N, inv);
+    const S dN = fabs(radd(Nn, -N)), den = max0(N, kFloorN);
+    o.ok = !ratio_gt(dN, den, 0.1);
+    o.small = ratio_lt(dN, den, 0.05);
+    o.Nn = Nn;
+    o.Fs = rmul(Fs, inv);
+    if constexpr (SM) o.Fb = rmul(radd(Fb, S(h)), inv);
+    const S crN = rmul(Nn, p.cr);
+    o.t0 = rmul(crN, p.gc.sigN[i][0]);
+    o.t1 = rmul(crN, p.gc.sigN[i][1]);
+    o.t2 = rmul(crN, p.gc.sigN[i][2]);
+    o.tq = rmul(crN, rfma(p.hq[i][2], nHeII, rfma(p.hq[i][1], nHeI, rmul(nHI, p.hq[i][0]))));
+}
+
+// a double or a dual from lane `src` of the warp
+__device__ __forceinline__ double shfl_s(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ Dual shfl_s(const Dual &v, int src)
+{
+    return Dual(__shfl_sync(0xffffffffu, v.v, src), __shfl_sync(0xffffffffu, v.d, src));
+}
+
 // One thermo_step over h.  Returns true and fills `o` when the 10% rule
 // holds; `small` then tells whether every checked change stayed below 5%.
 // The checks |dX| / den > 0.1 go through ratio_gt / ratio_lt (a division
@@ -235,9 +294,9 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         TranscT<S> t;
         get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
         if constexpr (WARP)   // lane k evaluates cooling term k
-            cooling_warp(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+            cooling_warp(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
         else
-            cooling_from(t, p.case_b, p.a_exp, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+            cooling_from(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
         cc.valid = true;
     }
 
@@ -248,71 +307,77 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         cc.rvalid = true;
     }
 
-    // 1. photons
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-        S Nn;
+    // 1. photons: group i's update depends on no other group, so the warp
+    // path gives group i to lane i; the one-thread path loops over the
+    // groups; both call photon_group and sum the groups' terms in the same
+    // order (rounded as written), so they give the same bits
+    PhotonTerms<S> pt;
+    if constexpr (WARP) {
+        const int lane = threadIdx.x & 31;
+        const int gi = lane < G ? lane : 0;
         S Crec = 0.0;
         if (p.emit) {
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (p.rec_g[j] == i) Crec += cc.rj[j];
+                if (p.rec_g[j] == gi) Crec += cc.rj[j];
         }
-        if constexpr (MIX) {
-            // absorption coefficient in FP32; the update itself in FP64, since
-            // a cell may take thousands of sub-steps and FP32 roundings of
-            // N would accumulate past the stated 1e-4
-            // (doubles narrowed and the float widened through integer
-            // operations, not FP64-pipe conversions)
-            float Df = narrow(cr) * (narrow(p.gc.sigN[i][0]) * narrow(nHI) + narrow(p.gc.sigN[i][1]) * narrow(nHeI) +
-                                     narrow(p.gc.sigN[i][2]) * narrow(nHeII));
-            double inv = 1.0 / (1.0 + h * dfm::widen(Df));
-            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
-            else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
-            else Nn = s.N[i] * inv;
-            double dN = fabs(Nn - s.N[i]), den = max0(s.N[i], kFloorN);
-            if (ratio_gt(dN, den, 0.1)) return false;
-            sm = sm && ratio_lt(dN, den, 0.05);
-            o.Fs[i] = s.Fs[i] * inv;
-            if constexpr (SM) o.Fb[i] = (s.Fb[i] + h) * inv;
-        } else {
-            S D = cr * (p.gc.sigN[i][0] * nHI + p.gc.sigN[i][1] * nHeI + p.gc.sigN[i][2] * nHeII);
-            S inv = 1.0 / (1.0 + h * D);
-            // smoothed RT: Eq. (SIE photons) with the rate Ndot_i; N + h Ndot
-            // rounded step by step (no fused multiply-add), so a cell growing
-            // linearly from zero meets its relative changes 1/k exactly
-            if constexpr (SM) Nn = __dadd_rn(s.N[i], __dmul_rn(h, s.Nd[i] + Crec)) * inv;
-            else if (p.emit) Nn = (s.N[i] + h * Crec) * inv;
-            else Nn = s.N[i] * inv;
-            S dN = fabs(Nn - s.N[i]), den = max0(s.N[i], kFloorN);
-            if (ratio_gt(dN, den, 0.1)) return false;
-            sm = sm && ratio_lt(dN, den, 0.05);
-            o.Fs[i] = s.Fs[i] * inv;
-            if constexpr (SM) o.Fb[i] = (s.Fb[i] + h) * inv;
+        photon_group<MIX, SM>(p, gi, s.N[gi], s.Fs[gi], s.Nd[gi], s.Fb[gi], Crec, nHI, nHeI, nHeII, h, pt);
+        const unsigned full = 0xffffffffu;
+        if (__any_sync(full, lane < G && !pt.ok)) return false;
+        sm = __all_sync(full, lane >= G || pt.small) != 0;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            o.N[i] = shfl_s(pt.Nn, i);
+            o.Fs[i] = shfl_s(pt.Fs, i);
+            if constexpr (SM) {
+                o.Fb[i] = shfl_s(pt.Fb, i);
+                o.Nd[i] = s.Nd[i];
+            }
+            const S t0 = shfl_s(pt.t0, i), t1 = shfl_s(pt.t1, i), t2 = shfl_s(pt.t2, i), tq = shfl_s(pt.tq, i);
+            if (i == 0) {
+                gam0 = t0; gam1 = t1; gam2 = t2; heat = tq;
+            } else {
+                gam0 = radd(gam0, t0); gam1 = radd(gam1, t1); gam2 = radd(gam2, t2); heat = radd(heat, tq);
+            }
         }
-        o.N[i] = Nn;
-        if constexpr (SM) o.Nd[i] = s.Nd[i];
-        S crN = cr * Nn;
-        gam0 += p.gc.sigN[i][0] * crN;
-        gam1 += p.gc.sigN[i][1] * crN;
-        gam2 += p.gc.sigN[i][2] * crN;
-        if (!p.isothermal) {
-            heat += crN * (nHI * (p.gc.egy[i] * p.gc.sigE[i][0] - kEps0 * p.gc.sigN[i][0]) +
-                           nHeI * (p.gc.egy[i] * p.gc.sigE[i][1] - kEps1 * p.gc.sigN[i][1]) +
-                           nHeII * (p.gc.egy[i] * p.gc.sigE[i][2] - kEps2 * p.gc.sigN[i][2]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            S Crec = 0.0;
+            if (p.emit) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (p.rec_g[j] == i) Crec += cc.rj[j];
+            }
+            photon_group<MIX, SM>(p, i, s.N[i], s.Fs[i], s.Nd[i], s.Fb[i], Crec, nHI, nHeI, nHeII, h, pt);
+            if (!pt.ok) return false;
+            sm = sm && pt.small;
+            o.N[i] = pt.Nn;
+            o.Fs[i] = pt.Fs;
+            if constexpr (SM) {
+                o.Fb[i] = pt.Fb;
+                o.Nd[i] = s.Nd[i];
+            }
+            if (i == 0) {
+                gam0 = pt.t0; gam1 = pt.t1; gam2 = pt.t2; heat = pt.tq;
+            } else {
+                gam0 = radd(gam0, pt.t0); gam1 = radd(gam1, pt.t1); gam2 = radd(gam2, pt.t2);
+                heat = radd(heat, pt.tq);
+            }
         }
     }
+    if (p.isothermal) heat = 0.0;
 
     // 2. temperature
     const S mden = mu_den(p.X, x, y2, y3);
-    const S mu = 1.0 / mden;
+    const S mu = qdiv(S(1.0), mden);
     S Tmu1 = 0.0;
     if (!p.isothermal) {
         S lam = heat - cc.L;
         S dlam = -mu * cc.dL;
         const S K = iso.K;
         S Tmu = s.T * mden;
-        S dT = lam * K * h / (1.0 - dlam * K * h);
+        S dT = qdiv(lam * K * h, 1.0 - dlam * K * h);
         Tmu1 = Tmu + dT;
         S adT = fabs(dT);
         if (ratio_gt(adT, Tmu, 0.1)) return false;
@@ -339,7 +404,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     }
     S J = dC - (C + Dd) - x * (dC + dD);
     S xdot = C - x * (C + Dd);
-    S x1 = x + h * xdot / (1.0 - J * h);
+    S x1 = x + qdiv(h * xdot, 1.0 - J * h);
     x1 = min0(max0(x1, kXMin), 1.0);
     {
         S xden = max0(x, kXMin);
@@ -359,27 +424,27 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             r2 = iso.he;
         } else {
             TranscT<S> t;
-            get_transc<WARP, MIX>(Tmu1 / mu_den(p.X, x1, y2, y3), p.case_b, kNeedHe, t);
+            get_transc<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2, y3)), p.case_b, kNeedHe, t);
             he_rates_from(t, p.case_b, r2);
         }
         S C1 = y2 * r2.alpha_HeII * ne2;
         S D1 = r2.beta_HeI * ne2 + gam1;
-        S yI1 = (yI + C1 * h) / (1.0 + D1 * h);
+        S yI1 = qdiv(yI + C1 * h, 1.0 + D1 * h);
         S C2 = yI1 * (r2.beta_HeI * ne2 + gam1) + y3 * r2.alpha_HeIII * ne2;
         S D2 = (r2.beta_HeII + r2.alpha_HeII) * ne2 + gam2;
-        y2n = (y2 + C2 * h) / (1.0 + D2 * h);
+        y2n = qdiv(y2 + C2 * h, 1.0 + D2 * h);
         S ne3 = x1 * nH + (y2n + 2.0 * y3) * nHe;
         HeRatesT<S> r3;
         if (p.isothermal) {
             r3 = iso.he;
         } else {
             TranscT<S> t;
-            get_transc<WARP, MIX>(Tmu1 / mu_den(p.X, x1, y2n, y3), p.case_b, kNeedHe3, t);
+            get_transc<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2n, y3)), p.case_b, kNeedHe3, t);
             he_rates_from(t, p.case_b, r3);
         }
         S C3 = y2n * (r3.beta_HeII * ne3 + gam2);
         S D3 = r3.alpha_HeIII * ne3;
-        y3n = (y3 + C3 * h) / (1.0 + D3 * h);
+        y3n = qdiv(y3 + C3 * h, 1.0 + D3 * h);
         // conservation: lower the largest fraction (HeI largest: no change)
         if (y2n >= yI1 && y2n >= y3n) y2n = 1.0 - yI1 - y3n;
         else if (y3n >= yI1 && y3n > y2n) y3n = 1.0 - yI1 - y2n;
@@ -392,7 +457,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         if (ratio_gt(dne, den, 0.1)) return false;
         sm = sm && ratio_lt(dne, den, 0.05);
     }
-    S Tf = p.isothermal ? s.T : Tmu1 / mu_den(p.X, x1, y2n, y3n);
+    S Tf = p.isothermal ? s.T : qdiv(Tmu1, mu_den(p.X, x1, y2n, y3n));
     o.x = x1;
     o.y2 = y2n;
     o.y3 = y3n;

@@ -41,3 +41,32 @@ def test_pairs_sum_to_their_values():
         inv = mpmath.mpf(h(row[2])) + mpmath.mpf(h(row[3]))
         assert abs(lnF - mpmath.log(F)) <= mpmath.mpf(2) ** -48 * max(mpmath.log(F), mpmath.mpf(2) ** -8)
         assert abs(inv * F - 1) < mpmath.mpf(2) ** -47
+
+
+def test_softplus_polynomials():
+    """The softplus table's pair coefficients give ln(1 + e^z) within
+    2e-14 absolute (the pair precision of the constant term at |z| ~ 16)
+    and its derivative 1/(1 + e^-z) within 1e-14, at 13 points of every
+    fourth interval of [-16, 16)."""
+    mpmath = pytest.importorskip("mpmath")
+    import re
+    mpmath.mp.dps = 40
+    with open(os.path.join(CSRC, "dfmath_tables.h")) as f:
+        text = f.read()
+    num = r"(-?0x[0-9a-fp.+-]+f|0\.0f)"
+    h = lambda s: float.fromhex(s[:-1]) if s != "0.0f" else 0.0  # noqa: E731
+    lo, per, n, deg = (int(v) for v in re.search(
+        r"kDfSpLo = (-?\d+), kDfSpPer = (\d+), kDfSpN = (\d+), kDfSpDeg = (\d+)", text).groups())
+    body = text.split("kDfSoftplusTab")[1].split("};")[0]
+    pairs = re.findall(r"\{%s, %s\}" % (num, num), body)
+    assert len(pairs) == n * (deg + 1)
+    for k in range(0, n, 4):
+        c = [mpmath.mpf(h(a)) + mpmath.mpf(h(b)) for a, b in pairs[k * (deg + 1):(k + 1) * (deg + 1)]]
+        mid = lo + (mpmath.mpf(k) + mpmath.mpf(1) / 2) / per
+        for i in range(13):
+            t = (mpmath.mpf(i) / 12 - mpmath.mpf(1) / 2) / per
+            z = mid + t
+            P = sum(c[j] * t ** j for j in range(deg + 1))
+            D = sum(j * c[j] * t ** (j - 1) for j in range(1, deg + 1))
+            assert abs(P - mpmath.log1p(mpmath.exp(z))) < 2e-14
+            assert abs(D - 1 / (1 + mpmath.exp(-z))) < 1e-14

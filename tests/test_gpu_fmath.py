@@ -9,6 +9,7 @@ take CUDA's own function):
   log(x)     absolute 2^-46 max(1, |ln x|)
   log1p(w)   relative 2^-45
   1/a, sqrt  relative 2^-44
+  softplus   absolute 2^-45 max(1, |x|), its derivative absolute 2^-42
 exact at the special points (exp 0 = 1, log 1 = 0, underflow to 0,
 overflow to infinity)."""
 import numpy as np
@@ -91,3 +92,18 @@ def test_reciprocal_and_sqrt(R, fn):
     ref = xd.reciprocal() if fn == 3 else xd.sqrt()
     bound = ref.abs().cpu().numpy() * 2.0 ** -44
     assert _check(y, ref, bound) <= 1.0
+
+
+def test_softplus_and_derivative(R):
+    import torch
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(-16.0, 16.0, 400000), rng.uniform(-1.0, 1.0, 100000),
+                        np.arange(-16.0, 16.0, 0.25), [-30.0, -16.0001, 15.9999, 16.0, 25.0]])
+    xd, y = _eval(R, 5, x)
+    ref = torch.nn.functional.softplus(xd, threshold=1000.0)
+    bound = np.maximum(1.0, np.abs(x)) * 2.0 ** -45
+    assert _check(y, ref, bound) <= 1.0
+    _, s = _eval(R, 6, x)
+    sref = torch.sigmoid(xd)
+    assert _check(s, sref, np.full(x.shape, 2.0 ** -42)) <= 1.0
+
