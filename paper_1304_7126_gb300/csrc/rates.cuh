@@ -95,6 +95,56 @@ static __device__ const RateTable g_rate_tab[2] = RTGB_RATE_TAB_INIT;
 constexpr RateTable kRateTabCx[2] = RTGB_RATE_TAB_INIT;
 #undef RTGB_RATE_TAB_INIT
 
+// The table's constants as float pairs (hi = the double rounded to a float,
+// lo = the rest rounded), made at compile time: a ln T + b/T + c and
+// p (ln T1 - ln T) - s l in pair arithmetic without splitting doubles at
+// run time.
+struct RateTableF2 {
+    dfm::F2 ea[NEXP][3];   // a, b, c
+    dfm::F2 hg[NHG][3];    // ln T1, p, s
+};
+constexpr dfm::F2 pair_of(double x)
+{
+    return dfm::F2{(float)x, (float)(x - (double)(float)x)};
+}
+constexpr RateTableF2 make_rate_f2(int cb)
+{
+    RateTableF2 t{};
+    const RateTable &R = kRateTabCx[cb];
+    for (int k = 0; k < NEXP; ++k) {
+        t.ea[k][0] = pair_of(R.ea[k].a);
+        t.ea[k][1] = pair_of(R.ea[k].b);
+        t.ea[k][2] = pair_of(R.ea[k].c);
+    }
+    for (int j = 0; j < NHG; ++j) {
+        t.hg[j][0] = pair_of(R.hg[j].lnT1);
+        t.hg[j][1] = pair_of(R.hg[j].p);
+        t.hg[j][2] = pair_of(R.hg[j].s);
+    }
+    return t;
+}
+static __device__ const RateTableF2 g_rate_f2[2] = {make_rate_f2(0), make_rate_f2(1)};
+
+__device__ __forceinline__ dfm::F2 ldg2(const dfm::F2 &v)
+{
+    const float2 f = __ldg(reinterpret_cast<const float2 *>(&v));
+    return dfm::F2{f.x, f.y};
+}
+
+// a ln T + b / T + c of table entry k
+__device__ __forceinline__ dfm::F2 exp_arg2(const RateTableF2 &R, int k, dfm::F2 lnT, dfm::F2 invT)
+{
+    using namespace dfm;
+    return add(add(ldg2(R.ea[k][2]), mul(lnT, ldg2(R.ea[k][0]))), mul(invT, ldg2(R.ea[k][1])));
+}
+
+// p (ln T1 - ln T) - s l of Hui & Gnedin fit j
+__device__ __forceinline__ dfm::F2 hg_arg2(const RateTableF2 &R, int j, dfm::F2 lnT, dfm::F2 l)
+{
+    using namespace dfm;
+    return add(mul(add(ldg2(R.hg[j][0]), neg(lnT)), ldg2(R.hg[j][1])), neg(mul(l, ldg2(R.hg[j][2]))));
+}
+
 // Stage 1 in double-float arithmetic (dfmath.cuh): ln T, 1/T, sqrt T and u
 // as float pairs, each exponential's argument formed in pair arithmetic and
 // e^x returned as a double; the Transc values are the doubles of the pairs.
@@ -125,62 +175,50 @@ __device__ __forceinline__ void transc_level0(double T, Transc &t, dfm::F2 &lnT,
     t.u = to_double(u);
 }
 
-// a ln T + b / T + c
-__device__ __forceinline__ dfm::F2 exp_arg(const ExpArg &q, dfm::F2 lnT, dfm::F2 invT)
-{
-    using namespace dfm;
-    return add(add(split(q.c), mul(lnT, split(q.a))), mul(invT, split(q.b)));
-}
-
-// p (ln T1 - ln T) - s log1p(w)
-__device__ __forceinline__ dfm::F2 hg_arg(const HGPar &h, dfm::F2 lnT, dfm::F2 l)
-{
-    using namespace dfm;
-    return add(mul(add(split(h.lnT1), neg(lnT)), split(h.p)), neg(mul(l, split(h.s))));
-}
-
 // Stage 1 in one thread.  need: bit k of the exponentials E_*, bit NEXP + j
 // of the Hui & Gnedin fits j.  A Hui & Gnedin fit A lam^p / (1 + w)^s with
 // w = (lam/l0)^r is exp(p ln lam - s softplus(z)), z = r ln(lam/l0): one
 // polynomial for ln(1 + e^z) (dfm::softplus2) instead of an exp and a log1p.
 __device__ __forceinline__ void transc_serial(double T, int case_b, unsigned need, Transc &t)
 {
-    const RateTable &R = c_rate_tab[case_b];
+    const RateTableF2 &R = g_rate_f2[case_b];
     dfm::F2 lnT, invT;
     transc_level0(T, t, lnT, invT);
 #pragma unroll
     for (int k = 0; k < E_W0; ++k)
-        if (need & (1u << k)) t.e[k] = dfm::exp2d(exp_arg(R.ea[k], lnT, invT));
+        if (need & (1u << k)) t.e[k] = dfm::exp2d(exp_arg2(R, k, lnT, invT));
 #pragma unroll
     for (int j = 0; j < NHG; ++j) {
         if (need & (1u << (NEXP + j))) {
             double sg;
-            const dfm::F2 l = dfm::softplus2(exp_arg(R.ea[E_W0 + j], lnT, invT), sg);
+            const dfm::F2 l = dfm::softplus2(exp_arg2(R, E_W0 + j, lnT, invT), sg);
             t.l[j] = dfm::to_double(l);
             t.s[j] = sg;
-            t.v[j] = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
+            t.v[j] = dfm::exp2d(hg_arg2(R, j, lnT, l));
         }
     }
 }
 
 // Stage 1 spread over a full warp (all 32 lanes must call it with the same
 // T); every lane ends with the complete, identical Transc.  Lanes 0..7
-// evaluate the exponentials, lanes 8..11 the Hui & Gnedin fits.
+// take the exponentials, lanes 8..11 the Hui & Gnedin fits, and every lane
+// runs the same instructions (a warp runs divergent paths one after the
+// other): the exponential lanes pass z = 0 through the softplus and ignore
+// it, then all lanes take one exp of their argument.
 __device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
 {
-    const RateTable &R = g_rate_tab[case_b];
+    const RateTableF2 &R = g_rate_f2[case_b];
     const int lane = threadIdx.x & 31;
     dfm::F2 lnT, invT;
     transc_level0(T, t, lnT, invT);
-    double ek, lj = 0.0, sj = 0.0;
-    if (lane < E_W0) {
-        ek = dfm::exp2d(exp_arg(R.ea[lane], lnT, invT));
-    } else {
-        const int j = (lane - E_W0) & 3;
-        const dfm::F2 l = dfm::softplus2(exp_arg(R.ea[E_W0 + j], lnT, invT), sj);
-        lj = dfm::to_double(l);
-        ek = dfm::exp2d(hg_arg(R.hg[j], lnT, l));
-    }
+    const bool fit = lane >= E_W0 && lane < E_W0 + NHG;
+    const int j = (lane - E_W0) & 3;
+    const dfm::F2 arg = exp_arg2(R, lane < E_W0 ? lane : E_W0 + j, lnT, invT);
+    double sj;
+    const dfm::F2 l = dfm::softplus2(fit ? arg : dfm::F2{0.0f, 0.0f}, sj);
+    const dfm::F2 hga = hg_arg2(R, j, lnT, l);
+    const double ek = dfm::exp2d(fit ? hga : arg);
+    const double lj = dfm::to_double(l);
 #pragma unroll
     for (int q = 0; q < E_W0; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
 #pragma unroll

@@ -239,6 +239,13 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
     }
 }
 
+// The tail: a pair of warps per queued cell (warps 2k, 2k + 1 of a block).
+// Both warps run the cell's attempts in step with identical state; in each
+// attempt that needs the cooling at T(t), warp 2k + 1 evaluates it while
+// warp 2k updates the photons (PairX exchange, thermo_step.cuh).  Warp 2k
+// takes the next queue item and posts it to its partner the same way.  A
+// wait that runs out (it cannot while both warps run the same code) sets
+// the queue status bit and ends the pair.
 template <int G, typename P, bool R32, bool SM>
 __global__ void __launch_bounds__(128)
 thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double *xHeII, double *xHeIII,
@@ -247,31 +254,53 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
     unsigned long long count = q.counters[4];
     if (count > (unsigned long long)q.capacity) count = (unsigned long long)q.capacity;
     if (count == 0) return;
+    __shared__ PairX<G> px[2];
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int team = warp >> 1;
+    PairCtx pc{&px[team], warp & 1, 0, false};
+    if (lane == 0) px[team].seq[pc.role] = 0;
+    __syncthreads();
+    PairX<G> &X = px[team];
     while (true) {
+        // the item: taken by role 0, posted to role 1 (exchange pc.n)
+        const int b = pc.n & 1;
+        const int n = ++pc.n;
         unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(&q.counters[5], 1ULL);
-        it = __shfl_sync(0xffffffffu, it, 0);
+        if (pc.role == 0) {
+            if (lane == 0) {
+                it = atomicAdd(&q.counters[5], 1ULL);
+                X.item[b] = it;
+            }
+            it = __shfl_sync(0xffffffffu, it, 0);
+            pair_post(&X.seq[0], n);
+            if (!pair_wait(&X.seq[1], n, status)) return;
+        } else {
+            pair_post(&X.seq[1], n);
+            if (!pair_wait(&X.seq[0], n, status)) return;
+            it = X.item[b];
+        }
         if (it >= count) break;
         const long long c = q.a.cell[it];
         double t_left = q.a.t_left[it];
         double dt_tc = q.a.dt_tc[it];
         int att = q.a.attempts[it];
-        const double n = nH[c];
+        const double n_h = nH[c];
         CellState<G> st;
         IsoRates<> iso;
         CoolCache<> cc;
         load_cell<G, true, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
-        cell_constants(p, n, iso);
+        cell_constants(p, n_h, iso);
         bool done = false;
         while (!done) {
-            done = subcycle_once<G, true, R32, double, SM>(p, n, st, t_left, dt_tc, att, iso, cc);
+            done = subcycle_once<G, true, R32, double, SM, true>(p, n_h, st, t_left, dt_tc, att, iso, cc, &pc, status);
+            if (pc.failed) return;
             if (!done && att >= p.max_sub) {
-                if (lane == 0) atomicOr(status, kStatusSubcycle);
+                if (lane == 0 && pc.role == 0) atomicOr(status, kStatusSubcycle);
                 done = true;
             }
         }
-        if (lane == 0) {
+        if (lane == 0 && pc.role == 0) {
             store_cell<G, P, SM>(p, c, false, false, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, st, status);
             subcycles[c] = att;
         }

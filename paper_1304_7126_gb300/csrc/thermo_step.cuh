@@ -260,6 +260,129 @@ __device__ __forceinline__ Dual shfl_s(const Dual &v, int src)
     return Dual(__shfl_sync(0xffffffffu, v.v, src), __shfl_sync(0xffffffffu, v.d, src));
 }
 
+// The photon stage of an attempt (group i on lane i of a warp), filling the
+// new N_i, flux scales, the photo-ionisation rates gam_j and the
+// photoheating; false when a group breaks the 10% rule.  The recombination
+// photons C_i (without the OTSA) come from cc.rj.
+template <int G, bool MIX, bool SM, typename S>
+__device__ __forceinline__ bool photons_warp(const ThermoParams &p, const CellState<G, S> &s, const CoolCache<S> &cc,
+                                             const S &nHI, const S &nHeI, const S &nHeII, double h,
+                                             CellState<G, S> &o, S &gam0, S &gam1, S &gam2, S &heat, bool &sm)
+{
+    PhotonTerms<S> pt;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane < G ? lane : 0;
+    S Crec = 0.0;
+    if (p.emit) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (p.rec_g[j] == gi) Crec += cc.rj[j];
+    }
+    photon_group<MIX, SM>(p, gi, s.N[gi], s.Fs[gi], s.Nd[gi], s.Fb[gi], Crec, nHI, nHeI, nHeII, h, pt);
+    const unsigned full = 0xffffffffu;
+    const bool ok = !__any_sync(full, lane < G && !pt.ok);
+    sm = sm && (__all_sync(full, lane >= G || pt.small) != 0);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        o.N[i] = shfl_s(pt.Nn, i);
+        o.Fs[i] = shfl_s(pt.Fs, i);
+        if constexpr (SM) {
+            o.Fb[i] = shfl_s(pt.Fb, i);
+            o.Nd[i] = s.Nd[i];
+        }
+        const S t0 = shfl_s(pt.t0, i), t1 = shfl_s(pt.t1, i), t2 = shfl_s(pt.t2, i), tq = shfl_s(pt.tq, i);
+        if (i == 0) {
+            gam0 = t0; gam1 = t1; gam2 = t2; heat = tq;
+        } else {
+            gam0 = radd(gam0, t0); gam1 = radd(gam1, t1); gam2 = radd(gam2, t2); heat = radd(heat, tq);
+        }
+    }
+    return ok;
+}
+
+template <int G, bool MIX, bool SM, typename S>
+__device__ __forceinline__ bool photons_serial(const ThermoParams &p, const CellState<G, S> &s,
+                                               const CoolCache<S> &cc, const S &nHI, const S &nHeI, const S &nHeII,
+                                               double h, CellState<G, S> &o, S &gam0, S &gam1, S &gam2, S &heat,
+                                               bool &sm)
+{
+    PhotonTerms<S> pt;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        S Crec = 0.0;
+        if (p.emit) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (p.rec_g[j] == i) Crec += cc.rj[j];
+        }
+        photon_group<MIX, SM>(p, i, s.N[i], s.Fs[i], s.Nd[i], s.Fb[i], Crec, nHI, nHeI, nHeII, h, pt);
+        if (!pt.ok) return false;
+        sm = sm && pt.small;
+        o.N[i] = pt.Nn;
+        o.Fs[i] = pt.Fs;
+        if constexpr (SM) {
+            o.Fb[i] = pt.Fb;
+            o.Nd[i] = s.Nd[i];
+        }
+        if (i == 0) {
+            gam0 = pt.t0; gam1 = pt.t1; gam2 = pt.t2; heat = pt.tq;
+        } else {
+            gam0 = radd(gam0, pt.t0); gam1 = radd(gam1, pt.t1); gam2 = radd(gam2, pt.t2);
+            heat = radd(heat, pt.tq);
+        }
+    }
+    return true;
+}
+
+// The two warps of a pair of the warp-per-cell kernel: while one evaluates
+// the cooling at T(t) the other updates the photons; each posts its results
+// in shared memory with a sequence number and waits (bounded) for the
+// other's.  Both then hold the same values and run the rest of the attempt
+// in step.  Two buffers alternate, so a post never overwrites data the
+// partner may still be reading (every exchange is two-way).
+template <int G>
+struct PairX {
+    double N[2][G], Fs[2][G], Fb[2][G], g[2][4], L[2], dL[2];
+    int ok[2], small[2];
+    unsigned long long item[2];
+    volatile int seq[2];   // last exchange posted by role 0, role 1
+};
+
+struct PairCtx {
+    void *x;          // PairX<G> of the pair, shared memory
+    int role;         // 0: photons, 1: cooling
+    int n;            // exchanges so far (the same in both warps)
+    bool failed;      // a wait ran out (status set; the cell is abandoned)
+};
+
+constexpr long long kPairSpinLimit = 1LL << 24;   // polls before a wait gives up
+
+// post this warp's part of exchange pc.n, then wait for the partner's
+__device__ __forceinline__ void pair_post(volatile int *seq_mine, int n)
+{
+    __threadfence_block();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) *seq_mine = n;
+}
+
+__device__ __forceinline__ bool pair_wait(volatile int *seq_other, int n, unsigned *status)
+{
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        long long k = 0;
+        while (*seq_other < n && k < kPairSpinLimit) {
+            __nanosleep(32);
+            ++k;
+        }
+        ok = *seq_other >= n;
+        if (!ok) atomicOr(status, kStatusQueue);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    __threadfence_block();
+    return ok;
+}
+
 // One thermo_step over h.  Returns true and fills `o` when the 10% rule
 // holds; `small` then tells whether every checked change stayed below 5%.
 // The checks |dX| / den > 0.1 go through ratio_gt / ratio_lt (a division
@@ -269,11 +392,12 @@ __device__ __forceinline__ Dual shfl_s(const Dual &v, int src)
 //
 // S is double, or Dual for the adjoint's differentiated recomputation
 // (values bit-identical to the double path; MIX only with double).
-template <int G, bool WARP, bool MIX, typename S = double, bool SM = false>
+template <int G, bool WARP, bool MIX, typename S = double, bool SM = false, bool PAIR = false>
 __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, const CellState<G, S> &s, double h,
                                         const IsoRates<S> &iso, CoolCache<S> &cc, CellState<G, S> &o,
-                                        bool &small)
+                                        bool &small, PairCtx *pc = nullptr, unsigned *status = nullptr)
 {
+    static_assert(!PAIR || (WARP && sizeof(S) == sizeof(double)), "pairs of warps: the warp path");
     static_assert(!MIX || sizeof(S) == sizeof(double), "the mixed path is not differentiated");
     const S nHe = iso.nHe;
     const S x = s.x, y2 = s.y2, y3 = s.y3;
@@ -290,81 +414,87 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     // cooling at T(t) and the state at t (step 2 below), first: it depends on
     // nothing this sub-step computes, so its FP32-pipe transcendentals can
     // overlap the FP64 photon update; kept over rejected attempts
-    if (!p.isothermal && !cc.valid) {
-        TranscT<S> t;
-        get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
-        if constexpr (WARP)   // lane k evaluates cooling term k
-            cooling_warp(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
-        else
-            cooling_from(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
-        cc.valid = true;
-    }
-
     // recombination photons without the OTSA, Eq. (cool_N_cr), at T(t) with
     // the backward abundances; group i gains C_i = sum_j [rec_g[j] == i] rj[j]
+    // (before the cooling: a pair of warps updates the photons there)
     if (p.emit && !cc.rvalid) {
         recomb_rates<WARP, MIX>(s.T, nHII, nHeII, nHeIII, ne, cc.rj);
         cc.rvalid = true;
     }
 
+    bool pair_photons = false;   // the photon stage was done in the pair exchange
+    if (!p.isothermal && !cc.valid) {
+        if constexpr (PAIR) {
+            // role 1 evaluates the cooling, role 0 the photon stage, at once
+            PairX<G> &X = *static_cast<PairX<G> *>(pc->x);
+            const int b = pc->n & 1;
+            const int n = ++pc->n;
+            const int lane = threadIdx.x & 31;
+            if (pc->role == 1) {
+                TranscT<S> t;
+                get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
+                cooling_warp(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII,
+                             cc.L, cc.dL);
+                if (lane == 0) {
+                    X.L[b] = cc.L;
+                    X.dL[b] = cc.dL;
+                }
+                pair_post(&X.seq[1], n);
+                if (!pair_wait(&X.seq[0], n, status)) { pc->failed = true; return false; }
+                if (!X.ok[b]) { cc.valid = true; return false; }
+#pragma unroll
+                for (int i = 0; i < G; ++i) {
+                    o.N[i] = X.N[b][i];
+                    o.Fs[i] = X.Fs[b][i];
+                    if constexpr (SM) {
+                        o.Fb[i] = X.Fb[b][i];
+                        o.Nd[i] = s.Nd[i];
+                    }
+                }
+                gam0 = X.g[b][0]; gam1 = X.g[b][1]; gam2 = X.g[b][2]; heat = X.g[b][3];
+                sm = X.small[b] != 0;
+            } else {
+                const bool ok = photons_warp<G, MIX, SM>(p, s, cc, nHI, nHeI, nHeII, h, o, gam0, gam1, gam2, heat, sm);
+                if (lane == 0) {
+#pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        X.N[b][i] = o.N[i];
+                        X.Fs[b][i] = o.Fs[i];
+                        if constexpr (SM) X.Fb[b][i] = o.Fb[i];
+                    }
+                    X.g[b][0] = gam0; X.g[b][1] = gam1; X.g[b][2] = gam2; X.g[b][3] = heat;
+                    X.ok[b] = ok;
+                    X.small[b] = sm;
+                }
+                pair_post(&X.seq[0], n);
+                if (!pair_wait(&X.seq[1], n, status)) { pc->failed = true; return false; }
+                cc.L = X.L[b];
+                cc.dL = X.dL[b];
+                if (!ok) { cc.valid = true; return false; }
+            }
+            cc.valid = true;
+            pair_photons = true;
+        } else {
+            TranscT<S> t;
+            get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
+            if constexpr (WARP)   // lane k evaluates cooling term k
+                cooling_warp(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+            else
+                cooling_from(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+            cc.valid = true;
+        }
+    }
+
+
     // 1. photons: group i's update depends on no other group, so the warp
     // path gives group i to lane i; the one-thread path loops over the
     // groups; both call photon_group and sum the groups' terms in the same
     // order (rounded as written), so they give the same bits
-    PhotonTerms<S> pt;
-    if constexpr (WARP) {
-        const int lane = threadIdx.x & 31;
-        const int gi = lane < G ? lane : 0;
-        S Crec = 0.0;
-        if (p.emit) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                if (p.rec_g[j] == gi) Crec += cc.rj[j];
-        }
-        photon_group<MIX, SM>(p, gi, s.N[gi], s.Fs[gi], s.Nd[gi], s.Fb[gi], Crec, nHI, nHeI, nHeII, h, pt);
-        const unsigned full = 0xffffffffu;
-        if (__any_sync(full, lane < G && !pt.ok)) return false;
-        sm = __all_sync(full, lane >= G || pt.small) != 0;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            o.N[i] = shfl_s(pt.Nn, i);
-            o.Fs[i] = shfl_s(pt.Fs, i);
-            if constexpr (SM) {
-                o.Fb[i] = shfl_s(pt.Fb, i);
-                o.Nd[i] = s.Nd[i];
-            }
-            const S t0 = shfl_s(pt.t0, i), t1 = shfl_s(pt.t1, i), t2 = shfl_s(pt.t2, i), tq = shfl_s(pt.tq, i);
-            if (i == 0) {
-                gam0 = t0; gam1 = t1; gam2 = t2; heat = tq;
-            } else {
-                gam0 = radd(gam0, t0); gam1 = radd(gam1, t1); gam2 = radd(gam2, t2); heat = radd(heat, tq);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            S Crec = 0.0;
-            if (p.emit) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    if (p.rec_g[j] == i) Crec += cc.rj[j];
-            }
-            photon_group<MIX, SM>(p, i, s.N[i], s.Fs[i], s.Nd[i], s.Fb[i], Crec, nHI, nHeI, nHeII, h, pt);
-            if (!pt.ok) return false;
-            sm = sm && pt.small;
-            o.N[i] = pt.Nn;
-            o.Fs[i] = pt.Fs;
-            if constexpr (SM) {
-                o.Fb[i] = pt.Fb;
-                o.Nd[i] = s.Nd[i];
-            }
-            if (i == 0) {
-                gam0 = pt.t0; gam1 = pt.t1; gam2 = pt.t2; heat = pt.tq;
-            } else {
-                gam0 = radd(gam0, pt.t0); gam1 = radd(gam1, pt.t1); gam2 = radd(gam2, pt.t2);
-                heat = radd(heat, pt.tq);
-            }
-        }
+    if (!pair_photons) {
+        bool ok;
+        if constexpr (WARP) ok = photons_warp<G, MIX, SM>(p, s, cc, nHI, nHeI, nHeII, h, o, gam0, gam1, gam2, heat, sm);
+        else ok = photons_serial<G, MIX, SM>(p, s, cc, nHI, nHeI, nHeII, h, o, gam0, gam1, gam2, heat, sm);
+        if (!ok) return false;
     }
     if (p.isothermal) heat = 0.0;
 
@@ -467,17 +597,17 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
 }
 
 // One attempt of the sub-cycling loop; returns true when the cell is done.
-template <int G, bool WARP, bool MIX, typename S = double, bool SM = false>
+template <int G, bool WARP, bool MIX, typename S = double, bool SM = false, bool PAIR = false>
 __device__ __forceinline__ bool subcycle_once(const ThermoParams &p, const S &nH, CellState<G, S> &st,
                                               double &t_left, double &dt_tc, int &att, const IsoRates<S> &iso,
-                                              CoolCache<S> &cc)
+                                              CoolCache<S> &cc, PairCtx *pc = nullptr, unsigned *status = nullptr)
 {
     // t_left, dt_tc > 0: compared through their bits
     double h = (dbits(dt_tc) < dbits(t_left)) ? dt_tc : t_left;
     ++att;
     CellState<G, S> o;
     bool small = false;
-    if (attempt<G, WARP, MIX, S, SM>(p, nH, st, h, iso, cc, o, small)) {
+    if (attempt<G, WARP, MIX, S, SM, PAIR>(p, nH, st, h, iso, cc, o, small, pc, status)) {
         st = o;
         cc.valid = false;
         cc.rvalid = false;
