@@ -243,7 +243,7 @@ int rt_hll_table(int nf, int nmu, double *out);
  * and the attempt counts are identical for every routing, F may differ in
  * its last bits (the flux scale prod 1/(1 + h D_i) of the attempts run so
  * far is applied to F when a cell moves between kernels).  Values <= 0
- * (drain2_min_cells < 0) restore the defaults 6, 192, 512 and eight cells
+ * (drain2_min_cells < 0) restore the defaults 6, 96, 512 and eight cells
  * per warp of the warp-per-cell kernel.  Takes effect at the next step. */
 int rt_set_thermo_routing(rt_handle *h, int pass1_attempts, int drain_budget, int drain2_budget,
                           long long drain2_min_cells);
@@ -310,7 +310,7 @@ int rt_batch_box_tiling(const rt_batch *b, int box, int *shape, int *planes);
  * pool, or a loop with a fixed memory footprint that must not call into
  * the CUDA allocator.  No handle is needed and nothing is allocated: the
  * work queue lives in a fixed device array of the library, sized for at
- * most 262144 cells (12.6 MB held on every GPU that loads the library until
+ * most 262144 cells (29.4 MB held on every GPU that loads the library until
  * the process exits).  ncells above that returns RT_EINVAL, as do the
  * option values rt_create rejects.
  * Arguments: ncells cells in any order (one value per cell), the options,

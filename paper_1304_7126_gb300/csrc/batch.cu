@@ -182,7 +182,7 @@ void bfree_all(rt_batch *b)
     for (ClassData &c : b->cls) {
         void *ptrs[] = {c.nH, c.xHII, c.xHeII, c.xHeIII, c.T, c.N[0], c.N[1], c.F[0], c.F[1], c.sub,
                         c.q.a.cell, c.q.a.t_left, c.q.a.dt_tc, c.q.a.attempts, c.q.b.cell, c.q.b.t_left,
-                        c.q.b.dt_tc, c.q.b.attempts, c.q.counters, c.src_cell, c.src_L};
+                        c.q.b.dt_tc, c.q.b.attempts, c.q.counters, c.q.fscale, c.src_cell, c.src_L};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -498,7 +498,7 @@ int rt_batch_create(int n_boxes, const rt_grid *grids, const int *n_groups, cons
                 (rc = balloc(b, &c.q.a.dt_tc, nc)) || (rc = balloc(b, &c.q.a.attempts, nc)) ||
                 (rc = balloc(b, &c.q.b.cell, nc)) || (rc = balloc(b, &c.q.b.t_left, nc)) ||
                 (rc = balloc(b, &c.q.b.dt_tc, nc)) || (rc = balloc(b, &c.q.b.attempts, nc)) ||
-                (rc = balloc(b, &c.q.counters, kQueueCounters)))
+                (rc = balloc(b, &c.q.counters, kQueueCounters)) || (rc = balloc(b, &c.q.fscale, G * nc)))
                 goto bad;
             c.q.capacity = c.nc;
             for (int k = 0; k < 2; ++k) {

@@ -124,7 +124,7 @@ void free_all(rt_handle *h)
     h->pending.clear();
     void *ptrs[] = {h->nH, h->xHII, h->xHeII, h->xHeIII, h->T, h->N[0], h->N[1], h->F[0], h->F[1],
                     h->Nf[0], h->Nf[1], h->Ff[0], h->Ff[1], h->hllf, h->hll, h->subcycles, h->q.a.cell, h->q.a.t_left, h->q.a.dt_tc, h->q.a.attempts,
-                    h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
+                    h->q.b.cell, h->q.b.t_left, h->q.b.dt_tc, h->q.b.attempts, h->q.counters, h->q.fscale, h->part.tr_inbox, h->part.tr_outflow, h->part.th_inbox,
                     h->budget, h->status, h->src_cell, h->src_L, h->src_cell_orig, h->adj, h->adj_sub, h->Npre, h->Fpre, h->inflow_d, h->inflow_f,
                     h->adj_count};
     for (void *p : ptrs)
@@ -460,6 +460,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
             (rc = dalloc(h, &h->q.b.cell, nc)) || (rc = dalloc(h, &h->q.b.t_left, nc)) ||
             (rc = dalloc(h, &h->q.b.dt_tc, nc)) || (rc = dalloc(h, &h->q.b.attempts, nc)) ||
             (rc = dalloc(h, &h->q.counters, kQueueCounters)) ||
+            (rc = dalloc(h, &h->q.fscale, (opt->smooth ? 2 : 1) * G * nc)) ||
             (rc = dalloc(h, &h->part.tr_inbox, G * h->part.n_tr_blocks)) ||
             (rc = dalloc(h, &h->part.tr_outflow, G * h->part.n_tr_blocks)) ||
             (rc = dalloc(h, &h->part.th_inbox, G * h->part.n_red_blocks)) ||

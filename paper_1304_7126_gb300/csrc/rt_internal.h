@@ -103,7 +103,7 @@ inline void derive_group_terms(ThermoParams &p)
 inline void default_routing(ThermoParams &p)
 {
     p.pass1_attempts = 6;
-    p.drain_budget = 192;
+    p.drain_budget = 96;
     p.drain2_budget = 512;
     p.drain2_min = -1;
 }
@@ -124,6 +124,8 @@ struct Queue {
     unsigned long long *counters;   // kQueueCounters: [0] a.count, [1] a.head, [2] b.count,
                                     // [3] b.head, [4] c.count, [5] c.head
     long long capacity;             // items per queue
+    double *fscale;                 // [2G][nc]: a queued cell's flux scale Fs_i (rows 0..G-1) and,
+                                    // smoothed RT, its Fdot weight Fb_i (rows G..2G-1)
 };
 
 // Per-block partial sums of the photon budget.

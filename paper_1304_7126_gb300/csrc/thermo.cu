@@ -95,11 +95,13 @@ namespace {
 
 constexpr long long kNoAllocMaxCells = 1LL << 18;   // 262144 cells
 // layout: [0,64) queue counters, [64,68) status; from byte 256 the two
-// queues, each cell / attempts / t_left / dt_tc arrays of kNoAllocMaxCells
+// queues, each cell / attempts / t_left / dt_tc arrays of kNoAllocMaxCells,
+// then the queued cells' flux scales, RT_MAX_GROUPS x kNoAllocMaxCells doubles
 constexpr size_t kNoAllocHeader = 256;
 constexpr size_t kNoAllocQueueBytes =
     (size_t)kNoAllocMaxCells * (sizeof(uint32_t) + sizeof(int32_t) + 2 * sizeof(double));
-constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * kNoAllocQueueBytes;
+constexpr size_t kNoAllocScaleBytes = (size_t)kNoAllocMaxCells * RT_MAX_GROUPS * sizeof(double);
+constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * kNoAllocQueueBytes + kNoAllocScaleBytes;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
@@ -230,6 +232,7 @@ extern "C" int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_o
         qa[k]->dt_tc = reinterpret_cast<double *>(qb + 16 * K);
     }
     q.capacity = ncells;
+    q.fscale = reinterpret_cast<double *>(base + kNoAllocHeader + 2 * kNoAllocQueueBytes);
 
     if (cudaMemsetAsync(base, 0, kNoAllocHeader, s) != cudaSuccess) return RT_ECUDA;
     if (launch_thermo(tp, n_groups, nH, xHII, xHeII, xHeIII, T, N, F, nullptr, nullptr, subcycles, q, status, n_sm,

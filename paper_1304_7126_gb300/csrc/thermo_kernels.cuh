@@ -30,8 +30,8 @@ constexpr int kPass1Block = 128;
 template <int G, bool WARP, typename P, bool R32, bool SM>
 __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, bool first, const double *xHII,
                                           const double *xHeII, const double *xHeIII, const double *T,
-                                          const P *N, const P *Npre, CellState<G> &st, IsoRates<> &iso,
-                                          CoolCache<> &cc)
+                                          const P *N, const P *Npre, const double *fscale, CellState<G> &st,
+                                          IsoRates<> &iso, CoolCache<> &cc)
 {
     st.x = xHII[c];
     st.y2 = xHeII[c];
@@ -49,11 +49,11 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, bo
                 st.N[i] = (double)N[k];
                 st.Nd[i] = (double)Npre[k];
             }
-            st.Fb[i] = 0.0;
+            st.Fb[i] = first ? 0.0 : fscale[(long long)(G + i) * p.nc + c];
         } else {
             st.N[i] = (double)N[k];
         }
-        st.Fs[i] = 1.0;
+        st.Fs[i] = first ? 1.0 : fscale[k];
     }
     cc.valid = false;
     cc.rvalid = false;
@@ -65,11 +65,14 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, bo
     }
 }
 
-// handoff: the cell goes to a queue unfinished
+// handoff: the cell goes to a queue unfinished.  Its flux scale (and Fdot
+// weight) then goes to fscale and F keeps F_base: the flux is formed once,
+// when the cell finishes, so it does not depend on where it sub-cycled.
 template <int G, typename P, bool SM>
 __device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, bool first, bool handoff,
                                            double *xHII, double *xHeII, double *xHeIII, double *T, P *N, P *F,
-                                           P *Npre, P *Fpre, const CellState<G> &st, unsigned *status)
+                                           P *Npre, P *Fpre, double *fscale, const CellState<G> &st,
+                                           unsigned *status)
 {
     xHII[c] = st.x;
     xHeII[c] = st.y2;
@@ -79,7 +82,13 @@ __device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, b
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         N[(long long)i * p.nc + c] = (P)st.N[i];
+        bad |= !isfinite(st.N[i]);
+        if (handoff) {
+            fscale[(long long)i * p.nc + c] = st.Fs[i];
+            if constexpr (SM) fscale[(long long)(G + i) * p.nc + c] = st.Fb[i];
+        }
         if constexpr (SM) {
+            if (handoff && !first) continue;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const long long b = (3LL * i + d) * p.nc + c;
@@ -91,18 +100,21 @@ __device__ __forceinline__ void store_cell(const ThermoParams &p, long long c, b
                     base = (double)F[b];
                     fd = (double)Fpre[b];
                 }
-                F[b] = (P)(st.Fs[i] * base + st.Fb[i] * fd);
-                if (first && handoff) Fpre[b] = (P)fd;
+                if (handoff) {
+                    F[b] = Fpre[b];
+                    Fpre[b] = (P)fd;
+                } else {
+                    F[b] = (P)(st.Fs[i] * base + st.Fb[i] * fd);
+                }
             }
-            if (first && handoff) Npre[(long long)i * p.nc + c] = (P)st.Nd[i];
-        } else if (st.Fs[i] != 1.0) {
+            if (handoff) Npre[(long long)i * p.nc + c] = (P)st.Nd[i];
+        } else if (!handoff && st.Fs[i] != 1.0) {
             long long b = 3LL * i * p.nc + c;
             const P f = (P)st.Fs[i];
             F[b] *= f;
             F[b + p.nc] *= f;
             F[b + 2 * p.nc] *= f;
         }
-        bad |= !isfinite(st.N[i]);
     }
     if (bad) atomicOr(status, kStatusNonFinite);
 }
@@ -134,7 +146,7 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
         CellState<G> st;
         IsoRates<> iso;
         CoolCache<> cc;
-        load_cell<G, false, P, R32, SM>(p, c, true, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
+        load_cell<G, false, P, R32, SM>(p, c, true, xHII, xHeII, xHeIII, T, N, Npre, q.fscale, st, iso, cc);
         double n = nH[c];
         cell_constants(p, n, iso);
         bool done = false;
@@ -145,7 +157,7 @@ thermo_pass1(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             atomicOr(status, kStatusSubcycle);
             done = true;
         }
-        store_cell<G, P, SM>(p, c, true, !done, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, st, status);
+        store_cell<G, P, SM>(p, c, true, !done, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, q.fscale, st, status);
         if (done) subcycles[c] = att;
         else push = true;
     }
@@ -211,7 +223,7 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             att = ds.src.attempts[it];
             n = nH[c];
             used = 0;
-            load_cell<G, false, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
+            load_cell<G, false, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, q.fscale, st, iso, cc);
             cell_constants(p, n, iso);
             have = true;
         } else {
@@ -226,12 +238,12 @@ thermo_drain(ThermoParams p, const double *__restrict__ nH, double *xHII, double
             done = true;
         }
         if (done) {
-            store_cell<G, P, SM>(p, c, false, false, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, st, status);
+            store_cell<G, P, SM>(p, c, false, false, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, q.fscale, st, status);
             subcycles[c] = att;
             fetch();
         } else if (++used >= ds.budget) {
             // long sub-cycler: hand it to the next stage
-            store_cell<G, P, SM>(p, c, false, true, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, st, status);
+            store_cell<G, P, SM>(p, c, false, true, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, q.fscale, st, status);
             unsigned long long slot = atomicAdd(&q.counters[ds.dst_cnt], 1ULL);
             push_item(ds.dst, slot, q.capacity, (uint32_t)c, t_left, dt_tc, att, status);
             fetch();
@@ -289,7 +301,7 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
         CellState<G> st;
         IsoRates<> iso;
         CoolCache<> cc;
-        load_cell<G, true, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, st, iso, cc);
+        load_cell<G, true, P, R32, SM>(p, c, false, xHII, xHeII, xHeIII, T, N, Npre, q.fscale, st, iso, cc);
         cell_constants(p, n_h, iso);
         bool done = false;
         while (!done) {
@@ -301,7 +313,7 @@ thermo_hard(ThermoParams p, const double *__restrict__ nH, double *xHII, double 
             }
         }
         if (lane == 0 && pc.role == 0) {
-            store_cell<G, P, SM>(p, c, false, false, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, st, status);
+            store_cell<G, P, SM>(p, c, false, false, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, q.fscale, st, status);
             subcycles[c] = att;
         }
         __syncwarp();

@@ -467,11 +467,11 @@ __device__ __forceinline__ void transport_kernel_body(GridDev g, S c, S dtdx, do
     }
 }
 
-// FP64: one CTA per SM fits (FP64-pipe bound).  FP32: capped at 80
+// FP64: capped at 128 registers so that two CTAs share an SM.  FP32: capped at 80
 // registers so that three CTAs share an SM and hide the shared-memory and
 // table-lookup latencies (the FP32 kernel is latency-bound).
 template <typename S, int FLUX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
                  const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
                  const S *__restrict__ tab, const S *__restrict__ inflow, double *__restrict__ part_inbox,
