@@ -450,7 +450,7 @@ int rt_create(const rt_grid *grid, int n_groups, const rt_options *opt, double c
     transport_init();
     {
         const size_t G = (size_t)n_groups;
-        h->part.n_tr_blocks = transport_blocks_per_group(h->g);
+        h->part.n_tr_blocks = transport_grid(h->n_sm, h->mixed);
         h->part.n_red_blocks = reduce_blocks_per_group();
         if ((rc = dalloc(h, &h->nH, nc)) || (rc = dalloc(h, &h->xHII, nc)) || (rc = dalloc(h, &h->xHeII, nc)) ||
             (rc = dalloc(h, &h->xHeIII, nc)) || (rc = dalloc(h, &h->T, nc)) ||

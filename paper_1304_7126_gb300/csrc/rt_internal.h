@@ -147,7 +147,9 @@ cudaError_t launch_transport(const GridDev &g, int G, int flux, double cr, doubl
 cudaError_t launch_transport_f32(const GridDev &g, int G, int flux, double cr, double dt, const float *N0,
                                  const float *F0, float *N1, float *F1, const float *hll_table,
                                  const float *inflow, const Partials &p, cudaStream_t s);
-int transport_blocks_per_group(const GridDev &g);
+// CTAs of the single-box transport launch (persistent: a fixed number per
+// SM), and so the budget partials per group
+int transport_grid(int n_sm, bool fp32);
 // Batched transport over items [item0, item0 + nitems) of one tile shape
 // (0: 32 x 8, 1: 16 x 16); N0/F0/N1/F1 are device arrays of per-class base
 // pointers; partials are indexed by item.

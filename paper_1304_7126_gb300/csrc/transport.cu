@@ -28,8 +28,6 @@
 namespace rtgb {
 namespace {
 
-constexpr int TZC = 16;   // planes per CTA (single-box launches)
-
 template <typename S>
 struct CellQ {
     S N, Fx, Fy, Fz;            // U
@@ -152,6 +150,28 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
+
+// A thread's share of the budget sums (photons left in the box, boundary
+// outflow): a double in the FP64 path; in the FP32 path a float pair summed
+// with TwoSum (no FP64 instruction per cell; exact to ~2^-48), widened once
+// per tile.
+template <typename S> struct BudgetAcc;
+template <> struct BudgetAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct BudgetAcc<float> {
+    float s = 0.0f, e = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float t, r;
+        two_sum(s, x, t, r);
+        s = t;
+        e = __fadd_rn(e, r);
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)e; }
+};
 
 // Load U at (x, y, z) where at most one coordinate may sit one cell outside
 // the box: that position is the boundary ghost (outflow: copy; reflect:
@@ -276,8 +296,7 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
 
     CellQ<S> cur, nxt;
     S flo[4] = {0, 0, 0, 0}, fhi[4] = {0, 0, 0, 0};
-    inbox = 0.0;
-    outflow = 0.0;
+    BudgetAcc<S> in_acc, out_acc;
     if (active) {
         S n, fx, fy, fz;
         load_U<S>(g, N0, F0, inf, x, y, z0 - 1, n, fx, fy, fz);
@@ -311,53 +330,56 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
         }
         __syncthreads();
 
-        // x faces: face f of row ty lies between smem columns f and f+1, at
-        // global x position x0 + f - 1/2; thread tx owns face tx, the last
-        // thread also face TBX
-        if (y < g.ny) {
-            const int nf = (tx == TBX - 1) ? 2 : 1;
-            for (int q = 0; q < nf; ++q) {
-                const int ff = tx + q;   // q = 1 only for the last thread: face TBX
-                const int gxf = x0 + ff;
-                if (gxf <= g.nx) {
-                    CellQ<S> L, R;
-                    get_plane<S, FLUX>(s, ty + 1, ff, L);
-                    get_plane<S, FLUX>(s, ty + 1, ff + 1, R);
-                    S fl[4];
-                    face_flux<S, FLUX, 0>(L, R, c, fl);
+        // x face ff of row r lies between smem columns ff and ff + 1, at
+        // global x position x0 + ff - 1/2; y face ff of column cx between
+        // smem rows ff and ff + 1.  Thread (tx, ty) takes x face tx of row ty
+        // and y face ty of column tx; the tile's far faces (x face TBX of
+        // each row, y face TBY of each column) go to warps of their own in a
+        // second pass of each (no warp runs a face pass for one lane).
+        constexpr int kFarX = ((TBX + 31) / 32) * 32;   // first thread of the far x faces
+        static_assert(kFarX + TBY <= TBX * TBY, "far faces need TBX + TBY threads in separate warps");
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            int r = ty, ff = tx;   // x face ff of row r
+            bool on = y < g.ny;
+            if (q == 1) {
+                r = tid - kFarX;
+                ff = TBX;
+                on = tid >= kFarX && tid < kFarX + TBY && y0 + r < g.ny;
+            }
+            const int gxf = x0 + ff;
+            if (on && gxf <= g.nx) {
+                CellQ<S> L, R;
+                get_plane<S, FLUX>(s, r + 1, ff, L);
+                get_plane<S, FLUX>(s, r + 1, ff + 1, R);
+                S fl[4];
+                face_flux<S, FLUX, 0>(L, R, c, fl);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) s.fxs[k][ty][ff] = fl[k];
-                    if (gxf == 0 && bc_x_lo) outflow -= (double)fl[0];
-                    if (gxf == g.nx && bc_x_hi) outflow += (double)fl[0];
-                }
+                for (int k = 0; k < 4; ++k) s.fxs[k][r][ff] = fl[k];
+                if (gxf == 0 && bc_x_lo) out_acc.add(-fl[0]);
+                if (gxf == g.nx && bc_x_hi) out_acc.add(fl[0]);
             }
         }
-        // y faces: face f of column tx lies between smem rows f and f+1
-        if (x < g.nx) {
-            int gyf = y0 + ty;
-            if (gyf <= g.ny) {
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            int cx = tx, ff = ty;   // y face ff of column cx
+            bool on = x < g.nx;
+            if (q == 1) {
+                cx = tid;
+                ff = TBY;
+                on = tid < TBX && x0 + cx < g.nx;
+            }
+            const int gyf = y0 + ff;
+            if (on && gyf <= g.ny) {
                 CellQ<S> L, R;
-                get_plane<S, FLUX>(s, ty, tx + 1, L);
-                get_plane<S, FLUX>(s, ty + 1, tx + 1, R);
+                get_plane<S, FLUX>(s, ff, cx + 1, L);
+                get_plane<S, FLUX>(s, ff + 1, cx + 1, R);
                 S fl[4];
                 face_flux<S, FLUX, 1>(L, R, c, fl);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) s.fys[k][ty][tx] = fl[k];
-                if (gyf == 0 && bc_y_lo) outflow -= (double)fl[0];
-                if (gyf == g.ny && bc_y_hi) outflow += (double)fl[0];
-            }
-            if (ty == TBY - 1) {
-                int gyt = y0 + TBY;
-                if (gyt <= g.ny) {
-                    CellQ<S> L, R;
-                    get_plane<S, FLUX>(s, TBY, tx + 1, L);
-                    get_plane<S, FLUX>(s, TBY + 1, tx + 1, R);
-                    S fl[4];
-                    face_flux<S, FLUX, 1>(L, R, c, fl);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) s.fys[k][TBY][tx] = fl[k];
-                    if (gyt == g.ny && bc_y_hi) outflow += (double)fl[0];
-                }
+                for (int k = 0; k < 4; ++k) s.fys[k][ff][cx] = fl[k];
+                if (gyf == 0 && bc_y_lo) out_acc.add(-fl[0]);
+                if (gyf == g.ny && bc_y_hi) out_acc.add(fl[0]);
             }
         }
         __syncthreads();
@@ -407,16 +429,17 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
             F1[i] = nw[1];
             F1[g.stride + i] = nw[2];
             F1[2 * g.stride + i] = nw[3];
-            inbox += (double)nw[0];
-            if (z == 0 && bc_z_lo) outflow -= (double)flo[0];
-            if (z == g.nz - 1 && bc_z_hi) outflow += (double)fhi[0];
+            in_acc.add(nw[0]);
+            if (z == 0 && bc_z_lo) out_acc.add(-flo[0]);
+            if (z == g.nz - 1 && bc_z_hi) out_acc.add(fhi[0]);
             cur = nxt;
 #pragma unroll
             for (int k = 0; k < 4; ++k) flo[k] = fhi[k];
         }
         __syncthreads();
     }
-
+    inbox = in_acc.get();
+    outflow = out_acc.get();
 }
 
 // fixed-order block reduction of the two budget sums (thread 0 gets them)
@@ -440,30 +463,74 @@ __device__ __forceinline__ void block_reduce2(double *red, double &a, double &b)
     }
 }
 
+// one column segment of the persistent kernel, out of line: inlined into the
+// segment loop it spilled registers inside the plane loop
+template <typename S, int FLUX, int TBX, int TBY>
+__device__ __noinline__ void transport_segment(PlaneSmem<S, TBX, TBY> &s, const GridDev &g, S c, S dtdx,
+                                               const S *__restrict__ N0, const S *__restrict__ F0,
+                                               S *__restrict__ N1, S *__restrict__ F1, const S *__restrict__ tab,
+                                               const S *__restrict__ inf, int x0, int y0, int z0, int z1,
+                                               double &inbox, double &outflow)
+{
+    transport_tile<S, FLUX, TBX, TBY>(s, g, c, dtdx, N0, F0, N1, F1, tab, inf, x0, y0, z0, z1, inbox, outflow);
+}
+
+// Single box: a persistent grid (kTransportCtasPerSm CTAs per SM).  The
+// (group, tile, plane) units, planes fastest, are cut into gridDim.x equal
+// contiguous ranges, one per CTA, so every CTA gets the same number of
+// planes (a launch of one CTA per tile chunk left a last, nearly empty wave);
+// a CTA walks its range one tile column segment at a time.  Budget partials:
+// [group][CTA], each the CTA's segments of that group summed in order.
 template <typename S, int FLUX>
-__device__ __forceinline__ void transport_kernel_body(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
-                 const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
-                 const S *__restrict__ tab, const S *__restrict__ inflow, double *__restrict__ part_inbox,
-                 double *__restrict__ part_out, int tiles_x, int tiles_y, int nblk)
+__device__ __forceinline__ void transport_kernel_body(GridDev g, int G, S c, S dtdx, double area_dt,
+                                                      const S *__restrict__ N0all, const S *__restrict__ F0all,
+                                                      S *__restrict__ N1all, S *__restrict__ F1all,
+                                                      const S *__restrict__ tab, const S *__restrict__ inflow,
+                                                      double *__restrict__ part_inbox,
+                                                      double *__restrict__ part_out, int tiles_x, int tiles_y)
 {
     constexpr int TBX = 32, TBY = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PlaneSmem<S, TBX, TBY> &s = *reinterpret_cast<PlaneSmem<S, TBX, TBY> *>(smem_raw);
-    const int grp = blockIdx.y;
-    const int tile = blockIdx.x;
-    const int tile_x = tile % tiles_x;
-    const int tile_y = (tile / tiles_x) % tiles_y;
-    const int zc = tile / (tiles_x * tiles_y);
-    const int z0 = zc * TZC;
-    double inbox, outflow;
-    transport_tile<S, FLUX, TBX, TBY>(s, g, c, dtdx, N0all + (long long)grp * g.stride,
-                                      F0all + 3LL * grp * g.stride, N1all + (long long)grp * g.stride,
-                                      F1all + 3LL * grp * g.stride, tab, inflow ? inflow + 24 * grp : nullptr,
-                                      tile_x * TBX, tile_y * TBY, z0, min(z0 + TZC, g.nz), inbox, outflow);
-    block_reduce2<TBX * TBY>(&s.red[0][0], inbox, outflow);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        part_inbox[(long long)grp * nblk + tile] = inbox;
-        part_out[(long long)grp * nblk + tile] = outflow * area_dt;
+    const long long tiles = (long long)tiles_x * tiles_y;
+    const long long units = tiles * G * g.nz;
+    const long long u1 = units * (blockIdx.x + 1) / gridDim.x;
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    // the range visits the groups in increasing order: the sums of the
+    // current one are kept, written when the group changes (every group's
+    // slot is zeroed first)
+    if (lead)
+        for (int k = 0; k < G; ++k) part_inbox[(long long)k * gridDim.x + blockIdx.x] = part_out[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+    int cur = -1;
+    double acc_in = 0.0, acc_out = 0.0;
+    for (long long u = units * blockIdx.x / gridDim.x; u < u1;) {
+        const long long col = u / g.nz;
+        const int z0 = (int)(u - col * g.nz);
+        const int z1 = (int)min((long long)g.nz, z0 + (u1 - u));
+        const int grp = (int)(col / tiles);
+        const int tile = (int)(col - grp * tiles);
+        double inbox, outflow;
+        transport_segment<S, FLUX, TBX, TBY>(s, g, c, dtdx, N0all + (long long)grp * g.stride,
+                                             F0all + 3LL * grp * g.stride, N1all + (long long)grp * g.stride,
+                                             F1all + 3LL * grp * g.stride, tab, inflow ? inflow + 24 * grp : nullptr,
+                                             (tile % tiles_x) * TBX, (tile / tiles_x) * TBY, z0, z1, inbox, outflow);
+        block_reduce2<TBX * TBY>(&s.red[0][0], inbox, outflow);
+        if (lead) {
+            if (grp != cur && cur >= 0) {
+                part_inbox[(long long)cur * gridDim.x + blockIdx.x] = acc_in;
+                part_out[(long long)cur * gridDim.x + blockIdx.x] = acc_out * area_dt;
+                acc_in = acc_out = 0.0;
+            }
+            cur = grp;
+            acc_in += inbox;
+            acc_out += outflow;
+        }
+        __syncthreads();
+        u += z1 - z0;
+    }
+    if (lead && cur >= 0) {
+        part_inbox[(long long)cur * gridDim.x + blockIdx.x] = acc_in;
+        part_out[(long long)cur * gridDim.x + blockIdx.x] = acc_out * area_dt;
     }
 }
 
@@ -472,25 +539,24 @@ __device__ __forceinline__ void transport_kernel_body(GridDev g, S c, S dtdx, do
 // table-lookup latencies (the FP32 kernel is latency-bound).
 template <typename S, int FLUX>
 __global__ void __launch_bounds__(256, 2)
-transport_kernel(GridDev g, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
+transport_kernel(GridDev g, int G, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
                  const S *__restrict__ F0all, S *__restrict__ N1all, S *__restrict__ F1all,
                  const S *__restrict__ tab, const S *__restrict__ inflow, double *__restrict__ part_inbox,
-                 double *__restrict__ part_out, int tiles_x, int tiles_y, int nblk)
+                 double *__restrict__ part_out, int tiles_x, int tiles_y)
 {
-    transport_kernel_body<S, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, inflow, part_inbox,
-                                   part_out, tiles_x, tiles_y, nblk);
+    transport_kernel_body<S, FLUX>(g, G, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, inflow, part_inbox,
+                                   part_out, tiles_x, tiles_y);
 }
 
 template <int FLUX>
 __global__ void __launch_bounds__(256, 3)
-transport_kernel_f32(GridDev g, float c, float dtdx, double area_dt, const float *__restrict__ N0all,
+transport_kernel_f32(GridDev g, int G, float c, float dtdx, double area_dt, const float *__restrict__ N0all,
                      const float *__restrict__ F0all, float *__restrict__ N1all, float *__restrict__ F1all,
                      const float *__restrict__ tab, const float *__restrict__ inflow,
-                     double *__restrict__ part_inbox, double *__restrict__ part_out, int tiles_x, int tiles_y,
-                     int nblk)
+                     double *__restrict__ part_inbox, double *__restrict__ part_out, int tiles_x, int tiles_y)
 {
-    transport_kernel_body<float, FLUX>(g, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, inflow, part_inbox,
-                                       part_out, tiles_x, tiles_y, nblk);
+    transport_kernel_body<float, FLUX>(g, G, c, dtdx, area_dt, N0all, F0all, N1all, F1all, tab, inflow,
+                                       part_inbox, part_out, tiles_x, tiles_y);
 }
 
 // Batched boxes: CTA i works on item i (box, group, tile, z range) of a
@@ -523,12 +589,9 @@ transport_batch_kernel(const BatchItem *__restrict__ items, const BatchBox *__re
 
 }  // namespace
 
-int transport_blocks_per_group(const GridDev &g)
+int transport_grid(int n_sm, bool fp32)
 {
-    int tx = (g.nx + 31) / 32;
-    int ty = (g.ny + 7) / 8;
-    int tz = (g.nz + TZC - 1) / TZC;
-    return tx * ty * tz;
+    return (fp32 ? 3 : 2) * (n_sm > 0 ? n_sm : 1);
 }
 
 template <typename S, int TBX, int TBY>
@@ -556,28 +619,26 @@ template <typename S>
 static cudaError_t launch_t(const GridDev &g, int G, int flux, double cr, double dt, const S *N0, const S *F0,
                             S *N1, S *F1, const S *tab, const S *inflow, const Partials &p, cudaStream_t st)
 {
-    int tiles_x = (g.nx + 31) / 32;
-    int tiles_y = (g.ny + 7) / 8;
-    int nblk = transport_blocks_per_group(g);
-    dim3 grid(nblk, G);
-    dim3 block(32, 8);
-    size_t smem = sizeof(PlaneSmem<S, 32, 8>);
-    S dtdx = (S)(dt / g.dx);
-    double area_dt = g.dx * g.dx * dt;
+    const int tiles_x = (g.nx + 31) / 32;
+    const int tiles_y = (g.ny + 7) / 8;
+    const dim3 grid(p.n_tr_blocks), block(32, 8);
+    const size_t smem = sizeof(PlaneSmem<S, 32, 8>);
+    const S dtdx = (S)(dt / g.dx);
+    const double area_dt = g.dx * g.dx * dt;
     if constexpr (sizeof(S) == sizeof(float)) {
         if (flux == RT_HLL)
-            transport_kernel_f32<RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
-                                                                    p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+            transport_kernel_f32<RT_HLL><<<grid, block, smem, st>>>(g, G, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                    inflow, p.tr_inbox, p.tr_outflow, tiles_x, tiles_y);
         else
-            transport_kernel_f32<RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
-                                                                    p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+            transport_kernel_f32<RT_GLF><<<grid, block, smem, st>>>(g, G, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                    inflow, p.tr_inbox, p.tr_outflow, tiles_x, tiles_y);
     } else {
         if (flux == RT_HLL)
-            transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
-                                                                   p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+            transport_kernel<S, RT_HLL><<<grid, block, smem, st>>>(g, G, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                   inflow, p.tr_inbox, p.tr_outflow, tiles_x, tiles_y);
         else
-            transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab, inflow,
-                                                                   p.tr_inbox, p.tr_outflow, tiles_x, tiles_y, nblk);
+            transport_kernel<S, RT_GLF><<<grid, block, smem, st>>>(g, G, (S)cr, dtdx, area_dt, N0, F0, N1, F1, tab,
+                                                                   inflow, p.tr_inbox, p.tr_outflow, tiles_x, tiles_y);
     }
     return cudaGetLastError();
 }
