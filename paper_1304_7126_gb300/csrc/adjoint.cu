@@ -101,10 +101,10 @@ thermo_vjp_kernel(ThermoParams p, const double *__restrict__ nH, const double *_
     cc.valid = false;
     cc.rvalid = false;
     if (p.isothermal) {
-        TranscT<Dual> t;
-        transc_dual(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
-        h_rates_from(t, p.case_b, iso.h);
-        if (p.helium) he_rates_from(t, p.case_b, iso.he);
+        RatesT<Dual> t;
+        rates_dual(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), kNeedH, t);
+        h_rates_from(t, iso.h);
+        if (p.helium) he_rates_from(t, iso.he);
     }
     double t_left = p.dt, dt_tc = p.dt;
     int att = 0;

@@ -4,20 +4,14 @@
 // 1992; bremsstrahlung; Compton: Haiman et al. 1996; dielectronic: Black
 // 1981), each with its analytic temperature derivative, in FP64.
 //
-// Evaluation is split in two stages so that the same arithmetic can be done
-// by one thread or spread over the lanes of a warp:
-//   1. transcendentals of one temperature (struct Transc; exp, log, log1p,
-//      square root and reciprocal in the double-float arithmetic of
-//      dfmath.cuh, on the FP32 pipe): ln T, sqrt T,
-//      1/T, and twelve exponentials exp(a ln T + b/T + c) - the Boltzmann
-//      factors exp(-T0/T), the power laws, and w = (lam/l0)^r of the four
-//      Hui & Gnedin fits A lam^p / (1 + w)^s - then log1p(w) and
-//      exp(p ln lam - s log1p(w)) of those four fits;
-//   2. assembly of the rates and derivatives from Transc (plain arithmetic).
-// transc_serial computes stage 1 in one thread; transc_warp lets lane k of a
-// warp evaluate exponential k, so a warp pays for three exponential levels
-// instead of twenty transcendental calls.  Both use identical expressions,
-// so they give identical bits.
+// Every rate coefficient and every cooling term is one function of T of
+// the form
+//     f(T) = Cc exp(c0 + c1 ln T + c2 / T - c3 softplus(c4 ln T + c5)),
+// softplus(z) = ln(1 + e^z) (see RateFn below).  A warp evaluates them all
+// at once, lane k function k; one thread evaluates the ones it needs.  The
+// argument is formed in the double-float arithmetic of dfmath.cuh (on the
+// FP32 pipe), exponentiated by dfm::exp2d and scaled by Cc in FP64; both
+// paths run the same expressions and so give identical bits.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -85,155 +79,17 @@ using Transc = TranscT<double>;
         {{2.753e-14, 12.662275226919286, 1.5, 0.407, 2.242}, {5.506e-14, 14.049024154019651, 1.5, 0.407, 2.242}, {3.435e-30, 12.662275226919286, 1.97, 0.376, 3.72}, {2.748e-29, 14.049024154019651, 1.97, 0.376, 3.72}},\
         1.26e-14, 0.75 }\
 }
-// uniform reads (an index the same in every lane): the constant cache
-static __constant__ RateTable c_rate_tab[2] = RTGB_RATE_TAB_INIT;
-// lane-indexed reads (lane k evaluates term k): global memory through the
-// L1 cache, which serves different addresses of a warp in one request where
-// the constant cache would serialise them
-static __device__ const RateTable g_rate_tab[2] = RTGB_RATE_TAB_INIT;
-// compile-time copy, for the derived constants of the cooling terms
+// compile-time copy, from which the rate functions below are built
 constexpr RateTable kRateTabCx[2] = RTGB_RATE_TAB_INIT;
 #undef RTGB_RATE_TAB_INIT
 
 // The table's constants as float pairs (hi = the double rounded to a float,
-// lo = the rest rounded), made at compile time: a ln T + b/T + c and
-// p (ln T1 - ln T) - s l in pair arithmetic without splitting doubles at
-// run time.
-struct RateTableF2 {
-    dfm::F2 ea[NEXP][3];   // a, b, c
-    dfm::F2 hg[NHG][3];    // ln T1, p, s
-};
+// lo = the rest rounded), made at compile time.
 constexpr dfm::F2 pair_of(double x)
 {
     return dfm::F2{(float)x, (float)(x - (double)(float)x)};
 }
-constexpr RateTableF2 make_rate_f2(int cb)
-{
-    RateTableF2 t{};
-    const RateTable &R = kRateTabCx[cb];
-    for (int k = 0; k < NEXP; ++k) {
-        t.ea[k][0] = pair_of(R.ea[k].a);
-        t.ea[k][1] = pair_of(R.ea[k].b);
-        t.ea[k][2] = pair_of(R.ea[k].c);
-    }
-    for (int j = 0; j < NHG; ++j) {
-        t.hg[j][0] = pair_of(R.hg[j].lnT1);
-        t.hg[j][1] = pair_of(R.hg[j].p);
-        t.hg[j][2] = pair_of(R.hg[j].s);
-    }
-    return t;
-}
-static __device__ const RateTableF2 g_rate_f2[2] = {make_rate_f2(0), make_rate_f2(1)};
 
-__device__ __forceinline__ dfm::F2 ldg2(const dfm::F2 &v)
-{
-    const float2 f = __ldg(reinterpret_cast<const float2 *>(&v));
-    return dfm::F2{f.x, f.y};
-}
-
-// a ln T + b / T + c of table entry k
-__device__ __forceinline__ dfm::F2 exp_arg2(const RateTableF2 &R, int k, dfm::F2 lnT, dfm::F2 invT)
-{
-    using namespace dfm;
-    return add(add(ldg2(R.ea[k][2]), mul(lnT, ldg2(R.ea[k][0]))), mul(invT, ldg2(R.ea[k][1])));
-}
-
-// p (ln T1 - ln T) - s l of Hui & Gnedin fit j
-__device__ __forceinline__ dfm::F2 hg_arg2(const RateTableF2 &R, int j, dfm::F2 lnT, dfm::F2 l)
-{
-    using namespace dfm;
-    return add(mul(add(ldg2(R.hg[j][0]), neg(lnT)), ldg2(R.hg[j][1])), neg(mul(l, ldg2(R.hg[j][2]))));
-}
-
-// Stage 1 in double-float arithmetic (dfmath.cuh): ln T, 1/T, sqrt T and u
-// as float pairs, each exponential's argument formed in pair arithmetic and
-// e^x returned as a double; the Transc values are the doubles of the pairs.
-constexpr double kUc = 0.003162277660168379;   // 1 / sqrt(1e5)
-constexpr float kUcHi = (float)kUc;
-constexpr float kUcLo = (float)(kUc - (double)kUcHi);
-
-__device__ __forceinline__ void transc_level0(double T, Transc &t, dfm::F2 &lnT, dfm::F2 &invT)
-{
-    using namespace dfm;
-    if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^120 K
-        t.lnT = log(T);
-        t.sqrtT = sqrt(T);
-        t.invT = 1.0 / T;
-        t.u = 1.0 / (1.0 + t.sqrtT * kUc);
-        lnT = split_any(t.lnT);
-        invT = split_any(t.invT);
-        return;
-    }
-    const F2 T2 = split(T);
-    lnT = log2f2(T2);
-    invT = rcp(T2);
-    const F2 sq = sqrt2(T2);
-    const F2 u = rcp(add(mul(sq, F2{kUcHi, kUcLo}), 1.0f));
-    t.lnT = to_double(lnT);
-    t.sqrtT = to_double(sq);
-    t.invT = to_double(invT);
-    t.u = to_double(u);
-}
-
-// Stage 1 in one thread.  need: bit k of the exponentials E_*, bit NEXP + j
-// of the Hui & Gnedin fits j.  A Hui & Gnedin fit A lam^p / (1 + w)^s with
-// w = (lam/l0)^r is exp(p ln lam - s softplus(z)), z = r ln(lam/l0): one
-// polynomial for ln(1 + e^z) (dfm::softplus2) instead of an exp and a log1p.
-__device__ __forceinline__ void transc_serial(double T, int case_b, unsigned need, Transc &t)
-{
-    const RateTableF2 &R = g_rate_f2[case_b];
-    dfm::F2 lnT, invT;
-    transc_level0(T, t, lnT, invT);
-#pragma unroll
-    for (int k = 0; k < E_W0; ++k)
-        if (need & (1u << k)) t.e[k] = dfm::exp2d(exp_arg2(R, k, lnT, invT));
-#pragma unroll
-    for (int j = 0; j < NHG; ++j) {
-        if (need & (1u << (NEXP + j))) {
-            double sg;
-            const dfm::F2 l = dfm::softplus2(exp_arg2(R, E_W0 + j, lnT, invT), sg);
-            t.l[j] = dfm::to_double(l);
-            t.s[j] = sg;
-            t.v[j] = dfm::exp2d(hg_arg2(R, j, lnT, l));
-        }
-    }
-}
-
-// Stage 1 spread over a full warp (all 32 lanes must call it with the same
-// T); every lane ends with the complete, identical Transc.  Lanes 0..7
-// take the exponentials, lanes 8..11 the Hui & Gnedin fits, and every lane
-// runs the same instructions (a warp runs divergent paths one after the
-// other): the exponential lanes pass z = 0 through the softplus and ignore
-// it, then all lanes take one exp of their argument.
-__device__ __forceinline__ void transc_warp(double T, int case_b, Transc &t)
-{
-    const RateTableF2 &R = g_rate_f2[case_b];
-    const int lane = threadIdx.x & 31;
-    dfm::F2 lnT, invT;
-    transc_level0(T, t, lnT, invT);
-    const bool fit = lane >= E_W0 && lane < E_W0 + NHG;
-    const int j = (lane - E_W0) & 3;
-    const dfm::F2 arg = exp_arg2(R, lane < E_W0 ? lane : E_W0 + j, lnT, invT);
-    double sj;
-    const dfm::F2 l = dfm::softplus2(fit ? arg : dfm::F2{0.0f, 0.0f}, sj);
-    const dfm::F2 hga = hg_arg2(R, j, lnT, l);
-    const double ek = dfm::exp2d(fit ? hga : arg);
-    const double lj = dfm::to_double(l);
-#pragma unroll
-    for (int q = 0; q < E_W0; ++q) t.e[q] = __shfl_sync(0xffffffffu, ek, q);
-#pragma unroll
-    for (int q = 0; q < NHG; ++q) {
-        t.l[q] = __shfl_sync(0xffffffffu, lj, E_W0 + q);
-        t.s[q] = __shfl_sync(0xffffffffu, sj, E_W0 + q);
-        t.v[q] = __shfl_sync(0xffffffffu, ek, E_W0 + q);
-    }
-}
-
-// FP32 transcendentals (the mixed-precision thermochemistry): the same
-// arguments evaluated in single precision, stored widened into Transc so the
-// assembly below is shared (widened through integer operations: a float ->
-// double conversion would take the FP64 pipe; float subnormals, far below
-// any rate that matters, count as zero).  Relative accuracy ~1e-7.
 // a double rounded to the nearest float (ties away from zero) through
 // integer operations: a double -> float conversion would take the FP64
 // pipe.  Below the normal float range the result is 0, above it infinity
@@ -251,195 +107,6 @@ __device__ __forceinline__ float narrow(double x)
     return __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((a >> 29) & 0x7fffff));
 }
 
-__device__ __forceinline__ void transc_level0_f(double T, Transc &t, float &lnT, float &invT)
-{
-    float Tf = narrow(T);
-    lnT = logf(Tf);
-    float sq = sqrtf(Tf);
-    invT = 1.0f / Tf;
-    t.lnT = dfm::widen(lnT);
-    t.sqrtT = dfm::widen(sq);
-    t.invT = dfm::widen(invT);
-    t.u = dfm::widen(1.0f / (1.0f + sq * 0.0031622776f));
-}
-
-__device__ __forceinline__ float exp_arg_f(const ExpArg &q, float lnT, float invT)
-{
-    return fmaf(narrow(q.a), lnT, fmaf(narrow(q.b), invT, narrow(q.c)));
-}
-
-__device__ __forceinline__ float hg_arg_f(const HGPar &h, float lnT, float l)
-{
-    return narrow(h.p) * (narrow(h.lnT1) - lnT) - narrow(h.s) * l;
-}
-
-__device__ __forceinline__ void transc_serial_f(double T, int case_b, unsigned need, Transc &t)
-{
-    const RateTable &R = c_rate_tab[case_b];
-    float lnT, invT;
-    transc_level0_f(T, t, lnT, invT);
-#pragma unroll
-    for (int k = 0; k < E_W0; ++k)
-        if (need & (1u << k)) t.e[k] = dfm::widen(expf(exp_arg_f(R.ea[k], lnT, invT)));
-#pragma unroll
-    for (int j = 0; j < NHG; ++j) {
-        if (need & (1u << (NEXP + j))) {
-            const float w = expf(exp_arg_f(R.ea[E_W0 + j], lnT, invT));
-            const float l = log1pf(w);
-            t.l[j] = dfm::widen(l);
-            t.s[j] = dfm::widen(w / (1.0f + w));
-            t.v[j] = dfm::widen(expf(hg_arg_f(R.hg[j], lnT, l)));
-        }
-    }
-}
-
-__device__ __forceinline__ void transc_warp_f(double T, int case_b, Transc &t)
-{
-    const RateTable &R = g_rate_tab[case_b];
-    const int lane = threadIdx.x & 31;
-    float lnT, invT;
-    transc_level0_f(T, t, lnT, invT);
-    float ek, lj = 0.0f, sj = 0.0f;
-    if (lane < E_W0) {
-        ek = expf(exp_arg_f(R.ea[lane], lnT, invT));
-    } else {
-        const int j = (lane - E_W0) & 3;
-        const float w = expf(exp_arg_f(R.ea[E_W0 + j], lnT, invT));
-        lj = log1pf(w);
-        sj = w / (1.0f + w);
-        ek = expf(hg_arg_f(R.hg[j], lnT, lj));
-    }
-#pragma unroll
-    for (int q = 0; q < E_W0; ++q) t.e[q] = dfm::widen(__shfl_sync(0xffffffffu, ek, q));
-#pragma unroll
-    for (int q = 0; q < NHG; ++q) {
-        t.l[q] = dfm::widen(__shfl_sync(0xffffffffu, lj, E_W0 + q));
-        t.s[q] = dfm::widen(__shfl_sync(0xffffffffu, sj, E_W0 + q));
-        t.v[q] = dfm::widen(__shfl_sync(0xffffffffu, ek, E_W0 + q));
-    }
-}
-
-// Stage 1 for a dual temperature: values from transc_serial (so they are
-// the bits of the double path), derivatives by the chain rule:
-// d lnT = dT/T, d sqrtT = sqrtT dT/(2T), d(1/T) = -dT/T^2, du = -u^2 k d sqrtT,
-// d exp(a lnT + b/T + c) = e (a d lnT + b d(1/T)), d softplus(z) = sigma dz,
-// d exp(p (lnT1 - lnT) - s l) = v (-p d lnT - s dl).
-__device__ __forceinline__ void transc_dual(const Dual &T, int case_b, unsigned need, TranscT<Dual> &t)
-{
-    const RateTable &R = c_rate_tab[case_b];
-    Transc p;
-    transc_serial(T.v, case_b, need, p);
-    const double dT = T.d;
-    const double dln = p.invT * dT, dinv = -p.invT * p.invT * dT;
-    const double dsq = 0.5 * p.sqrtT * p.invT * dT;
-    t.lnT = Dual(p.lnT, dln);
-    t.sqrtT = Dual(p.sqrtT, dsq);
-    t.invT = Dual(p.invT, dinv);
-    t.u = Dual(p.u, -p.u * p.u * 0.003162277660168379 * dsq);
-#pragma unroll
-    for (int k = 0; k < E_W0; ++k)
-        if (need & (1u << k)) t.e[k] = Dual(p.e[k], p.e[k] * (R.ea[k].a * dln + R.ea[k].b * dinv));
-#pragma unroll
-    for (int j = 0; j < NHG; ++j) {
-        if (need & (1u << (NEXP + j))) {
-            // z = a lnT + b/T + c; d softplus(z) = sigma dz, d sigma = sigma (1 - sigma) dz
-            const double dz = R.ea[E_W0 + j].a * dln + R.ea[E_W0 + j].b * dinv;
-            const double sg = p.s[j];
-            const double dl = sg * dz;
-            t.l[j] = Dual(p.l[j], dl);
-            t.s[j] = Dual(sg, sg * (1.0 - sg) * dz);
-            t.v[j] = Dual(p.v[j], p.v[j] * (-R.hg[j].p * dln - R.hg[j].s * dl));
-        }
-    }
-}
-
-// d ln v / dT of a Hui & Gnedin fit: -(1/T) (p - s r w / (1 + w))
-template <typename S>
-__device__ __forceinline__ S hg_dlog(const HGPar &h, const TranscT<S> &t, int j)
-{
-    return -t.invT * (h.p - h.s * h.r * t.s[j]);
-}
-
-// bits of Transc needed by each consumer
-constexpr unsigned kNeedH = (1u << E_BETA_HI) | (1u << E_W0) | (1u << (NEXP + HG_ALPHA_HII));
-constexpr unsigned kNeedHe = (1u << E_BETA_HEI) | (1u << E_BETA_HEII) | (1u << E_ALPHA_HEII) |
-                             (1u << (E_W0 + HG_ALPHA_HEIII)) | (1u << (NEXP + HG_ALPHA_HEIII));
-constexpr unsigned kNeedHe3 = (1u << E_BETA_HEII) | (1u << (E_W0 + HG_ALPHA_HEIII)) |
-                              (1u << (NEXP + HG_ALPHA_HEIII));
-constexpr unsigned kNeedCoolH = (1u << E_BETA_HI) | (1u << E_PSI_HI) | (1u << (E_W0 + HG_ETA_HII)) |
-                                (1u << (NEXP + HG_ETA_HII));
-// the three recombination rates alpha_HII, alpha_HeII, alpha_HeIII
-constexpr unsigned kNeedRec = (1u << E_ALPHA_HEII) | (1u << (E_W0 + HG_ALPHA_HII)) |
-                              (1u << (E_W0 + HG_ALPHA_HEIII)) | (1u << (NEXP + HG_ALPHA_HII)) |
-                              (1u << (NEXP + HG_ALPHA_HEIII));
-constexpr unsigned kNeedCoolHe = (1u << E_BETA_HEI) | (1u << E_BETA_HEII) | (1u << E_PSI_HEII) |
-                                 (1u << E_OMEGA1) | (1u << E_OMEGA2) | (1u << E_ALPHA_HEII) |
-                                 (1u << (E_W0 + HG_ETA_HEIII)) | (1u << (NEXP + HG_ETA_HEIII));
-
-template <typename S>
-struct HRatesT {      // rates needed by the x_HII update
-    S beta, dbeta, alpha, dalpha;
-};
-template <typename S>
-struct HeRatesT {
-    S beta_HeI, beta_HeII, alpha_HeII, alpha_HeIII;
-};
-using HRates = HRatesT<double>;
-using HeRates = HeRatesT<double>;
-
-// Cen (1992) form A sqrt(T) u exp(-T0/T)
-template <typename S>
-__device__ __forceinline__ void cen_fit(double A, double T0, const S &e, const TranscT<S> &t, S &v, S &dv)
-{
-    v = A * t.sqrtT * t.u * e;
-    dv = v * (0.5 * t.u * t.invT + T0 * t.invT * t.invT);
-}
-
-template <typename S>
-__device__ __forceinline__ void h_rates_from(const TranscT<S> &t, int case_b, HRatesT<S> &r)
-{
-    const RateTable &R = c_rate_tab[case_b];
-    cen_fit(5.85e-11, 157809.1, t.e[E_BETA_HI], t, r.beta, r.dbeta);
-    r.alpha = R.hg[HG_ALPHA_HII].A * t.v[HG_ALPHA_HII];
-    r.dalpha = r.alpha * hg_dlog(R.hg[HG_ALPHA_HII], t, HG_ALPHA_HII);
-}
-
-template <typename S>
-__device__ __forceinline__ void he_rates_from(const TranscT<S> &t, int case_b, HeRatesT<S> &r)
-{
-    const RateTable &R = c_rate_tab[case_b];
-    S d;
-    cen_fit(2.38e-11, 285335.4, t.e[E_BETA_HEI], t, r.beta_HeI, d);
-    cen_fit(5.68e-12, 631515.0, t.e[E_BETA_HEII], t, r.beta_HeII, d);
-    r.alpha_HeII = R.A_aHeII * t.e[E_ALPHA_HEII];
-    r.alpha_HeIII = R.hg[HG_ALPHA_HEIII].A * t.v[HG_ALPHA_HEIII];
-}
-
-// Recombination rates of HII, HeII, HeIII (the case of the table t was
-// evaluated with)
-template <typename S>
-__device__ __forceinline__ void recomb_alphas(const TranscT<S> &t, int case_b, S a[3])
-{
-    const RateTable &R = c_rate_tab[case_b];
-    a[0] = R.hg[HG_ALPHA_HII].A * t.v[HG_ALPHA_HII];
-    a[1] = R.A_aHeII * t.e[E_ALPHA_HEII];
-    a[2] = R.hg[HG_ALPHA_HEIII].A * t.v[HG_ALPHA_HEIII];
-}
-
-// Primordial cooling magnitude L (Eq. (rate_cooling), positive = cooling)
-// and dL/dT, as a sum of terms of one form,
-//     C n_s sqrt(T)^a u^b T^c X1 X2 A,
-// X1 an exponential e[i1] of the Transc (or the Hui & Gnedin value v[hg]),
-// X2 an optional second exponential, A the fit's amplitude where the rate
-// table holds it (it depends on the recombination case), n_s a density;
-// each term's T-derivative is the term times its log-derivative
-//     a/(2T) - b (1 - u)/(2T) + c/T + dln X1/dT + dln X2/dT,
-// dln e/dT = a_e/T - b_e/T^2 from the exponential's argument, and the Hui &
-// Gnedin log-derivative.  The terms (collisional ionisation and excitation,
-// recombination and dielectronic cooling, bremsstrahlung) are summed in a
-// fixed pairwise order; Compton cooling is added after.  All products and
-// sums are rounded as written (rmul, radd), so the one-thread sum and the
-// warp sum (lane k evaluates term k) give the same bits.
 enum { SP_HI = 0, SP_HII, SP_HEI, SP_HEII, SP_HEIII, SP_FF, NSP };   // SP_FF: n_HII + n_HeII + 4 n_HeIII
 
 struct CoolTerm {
@@ -474,11 +141,345 @@ __host__ __device__ __forceinline__ constexpr CoolTerm cool_row(int k)
     constexpr CoolTerm rows[kNCool] = {RTGB_COOL_TERMS(RTGB_COOL_ROW)};
     return rows[k];
 }
-// the same rows in device memory, indexed by lane (the warp sum)
-static __device__ const CoolTerm kCoolTermsDev[kNCool] = {RTGB_COOL_TERMS(RTGB_COOL_ROW)};
 #undef RTGB_COOL_ROW
 #undef RTGB_COOL_TERMS
 
+// ---- rate functions ----
+//   Cen (1992) collisional rates A sqrt(T) u exp(-T0/T), u = 1/(1 + sqrt(T/1e5)):
+//     Cc = A, c1 = 1/2, c2 = -T0, c3 = 1, z = (ln T - ln 1e5)/2, since
+//     ln u = -softplus(z);
+//   Hui & Gnedin (1997) fits A lam^p / (1 + (lam/l0)^r)^s, lam = T1/T:
+//     Cc = A, c0 = p ln T1, c1 = -p, c3 = s, z = r ln(lam/l0) (the table's
+//     argument E_W0 + j: a = -r, c = r (ln T1 - ln l0));
+//   alpha_HeII = A (570670/T)^p and the Boltzmann factors: c3 = 0;
+//   a cooling term C n_s sqrt(T)^sq u^uu T^tt X1 X2 v^hg adds the exponents
+//     of its factors (no term has both u and a Hui & Gnedin factor) and
+//     times its density n_s after the function.
+// d ln f/dT = (c1 - c2/T - c3 c4 sigma(z)) / T, sigma = e^z / (1 + e^z).
+enum {
+    RF_COOL0 = 0,                 // slots 0..10: the cooling terms; 11..15 zero
+    RF_BETA_HI = 16, RF_ALPHA_HII, RF_BETA_HEI, RF_BETA_HEII, RF_ALPHA_HEII, RF_ALPHA_HEIII,
+    NRF
+};
+static_assert(kNCool <= 16 && NRF <= 32, "function slots are warp lanes");
+
+struct RateFn {
+    double Cc;
+    dfm::F2 c0, c1, c2, c3, c4, c5;
+    double d1, d2, d34, d344;   // c1, c2, c3 c4, c3 c4^2 (log-derivative and its derivative)
+    float g34;                  // c3 c4 as a float (FP32 path)
+};
+struct RateFnTab {
+    RateFn f[32];
+};
+
+constexpr double kHalfLn1e5 = 5.756462732485114;   // ln(1e5) / 2
+
+constexpr RateFn rate_fn(double Cc, double c0, double c1, double c2, double c3, double c4, double c5)
+{
+    return RateFn{Cc, pair_of(c0), pair_of(c1), pair_of(c2), pair_of(c3), pair_of(c4), pair_of(c5),
+                  c1, c2, c3 * c4, c3 * c4 * c4, (float)(c3 * c4)};
+}
+constexpr RateFn cen_fn(double A, double T0) { return rate_fn(A, 0.0, 0.5, -T0, 1.0, 0.5, -kHalfLn1e5); }
+constexpr RateFn hg_fn(const RateTable &R, int j)
+{
+    return rate_fn(R.hg[j].A, R.hg[j].p * R.hg[j].lnT1, -R.hg[j].p, 0.0, R.hg[j].s, R.ea[E_W0 + j].a,
+                   R.ea[E_W0 + j].c);
+}
+constexpr RateFn cool_fn(const RateTable &R, const CoolTerm &q)
+{
+    double Cc = q.C, c0 = 0.0, c1 = 0.5 * q.sq + q.tt, c2 = 0.0, c3 = 0.0, c4 = 0.0, c5 = 0.0;
+    if (q.e1 >= 0) { c0 += R.ea[q.e1].c; c1 += R.ea[q.e1].a; c2 += R.ea[q.e1].b; }
+    if (q.e2 >= 0) { c0 += R.ea[q.e2].c; c1 += R.ea[q.e2].a; c2 += R.ea[q.e2].b; }
+    if (q.hg >= 0) {
+        Cc *= R.hg[q.hg].A;
+        c0 += R.hg[q.hg].p * R.hg[q.hg].lnT1;
+        c1 -= R.hg[q.hg].p;
+        c3 = R.hg[q.hg].s;
+        c4 = R.ea[E_W0 + q.hg].a;
+        c5 = R.ea[E_W0 + q.hg].c;
+    }
+    if (q.uu) { c3 = 1.0; c4 = 0.5; c5 = -kHalfLn1e5; }
+    if (q.amp) Cc *= R.A_aHeII;
+    return rate_fn(Cc, c0, c1, c2, c3, c4, c5);
+}
+constexpr RateFnTab make_rate_fns(int cb)
+{
+    RateFnTab t{};
+    const RateTable &R = kRateTabCx[cb];
+    for (int k = 0; k < kNCool; ++k) t.f[RF_COOL0 + k] = cool_fn(R, cool_row(k));
+    for (int k = kNCool; k < 16; ++k) t.f[k] = rate_fn(0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0);
+    t.f[RF_BETA_HI] = cen_fn(5.85e-11, 157809.1);
+    t.f[RF_ALPHA_HII] = hg_fn(R, HG_ALPHA_HII);
+    t.f[RF_BETA_HEI] = cen_fn(2.38e-11, 285335.4);
+    t.f[RF_BETA_HEII] = cen_fn(5.68e-12, 631515.0);
+    t.f[RF_ALPHA_HEII] = rate_fn(R.A_aHeII, R.ea[E_ALPHA_HEII].c, R.ea[E_ALPHA_HEII].a, R.ea[E_ALPHA_HEII].b, 0.0,
+                                 0.0, 0.0);
+    t.f[RF_ALPHA_HEIII] = hg_fn(R, HG_ALPHA_HEIII);
+    for (int k = NRF; k < 32; ++k) t.f[k] = rate_fn(0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0);
+    return t;
+}
+// uniform reads (one thread, a compile-time slot): the constant cache;
+// lane-indexed reads (a warp): global memory through the L1 cache, which
+// serves different addresses of a warp in one request
+static __constant__ RateFnTab c_rate_fn[2] = {make_rate_fns(0), make_rate_fns(1)};
+static __device__ const RateFnTab g_rate_fn[2] = {make_rate_fns(0), make_rate_fns(1)};
+
+// density factor and helium flag of each cooling slot
+static __device__ const int g_cool_sp[16] = {SP_HI, SP_HI, SP_HII, SP_FF, SP_HEI, SP_HEII, SP_HEII, SP_HEII,
+                                             SP_HEII, SP_HEII, SP_HEIII, 0, 0, 0, 0, 0};
+
+// ln T and 1/T of one temperature as pairs, 1/T as a double
+struct TLevel {
+    dfm::F2 lnT, invT;
+    double invTd;
+};
+__device__ __forceinline__ void t_level(double T, TLevel &L)
+{
+    using namespace dfm;
+    if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^60 K
+        L.invTd = 1.0 / T;
+        L.lnT = split_any(log(T));
+        L.invT = split_any(L.invTd);
+        return;
+    }
+    const F2 T2 = split(T);
+    L.lnT = log2f2(T2);
+    L.invT = rcp(T2);
+    L.invTd = to_double(L.invT);
+}
+
+// f(T) of one function given l = softplus(z); all FP64 products rounded as
+// written
+__device__ __forceinline__ double rate_from_l(const RateFn &q, const TLevel &L, dfm::F2 l)
+{
+    using namespace dfm;
+    const F2 arg = add(add(add(q.c0, mul(L.lnT, q.c1)), mul(L.invT, q.c2)), neg(mul(l, q.c3)));
+    return rmul(q.Cc, exp2d(arg));
+}
+__device__ __forceinline__ dfm::F2 rate_softplus(const RateFn &q, const TLevel &L, double &sig)
+{
+    using namespace dfm;
+    return softplus2(add(mul(L.lnT, q.c4), q.c5), sig);
+}
+// f(T) of one function and sigma(z)
+__device__ __forceinline__ double rate_value(const RateFn &q, const TLevel &L, double &sig)
+{
+    return rate_from_l(q, L, rate_softplus(q, L, sig));
+}
+// df/dT = f (c1 - c2/T - c3 c4 sigma) / T
+__device__ __forceinline__ double rate_deriv(const RateFn &q, double invT, double f, double sig)
+{
+    return rmul(f, rmul(rfma(-q.d34, sig, rfma(-q.d2, invT, q.d1)), invT));
+}
+
+// FP32 (the mixed-precision thermochemistry, RT_MIXED32): the same form in
+// single precision (the pairs' high parts), widened through integer
+// operations and scaled by Cc in FP64; relative accuracy ~1e-6.
+__device__ __forceinline__ void rate_value_f(const RateFn &q, float lnT, float invT, double &f, double &df)
+{
+    const float z = __fmaf_rn(q.c4.hi, lnT, q.c5.hi);
+    const float e = __expf(-fabsf(z));
+    const float l = fmaxf(z, 0.0f) + log1pf(e);
+    const float sg = (z >= 0.0f ? 1.0f : e) / (1.0f + e);
+    const float arg = __fmaf_rn(-q.c3.hi, l, __fmaf_rn(q.c2.hi, invT, __fmaf_rn(q.c1.hi, lnT, q.c0.hi)));
+    f = rmul(q.Cc, dfm::widen(expf(arg)));
+    const float g = __fmul_rn(__fmaf_rn(-q.g34, sg, __fmaf_rn(-q.c2.hi, invT, q.c1.hi)), invT);
+    df = rmul(f, dfm::widen(g));
+}
+__device__ __forceinline__ void t_level_f(double T, float &lnT, float &invT)
+{
+    const float Tf = narrow(T);
+    lnT = logf(Tf);
+    invT = 1.0f / Tf;
+}
+
+// values (and derivatives) of several functions at one temperature
+template <typename S>
+struct RatesT {
+    S f[NRF], df[NRF];
+};
+using Rates = RatesT<double>;
+
+__host__ __device__ constexpr unsigned rf_bit(int k) { return 1u << k; }
+constexpr unsigned kNeedH = rf_bit(RF_BETA_HI) | rf_bit(RF_ALPHA_HII);   // values and derivatives
+constexpr unsigned kNeedHe = rf_bit(RF_BETA_HEI) | rf_bit(RF_BETA_HEII) | rf_bit(RF_ALPHA_HEII) |
+                             rf_bit(RF_ALPHA_HEIII);
+constexpr unsigned kNeedHe3 = rf_bit(RF_BETA_HEII) | rf_bit(RF_ALPHA_HEIII);
+constexpr unsigned kNeedRec = rf_bit(RF_ALPHA_HII) | rf_bit(RF_ALPHA_HEII) | rf_bit(RF_ALPHA_HEIII);
+__host__ __device__ constexpr unsigned cool_mask(int he)
+{
+    unsigned m = 0;
+    for (int k = 0; k < kNCool; ++k)
+        if (cool_row(k).he == he) m |= rf_bit(RF_COOL0 + k);
+    return m;
+}
+constexpr unsigned kNeedCoolH = cool_mask(0), kNeedCoolHe = cool_mask(1);
+
+// slots whose softplus is that of u (z = (ln T - ln 1e5)/2, the same in
+// all of them) and slots without a softplus (c3 = 0: l and sigma enter
+// multiplied by zero, exactly)
+__host__ __device__ constexpr unsigned rf_u_mask()
+{
+    unsigned m = rf_bit(RF_BETA_HI) | rf_bit(RF_BETA_HEI) | rf_bit(RF_BETA_HEII);
+    for (int k = 0; k < kNCool; ++k)
+        if (cool_row(k).uu) m |= rf_bit(RF_COOL0 + k);
+    return m;
+}
+__host__ __device__ constexpr unsigned rf_plain_mask()
+{
+    unsigned m = rf_bit(RF_ALPHA_HEII);
+    for (int k = 0; k < 16; ++k)
+        if (k >= kNCool || (!cool_row(k).uu && cool_row(k).hg < 0)) m |= rf_bit(RF_COOL0 + k);
+    return m;
+}
+
+// one thread: the functions in needF (derivatives of those in needD); the
+// shared softplus of u once, none where it is multiplied by zero (the same
+// bits as the warp, which evaluates every slot's own)
+__device__ __forceinline__ void rates_serial(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
+{
+    constexpr unsigned kU = rf_u_mask(), kPlain = rf_plain_mask();
+    TLevel L;
+    t_level(T, L);
+    const RateFnTab &R = c_rate_fn[case_b];
+    double sgu = 0.0;
+    dfm::F2 lu{0.0f, 0.0f};
+    if (needF & kU) lu = rate_softplus(R.f[RF_BETA_HI], L, sgu);
+#pragma unroll
+    for (int k = 0; k < NRF; ++k) {
+        if (needF & rf_bit(k)) {
+            double sg = 0.0;
+            if (kU & rf_bit(k)) {
+                sg = sgu;
+                r.f[k] = rate_from_l(R.f[k], L, lu);
+            } else if (kPlain & rf_bit(k)) {
+                r.f[k] = rate_from_l(R.f[k], L, dfm::F2{0.0f, 0.0f});
+            } else {
+                r.f[k] = rate_value(R.f[k], L, sg);
+            }
+            if (needD & rf_bit(k)) r.df[k] = rate_deriv(R.f[k], L.invTd, r.f[k], sg);
+        }
+    }
+}
+__device__ __forceinline__ void rates_serial_f(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
+{
+    float lnT, invT;
+    t_level_f(T, lnT, invT);
+    const RateFnTab &R = c_rate_fn[case_b];
+#pragma unroll
+    for (int k = 0; k < NRF; ++k) {
+        if (needF & rf_bit(k)) {
+            double df;
+            rate_value_f(R.f[k], lnT, invT, r.f[k], df);
+            if (needD & rf_bit(k)) r.df[k] = df;
+        }
+    }
+}
+
+// a full warp (all 32 lanes, the same T): lane k's function k
+template <bool MIX>
+__device__ __forceinline__ void rate_lane(double T, int case_b, double &f, double &df)
+{
+    const RateFn &q = g_rate_fn[case_b].f[threadIdx.x & 31];
+    if constexpr (MIX) {
+        float lnT, invT;
+        t_level_f(T, lnT, invT);
+        rate_value_f(q, lnT, invT, f, df);
+    } else {
+        TLevel L;
+        t_level(T, L);
+        double sg;
+        f = rate_value(q, L, sg);
+        df = rate_deriv(q, L.invTd, f, sg);
+    }
+}
+// ... and the needed ones in every lane
+template <bool MIX>
+__device__ __forceinline__ void rates_warp(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
+{
+    double f, df;
+    rate_lane<MIX>(T, case_b, f, df);
+#pragma unroll
+    for (int k = 0; k < NRF; ++k) {
+        if (needF & rf_bit(k)) r.f[k] = __shfl_sync(0xffffffffu, f, k);
+        if (needD & rf_bit(k)) r.df[k] = __shfl_sync(0xffffffffu, df, k);
+    }
+}
+
+// A dual temperature: values from rates_serial (the bits of the double
+// path); with g = c1 - c2/T - c3 c4 sigma, d ln f/dT = g/T and
+//     d2f/dT2 = f [(g/T)^2 + (-g + c2/T - c3 c4^2 sigma (1 - sigma)) / T^2],
+// so f carries df dT and df carries d2f dT.
+__device__ __forceinline__ void rates_dual(const Dual &T, int case_b, unsigned needF, unsigned needD,
+                                           RatesT<Dual> &r)
+{
+    TLevel L;
+    t_level(T.v, L);
+    const RateFnTab &R = c_rate_fn[case_b];
+    const double x = L.invTd, dT = T.d;
+#pragma unroll
+    for (int k = 0; k < NRF; ++k) {
+        if (needF & rf_bit(k)) {
+            const RateFn &q = R.f[k];
+            double sg;
+            const double f = rate_value(q, L, sg);
+            const double df = rate_deriv(q, x, f, sg);
+            r.f[k] = Dual(f, df * dT);
+            if (needD & rf_bit(k)) {
+                const double g = q.d1 - q.d2 * x - q.d34 * sg;
+                const double D = g * x;
+                const double d2f = f * (D * D + x * x * (-g + q.d2 * x - q.d344 * sg * (1.0 - sg)));
+                r.df[k] = Dual(df, d2f * dT);
+            }
+        }
+    }
+}
+
+template <typename S>
+struct HRatesT {      // rates needed by the x_HII update
+    S beta, dbeta, alpha, dalpha;
+};
+template <typename S>
+struct HeRatesT {
+    S beta_HeI, beta_HeII, alpha_HeII, alpha_HeIII;
+};
+using HRates = HRatesT<double>;
+using HeRates = HeRatesT<double>;
+
+template <typename S>
+__device__ __forceinline__ void h_rates_from(const RatesT<S> &t, HRatesT<S> &r)
+{
+    r.beta = t.f[RF_BETA_HI];
+    r.dbeta = t.df[RF_BETA_HI];
+    r.alpha = t.f[RF_ALPHA_HII];
+    r.dalpha = t.df[RF_ALPHA_HII];
+}
+
+template <typename S>
+__device__ __forceinline__ void he_rates_from(const RatesT<S> &t, HeRatesT<S> &r)
+{
+    r.beta_HeI = t.f[RF_BETA_HEI];
+    r.beta_HeII = t.f[RF_BETA_HEII];
+    r.alpha_HeII = t.f[RF_ALPHA_HEII];
+    r.alpha_HeIII = t.f[RF_ALPHA_HEIII];
+}
+
+// Recombination rates of HII, HeII, HeIII (the case t was evaluated with)
+template <typename S>
+__device__ __forceinline__ void recomb_alphas(const RatesT<S> &t, S a[3])
+{
+    a[0] = t.f[RF_ALPHA_HII];
+    a[1] = t.f[RF_ALPHA_HEII];
+    a[2] = t.f[RF_ALPHA_HEIII];
+}
+
+// Primordial cooling magnitude L (Eq. (rate_cooling), positive = cooling)
+// and dL/dT: the sum of the cooling functions (collisional ionisation and
+// excitation, recombination and dielectronic cooling, bremsstrahlung) each
+// times its density, in a fixed pairwise order, then Compton cooling.  All
+// products and sums are rounded as written (rmul, radd), so the one-thread
+// sum and the warp sum (lane k term k) give the same bits.
 // a[i] through selects (registers, not local memory, for a lane-dependent
 // i; a plain a[i] once unrolled with a constant i)
 template <typename T, int N>
@@ -488,67 +489,6 @@ __device__ __forceinline__ T pick(const T (&a)[N], int i)
 #pragma unroll
     for (int j = 1; j < N; ++j) r = (i == j) ? a[j] : r;
     return r;
-}
-
-// dln e/dT of exp(a ln T + b/T + c)
-template <typename S>
-__device__ __forceinline__ S exp_dlog(const ExpArg &q, const S &x)
-{
-    return radd(rmul(x, q.a), rmul(rmul(x, x), -q.b));
-}
-
-// Per recombination case and term, the constants of the term and of its
-// log-derivative, folded at compile time:
-//   value  = Cc n_s sqrtT^sq u^uu T^tt X1 X2 v^hg, Cc = C (A_hg)^hg (A_aHeII)^amp
-//   dln/dT = invT [K0 + U (1 - u) - Kb invT + SR sigma]
-// with K0 = sq/2 + tt + a1 + a2 - hg p, U = -uu/2, Kb = b1 + b2,
-// SR = hg s r (X_k = exp(a_k ln T + b_k / T + c_k), sigma = w/(1 + w) of
-// the Hui & Gnedin fit: d ln v/dT = -(p - s r sigma)/T).
-struct CoolK {
-    double Cc, K0, U, Kb, SR;
-};
-struct CoolKTab {
-    CoolK k[2][kNCool];
-};
-constexpr CoolKTab make_cool_k()
-{
-    CoolKTab t{};
-    for (int cb = 0; cb < 2; ++cb) {
-        const RateTable &R = kRateTabCx[cb];
-        for (int k = 0; k < kNCool; ++k) {
-            const CoolTerm q = cool_row(k);
-            double Cc = q.C, K0 = 0.5 * q.sq + q.tt, Kb = 0.0, SR = 0.0;
-            if (q.e1 >= 0) { K0 += R.ea[q.e1].a; Kb += R.ea[q.e1].b; }
-            if (q.e2 >= 0) { K0 += R.ea[q.e2].a; Kb += R.ea[q.e2].b; }
-            if (q.hg >= 0) { Cc *= R.hg[q.hg].A; K0 -= R.hg[q.hg].p; SR = R.hg[q.hg].s * R.hg[q.hg].r; }
-            if (q.amp) Cc *= R.A_aHeII;
-            t.k[cb][k] = CoolK{Cc, K0, -0.5 * q.uu, Kb, SR};
-        }
-    }
-    return t;
-}
-static __device__ const CoolKTab g_cool_k = make_cool_k();
-
-// One term and its T-derivative; q the row, kc its constants.  A factor the
-// row lacks multiplies by 1 and a missing part of the log-derivative adds
-// 0 (both exact), so the one-thread sum (q known at compile time) and the
-// warp sum (q indexed by lane) give the same bits.
-template <typename S>
-__device__ __forceinline__ void cool_term(const CoolTerm &q, const CoolK &kc, const TranscT<S> &t, const S &T,
-                                          const S (&n)[NSP], S &v, S &dv)
-{
-    const S x = t.invT;
-    const int e1 = q.e1 >= 0 ? q.e1 : 0, e2 = q.e2 >= 0 ? q.e2 : 0, hg = q.hg >= 0 ? q.hg : 0;
-    const S one(1.0);
-    const S a = rmul(q.sq ? t.sqrtT : one, q.uu ? t.u : one);
-    const S b = rmul(q.tt ? T : one, q.e1 >= 0 ? pick(t.e, e1) : one);
-    const S c = rmul(q.e2 >= 0 ? pick(t.e, e2) : one, q.hg >= 0 ? pick(t.v, hg) : one);
-    const S f = rmul(rmul(rmul(a, b), rmul(c, pick(n, q.sp))), kc.Cc);
-    const S sg = q.hg >= 0 ? pick(t.s, hg) : S(0.0);
-    const S d = rfma(kc.U, radd(one, -t.u), S(kc.K0));
-    const S d2 = rfma(kc.SR, sg, rfma(-kc.Kb, x, d));
-    v = f;
-    dv = rmul(f, rmul(d2, x));
 }
 
 // the fixed pairwise order of a 16-lane butterfly (offsets 8, 4, 2, 1)
@@ -588,8 +528,8 @@ __device__ __forceinline__ void cooling_close(double comp, double tg, const S &T
 
 // one thread
 template <typename S>
-__device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, double comp, double tg, bool helium,
-                                             const S &T, const S &ne, const S &nHI, const S &nHII, const S &nHeI,
+__device__ __forceinline__ void cooling_from(const RatesT<S> &t, double comp, double tg, bool helium, const S &T,
+                                             const S &ne, const S &nHI, const S &nHII, const S &nHeI,
                                              const S &nHeII, const S &nHeIII, S &L, S &dL)
 {
     S n[NSP];
@@ -603,31 +543,38 @@ __device__ __forceinline__ void cooling_from(const TranscT<S> &t, int case_b, do
 #pragma unroll
     for (int k = 0; k < kNCool; ++k) {
         const CoolTerm q = cool_row(k);
-        if (helium || !q.he) cool_term(q, g_cool_k.k[case_b][k], t, T, n, a[k], b[k]);
+        if (helium || !q.he) {
+            a[k] = rmul(t.f[RF_COOL0 + k], n[q.sp]);
+            b[k] = rmul(t.df[RF_COOL0 + k], n[q.sp]);
+        }
     }
     const S Ls = tree_sum16(a), dLs = tree_sum16(b);
     cooling_close(comp, tg, T, ne, Ls, dLs, L, dL);
 }
 
-// a full warp (all 32 lanes, the same arguments): lane k < 11 evaluates
-// term k, the sums run over shuffles in the same pairwise order
-__device__ __forceinline__ void cooling_warp(const Transc &t, int case_b, double comp, double tg, bool helium,
-                                             double T, double ne, double nHI, double nHII, double nHeI,
-                                             double nHeII, double nHeIII, double &L, double &dL)
+// a full warp (all 32 lanes, the same arguments): lane k < 16 holds term k,
+// the sums run over shuffles in the same pairwise order
+template <bool MIX>
+__device__ __forceinline__ void cooling_warp(int case_b, double comp, double tg, bool helium, double T, double ne,
+                                             double nHI, double nHII, double nHeI, double nHeII, double nHeIII,
+                                             double &L, double &dL)
 {
+    double f, df;
+    rate_lane<MIX>(T, case_b, f, df);
     double n[NSP];
     cool_densities(nHI, nHII, nHeI, nHeII, nHeIII, n);
     const int k = threadIdx.x & 15;
-    const int kk = k < kNCool ? k : 0;
-    const CoolTerm q = kCoolTermsDev[kk];
-    double v, dv;
-    cool_term(q, g_cool_k.k[case_b][kk], t, T, n, v, dv);
-    if (k >= kNCool || (!helium && q.he)) v = dv = 0.0;
+    const double nk = pick(n, g_cool_sp[k]);
+    double v = rmul(f, nk), dv = rmul(df, nk);
+    if (!helium && (cool_mask(1) & rf_bit(k))) v = dv = 0.0;
 #pragma unroll
     for (int m = 8; m >= 1; m >>= 1) {
         v = radd(v, __shfl_xor_sync(0xffffffffu, v, m));
         dv = radd(dv, __shfl_xor_sync(0xffffffffu, dv, m));
     }
+    // lanes 16..31 summed other functions: every lane takes lane 0's sums
+    v = __shfl_sync(0xffffffffu, v, 0);
+    dv = __shfl_sync(0xffffffffu, dv, 0);
     cooling_close(comp, tg, T, ne, v, dv, L, dL);
 }
 

@@ -58,10 +58,10 @@ __device__ __forceinline__ void load_cell(const ThermoParams &p, long long c, bo
     cc.valid = false;
     cc.rvalid = false;
     if (p.isothermal) {
-        Transc t;
-        get_transc<WARP, R32>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), t);
-        h_rates_from(t, p.case_b, iso.h);
-        if (p.helium) he_rates_from(t, p.case_b, iso.he);
+        Rates t;
+        get_rates<WARP, R32>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), kNeedH, t);
+        h_rates_from(t, iso.h);
+        if (p.helium) he_rates_from(t, iso.he);
     }
 }
 

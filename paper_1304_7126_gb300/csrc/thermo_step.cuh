@@ -160,22 +160,19 @@ __device__ __forceinline__ bool ratio_lt(const S &a, const S &b, double t)
 }
 
 template <bool WARP, bool MIX>
-__device__ __forceinline__ void get_transc(const Dual &T, int case_b, unsigned need, TranscT<Dual> &t)
+__device__ __forceinline__ void get_rates(const Dual &T, int case_b, unsigned needF, unsigned needD,
+                                          RatesT<Dual> &r)
 {
     static_assert(!WARP && !MIX, "dual rates: one thread, FP64");
-    transc_dual(T, case_b, need, t);
+    rates_dual(T, case_b, needF, needD, r);
 }
 
 template <bool WARP, bool MIX>
-__device__ __forceinline__ void get_transc(double T, int case_b, unsigned need, Transc &t)
+__device__ __forceinline__ void get_rates(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
 {
-    if (MIX) {
-        if (WARP) transc_warp_f(T, case_b, t);
-        else transc_serial_f(T, case_b, need, t);
-    } else {
-        if (WARP) transc_warp(T, case_b, t);
-        else transc_serial(T, case_b, need, t);
-    }
+    if constexpr (WARP) rates_warp<MIX>(T, case_b, needF, needD, r);
+    else if constexpr (MIX) rates_serial_f(T, case_b, needF, needD, r);
+    else rates_serial(T, case_b, needF, needD, r);
 }
 
 // (alpha^A_j - alpha^B_j) n_j n_e of HII, HeII, HeIII at temperature T
@@ -187,14 +184,14 @@ __device__ __noinline__ void recomb_rates(S T, S nHII, S nHeII, S nHeIII, S ne, 
 {
     S aA[3], aB[3];
     {
-        TranscT<S> t;
-        get_transc<WARP, MIX>(T, 0, kNeedRec, t);
-        recomb_alphas(t, 0, aA);
+        RatesT<S> t;
+        get_rates<WARP, MIX>(T, 0, kNeedRec, 0u, t);
+        recomb_alphas(t, aA);
     }
     {
-        TranscT<S> t;
-        get_transc<WARP, MIX>(T, 1, kNeedRec, t);
-        recomb_alphas(t, 1, aB);
+        RatesT<S> t;
+        get_rates<WARP, MIX>(T, 1, kNeedRec, 0u, t);
+        recomb_alphas(t, aB);
     }
     rj[0] = (aA[0] - aB[0]) * nHII * ne;
     rj[1] = (aA[1] - aB[1]) * nHeII * ne;
@@ -342,7 +339,7 @@ __device__ __forceinline__ bool photons_serial(const ThermoParams &p, const Cell
 // partner may still be reading (every exchange is two-way).
 template <int G>
 struct PairX {
-    double N[2][G], Fs[2][G], Fb[2][G], g[2][4], L[2], dL[2];
+    double N[2][G], Fs[2][G], Fb[2][G], g[2][4], L[2], dL[2], m[2][3];
     int ok[2], small[2];
     unsigned long long item[2];
     volatile int seq[2];   // last exchange posted by role 0, role 1
@@ -423,6 +420,9 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     }
 
     bool pair_photons = false;   // the photon stage was done in the pair exchange
+    // the parts of step 2 that depend on the state only: 1/mu, mu, T/mu
+    S mden, mu, Tmu;
+    bool have_mu = false;
     if (!p.isothermal && !cc.valid) {
         if constexpr (PAIR) {
             // role 1 evaluates the cooling, role 0 the photon stage, at once
@@ -431,10 +431,8 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             const int n = ++pc->n;
             const int lane = threadIdx.x & 31;
             if (pc->role == 1) {
-                TranscT<S> t;
-                get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
-                cooling_warp(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII,
-                             cc.L, cc.dL);
+                cooling_warp<MIX>(p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII,
+                                  cc.L, cc.dL);
                 if (lane == 0) {
                     X.L[b] = cc.L;
                     X.dL[b] = cc.dL;
@@ -453,9 +451,15 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
                 }
                 gam0 = X.g[b][0]; gam1 = X.g[b][1]; gam2 = X.g[b][2]; heat = X.g[b][3];
                 sm = X.small[b] != 0;
+                mden = X.m[b][0]; mu = X.m[b][1]; Tmu = X.m[b][2];
             } else {
                 const bool ok = photons_warp<G, MIX, SM>(p, s, cc, nHI, nHeI, nHeII, h, o, gam0, gam1, gam2, heat, sm);
+                // (this warp would wait for the cooling meanwhile)
+                mden = mu_den(p.X, x, y2, y3);
+                mu = qdiv(S(1.0), mden);
+                Tmu = s.T * mden;
                 if (lane == 0) {
+                    X.m[b][0] = mden; X.m[b][1] = mu; X.m[b][2] = Tmu;
 #pragma unroll
                     for (int i = 0; i < G; ++i) {
                         X.N[b][i] = o.N[i];
@@ -474,13 +478,17 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             }
             cc.valid = true;
             pair_photons = true;
+            have_mu = true;
         } else {
-            TranscT<S> t;
-            get_transc<WARP, MIX>(s.T, p.case_b, kNeedCoolH | (p.helium ? kNeedCoolHe : 0u), t);
-            if constexpr (WARP)   // lane k evaluates cooling term k
-                cooling_warp(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
-            else
-                cooling_from(t, p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+            if constexpr (WARP) {   // lane k evaluates cooling term k
+                cooling_warp<MIX>(p.case_b, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII,
+                                  cc.L, cc.dL);
+            } else {
+                const unsigned need = kNeedCoolH | (p.helium ? kNeedCoolHe : 0u);
+                RatesT<S> t;
+                get_rates<WARP, MIX>(s.T, p.case_b, need, need, t);
+                cooling_from(t, p.comp, p.tg, p.helium != 0, s.T, ne, nHI, nHII, nHeI, nHeII, nHeIII, cc.L, cc.dL);
+            }
             cc.valid = true;
         }
     }
@@ -498,20 +506,22 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     }
     if (p.isothermal) heat = 0.0;
 
-    // 2. temperature
-    const S mden = mu_den(p.X, x, y2, y3);
-    const S mu = qdiv(S(1.0), mden);
+    // 2. temperature: T/mu + K h (Lambda) / (1 + mu (dL/dT) K h), Lambda =
+    // heating - cooling, d Lambda/d(T/mu) = -mu dL/dT
+    if (!have_mu) {
+        mden = mu_den(p.X, x, y2, y3);
+        mu = qdiv(S(1.0), mden);
+        Tmu = s.T * mden;
+    }
     S Tmu1 = 0.0;
     if (!p.isothermal) {
-        S lam = heat - cc.L;
-        S dlam = -mu * cc.dL;
-        const S K = iso.K;
-        S Tmu = s.T * mden;
-        S dT = qdiv(lam * K * h, 1.0 - dlam * K * h);
+        const S Kh = iso.K * h;
+        const S num = (heat - cc.L) * Kh;
+        const S dT = qdiv(num, 1.0 + (mu * cc.dL) * Kh);
         Tmu1 = Tmu + dT;
         S adT = fabs(dT);
+        if (ratio_gt(fabs(num), Tmu, 0.1)) return false;
         if (ratio_gt(adT, Tmu, 0.1)) return false;
-        if (ratio_gt(fabs(K * lam * h), Tmu, 0.1)) return false;
         sm = sm && ratio_lt(adT, Tmu, 0.05);
     }
 
@@ -520,9 +530,9 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     if (p.isothermal) {
         hr = iso.h;
     } else {
-        TranscT<S> t;
-        get_transc<WARP, MIX>(Tmu1 * mu, p.case_b, kNeedH, t);
-        h_rates_from(t, p.case_b, hr);
+        RatesT<S> t;
+        get_rates<WARP, MIX>(Tmu1 * mu, p.case_b, kNeedH, kNeedH, t);
+        h_rates_from(t, hr);
     }
     S C = hr.beta * ne + gam0;
     S Dd = hr.alpha * ne;
@@ -553,9 +563,9 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         if (p.isothermal) {
             r2 = iso.he;
         } else {
-            TranscT<S> t;
-            get_transc<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2, y3)), p.case_b, kNeedHe, t);
-            he_rates_from(t, p.case_b, r2);
+            RatesT<S> t;
+            get_rates<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2, y3)), p.case_b, kNeedHe, 0u, t);
+            he_rates_from(t, r2);
         }
         S C1 = y2 * r2.alpha_HeII * ne2;
         S D1 = r2.beta_HeI * ne2 + gam1;
@@ -568,9 +578,10 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         if (p.isothermal) {
             r3 = iso.he;
         } else {
-            TranscT<S> t;
-            get_transc<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2n, y3)), p.case_b, kNeedHe3, t);
-            he_rates_from(t, p.case_b, r3);
+            RatesT<S> t;
+            get_rates<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2n, y3)), p.case_b, kNeedHe3, 0u, t);
+            r3.beta_HeII = t.f[RF_BETA_HEII];
+            r3.alpha_HeIII = t.f[RF_ALPHA_HEIII];
         }
         S C3 = y2n * (r3.beta_HeII * ne3 + gam2);
         S D3 = r3.alpha_HeIII * ne3;
