@@ -102,7 +102,7 @@ thermo_vjp_kernel(ThermoParams p, const double *__restrict__ nH, const double *_
     cc.rvalid = false;
     if (p.isothermal) {
         RatesT<Dual> t;
-        rates_dual(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), kNeedH, t);
+        get_rates<false, false>(st.T, p.case_b, kNeedH | (p.helium ? kNeedHe : 0u), kNeedH, t);
         h_rates_from(t, iso.h);
         if (p.helium) he_rates_from(t, iso.he);
     }

@@ -152,6 +152,14 @@ __device__ __forceinline__ F2 rcp(F2 a)
     return fast_two_sum(r0, r0 * err);
 }
 
+// 1/a refined by a second Newton step in pair arithmetic (2^-47)
+__device__ __forceinline__ F2 rcp2(F2 a)
+{
+    const F2 r = rcp(a);
+    const F2 e = add(F2{1.0f, 0.0f}, neg(mul(a, r)));
+    return add(r, mul(r, e));
+}
+
 __device__ __forceinline__ F2 sqrt2(F2 a)
 {
     const float s0 = __fsqrt_rn(a.hi);

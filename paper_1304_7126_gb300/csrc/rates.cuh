@@ -229,26 +229,47 @@ static __device__ const RateFnTab g_rate_fn[2] = {make_rate_fns(0), make_rate_fn
 static __device__ const int g_cool_sp[16] = {SP_HI, SP_HI, SP_HII, SP_FF, SP_HEI, SP_HEII, SP_HEII, SP_HEII,
                                              SP_HEII, SP_HEII, SP_HEIII, 0, 0, 0, 0, 0};
 
-// ln T and 1/T of one temperature as pairs, 1/T as a double
+// ln T and 1/T of one temperature: as pairs and 1/T as a double (FP64
+// path), as floats (FP32 path)
 struct TLevel {
     dfm::F2 lnT, invT;
     double invTd;
+    float lnTf, invTf;
 };
+template <bool MIX>
 __device__ __forceinline__ void t_level(double T, TLevel &L)
 {
     using namespace dfm;
-    if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^60 K
+    if constexpr (MIX) {
+        const float Tf = narrow(T);
+        L.lnTf = logf(Tf);
+        L.invTf = 1.0f / Tf;
+    } else if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^60 K
         L.invTd = 1.0 / T;
         L.lnT = split_any(log(T));
         L.invT = split_any(L.invTd);
-        return;
+    } else {
+        const F2 T2 = split(T);
+        L.lnT = log2f2(T2);
+        L.invT = rcp(T2);
+        L.invTd = to_double(L.invT);
     }
-    const F2 T2 = split(T);
-    L.lnT = log2f2(T2);
-    L.invT = rcp(T2);
-    L.invTd = to_double(L.invT);
 }
-
+// the same from 1/T as a pair
+template <bool MIX>
+__device__ __forceinline__ void t_level_inv(dfm::F2 invT, TLevel &L)
+{
+    using namespace dfm;
+    if constexpr (MIX) {
+        L.invTf = invT.hi;
+        L.lnTf = -logf(L.invTf);
+    } else {
+        L.invT = invT;
+        L.invTd = to_double(invT);
+        if (invT.hi > 0.0f && splittable(L.invTd)) L.lnT = neg(log2f2(invT));
+        else L.lnT = split_any(-log(L.invTd));
+    }
+}
 // f(T) of one function given l = softplus(z); all FP64 products rounded as
 // written
 __device__ __forceinline__ double rate_from_l(const RateFn &q, const TLevel &L, dfm::F2 l)
@@ -287,13 +308,6 @@ __device__ __forceinline__ void rate_value_f(const RateFn &q, float lnT, float i
     const float g = __fmul_rn(__fmaf_rn(-q.g34, sg, __fmaf_rn(-q.c2.hi, invT, q.c1.hi)), invT);
     df = rmul(f, dfm::widen(g));
 }
-__device__ __forceinline__ void t_level_f(double T, float &lnT, float &invT)
-{
-    const float Tf = narrow(T);
-    lnT = logf(Tf);
-    invT = 1.0f / Tf;
-}
-
 // values (and derivatives) of several functions at one temperature
 template <typename S>
 struct RatesT {
@@ -337,11 +351,9 @@ __host__ __device__ constexpr unsigned rf_plain_mask()
 // one thread: the functions in needF (derivatives of those in needD); the
 // shared softplus of u once, none where it is multiplied by zero (the same
 // bits as the warp, which evaluates every slot's own)
-__device__ __forceinline__ void rates_serial(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
+__device__ __forceinline__ void rates_serial(const TLevel &L, int case_b, unsigned needF, unsigned needD, Rates &r)
 {
     constexpr unsigned kU = rf_u_mask(), kPlain = rf_plain_mask();
-    TLevel L;
-    t_level(T, L);
     const RateFnTab &R = c_rate_fn[case_b];
     double sgu = 0.0;
     dfm::F2 lu{0.0f, 0.0f};
@@ -362,16 +374,14 @@ __device__ __forceinline__ void rates_serial(double T, int case_b, unsigned need
         }
     }
 }
-__device__ __forceinline__ void rates_serial_f(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
+__device__ __forceinline__ void rates_serial_f(const TLevel &L, int case_b, unsigned needF, unsigned needD, Rates &r)
 {
-    float lnT, invT;
-    t_level_f(T, lnT, invT);
     const RateFnTab &R = c_rate_fn[case_b];
 #pragma unroll
     for (int k = 0; k < NRF; ++k) {
         if (needF & rf_bit(k)) {
             double df;
-            rate_value_f(R.f[k], lnT, invT, r.f[k], df);
+            rate_value_f(R.f[k], L.lnTf, L.invTf, r.f[k], df);
             if (needD & rf_bit(k)) r.df[k] = df;
         }
     }
@@ -379,16 +389,12 @@ __device__ __forceinline__ void rates_serial_f(double T, int case_b, unsigned ne
 
 // a full warp (all 32 lanes, the same T): lane k's function k
 template <bool MIX>
-__device__ __forceinline__ void rate_lane(double T, int case_b, double &f, double &df)
+__device__ __forceinline__ void rate_lane(const TLevel &L, int case_b, double &f, double &df)
 {
     const RateFn &q = g_rate_fn[case_b].f[threadIdx.x & 31];
     if constexpr (MIX) {
-        float lnT, invT;
-        t_level_f(T, lnT, invT);
-        rate_value_f(q, lnT, invT, f, df);
+        rate_value_f(q, L.lnTf, L.invTf, f, df);
     } else {
-        TLevel L;
-        t_level(T, L);
         double sg;
         f = rate_value(q, L, sg);
         df = rate_deriv(q, L.invTd, f, sg);
@@ -396,10 +402,10 @@ __device__ __forceinline__ void rate_lane(double T, int case_b, double &f, doubl
 }
 // ... and the needed ones in every lane
 template <bool MIX>
-__device__ __forceinline__ void rates_warp(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
+__device__ __forceinline__ void rates_warp(const TLevel &L, int case_b, unsigned needF, unsigned needD, Rates &r)
 {
     double f, df;
-    rate_lane<MIX>(T, case_b, f, df);
+    rate_lane<MIX>(L, case_b, f, df);
 #pragma unroll
     for (int k = 0; k < NRF; ++k) {
         if (needF & rf_bit(k)) r.f[k] = __shfl_sync(0xffffffffu, f, k);
@@ -407,17 +413,16 @@ __device__ __forceinline__ void rates_warp(double T, int case_b, unsigned needF,
     }
 }
 
-// A dual temperature: values from rates_serial (the bits of the double
-// path); with g = c1 - c2/T - c3 c4 sigma, d ln f/dT = g/T and
+// A dual temperature (level L of its value, derivative dT): values as in
+// rates_serial (the bits of the double path); with g = c1 - c2/T - c3 c4
+// sigma, d ln f/dT = g/T and
 //     d2f/dT2 = f [(g/T)^2 + (-g + c2/T - c3 c4^2 sigma (1 - sigma)) / T^2],
 // so f carries df dT and df carries d2f dT.
-__device__ __forceinline__ void rates_dual(const Dual &T, int case_b, unsigned needF, unsigned needD,
+__device__ __forceinline__ void rates_dual(const TLevel &L, double dT, int case_b, unsigned needF, unsigned needD,
                                            RatesT<Dual> &r)
 {
-    TLevel L;
-    t_level(T.v, L);
     const RateFnTab &R = c_rate_fn[case_b];
-    const double x = L.invTd, dT = T.d;
+    const double x = L.invTd;
 #pragma unroll
     for (int k = 0; k < NRF; ++k) {
         if (needF & rf_bit(k)) {
@@ -559,8 +564,10 @@ __device__ __forceinline__ void cooling_warp(int case_b, double comp, double tg,
                                              double nHI, double nHII, double nHeI, double nHeII, double nHeIII,
                                              double &L, double &dL)
 {
+    TLevel Lv;
+    t_level<MIX>(T, Lv);
     double f, df;
-    rate_lane<MIX>(T, case_b, f, df);
+    rate_lane<MIX>(Lv, case_b, f, df);
     double n[NSP];
     cool_densities(nHI, nHII, nHeI, nHeII, nHeIII, n);
     const int k = threadIdx.x & 15;

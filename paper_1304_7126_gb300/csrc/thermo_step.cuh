@@ -164,15 +164,49 @@ __device__ __forceinline__ void get_rates(const Dual &T, int case_b, unsigned ne
                                           RatesT<Dual> &r)
 {
     static_assert(!WARP && !MIX, "dual rates: one thread, FP64");
-    rates_dual(T, case_b, needF, needD, r);
+    TLevel L;
+    t_level<false>(T.v, L);
+    rates_dual(L, T.d, case_b, needF, needD, r);
 }
-
+template <bool WARP, bool MIX>
+__device__ __forceinline__ void rates_at(const TLevel &L, int case_b, unsigned needF, unsigned needD, Rates &r)
+{
+    if constexpr (WARP) rates_warp<MIX>(L, case_b, needF, needD, r);
+    else if constexpr (MIX) rates_serial_f(L, case_b, needF, needD, r);
+    else rates_serial(L, case_b, needF, needD, r);
+}
 template <bool WARP, bool MIX>
 __device__ __forceinline__ void get_rates(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
 {
-    if constexpr (WARP) rates_warp<MIX>(T, case_b, needF, needD, r);
-    else if constexpr (MIX) rates_serial_f(T, case_b, needF, needD, r);
-    else rates_serial(T, case_b, needF, needD, r);
+    TLevel L;
+    t_level<MIX>(T, L);
+    rates_at<WARP, MIX>(L, case_b, needF, needD, r);
+}
+// Rates at T = (T/mu') mu_j given 1/mu_j = md and 1/(T/mu') = iT as a pair
+// (the helium temperatures of step 4 enter their rates only through 1/T and
+// ln T): 1/T = md iT in pair arithmetic, no FP64 quotient.  A dual T takes
+// the levels of its value and the derivative of Tmu1 / md.
+__device__ __forceinline__ dfm::F2 inv_pair(double x)
+{
+    if (!(x > 0.0) || !dfm::splittable(x)) return dfm::split_any(1.0 / x);
+    return dfm::rcp2(dfm::split(x));
+}
+template <bool WARP, bool MIX>
+__device__ __forceinline__ void rates_mu(const Dual &md, dfm::F2 iT, const Dual &Tmu1, int case_b, unsigned needF,
+                                         unsigned needD, RatesT<Dual> &r)
+{
+    static_assert(!WARP && !MIX, "dual rates: one thread, FP64");
+    TLevel L;
+    t_level_inv<false>(dfm::mul(dfm::split_any(md.v), iT), L);
+    rates_dual(L, (Tmu1 / md).d, case_b, needF, needD, r);
+}
+template <bool WARP, bool MIX>
+__device__ __forceinline__ void rates_mu(double md, dfm::F2 iT, double, int case_b, unsigned needF,
+                                         unsigned needD, Rates &r)
+{
+    TLevel L;
+    t_level_inv<MIX>(dfm::mul(dfm::split_any(md), iT), L);
+    rates_at<WARP, MIX>(L, case_b, needF, needD, r);
 }
 
 // (alpha^A_j - alpha^B_j) n_j n_e of HII, HeII, HeIII at temperature T
@@ -524,6 +558,8 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
         if (ratio_gt(adT, Tmu, 0.1)) return false;
         sm = sm && ratio_lt(adT, Tmu, 0.05);
     }
+    // 1/(T/mu') as a pair, for the helium temperatures (T/mu') mu_j
+    const dfm::F2 iT = (p.isothermal || !p.helium) ? dfm::F2{0.0f, 0.0f} : inv_pair(val(Tmu1));
 
     // 3. hydrogen
     HRatesT<S> hr;
@@ -564,7 +600,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             r2 = iso.he;
         } else {
             RatesT<S> t;
-            get_rates<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2, y3)), p.case_b, kNeedHe, 0u, t);
+            rates_mu<WARP, MIX>(mu_den(p.X, x1, y2, y3), iT, Tmu1, p.case_b, kNeedHe, 0u, t);
             he_rates_from(t, r2);
         }
         S C1 = y2 * r2.alpha_HeII * ne2;
@@ -579,7 +615,7 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
             r3 = iso.he;
         } else {
             RatesT<S> t;
-            get_rates<WARP, MIX>(qdiv(Tmu1, mu_den(p.X, x1, y2n, y3)), p.case_b, kNeedHe3, 0u, t);
+            rates_mu<WARP, MIX>(mu_den(p.X, x1, y2n, y3), iT, Tmu1, p.case_b, kNeedHe3, 0u, t);
             r3.beta_HeII = t.f[RF_BETA_HEII];
             r3.alpha_HeIII = t.f[RF_ALPHA_HEIII];
         }
