@@ -5,16 +5,18 @@
 // P = c^2 N D(f, n) (Sec. 2, Eqs. (edd2), (eddTens), (Udir)) and the GLF
 // (Eq. (glf)) or HLL (Eq. (hll)) intercell flux.
 //
-// Data layout: N[g][z][y][x], F[g][3][z][y][x], x fastest.  One CTA owns a
-// 32 x 8 (x, y) tile of one group and marches along z over a chunk of
-// planes.  Each thread keeps its own column's cells z-1, z, z+1 in
-// registers, so the closure is evaluated once per cell and every z face
-// flux once; the in-plane neighbours (and the one-cell halo ring of the
-// tile, recomputed by the ring threads) go through shared memory, where
-// every x and y face flux is also evaluated once.  Reads and writes of the
-// planes are coalesced 256-byte rows.  Per-block photon sums (in the box
-// after transport, net outflow through boundary faces) go to a partials
-// array reduced later in a fixed order, so the budget is reproducible.
+// Data layout: N[g][z][y][x], F[g][3][z][y][x], x fastest.  A CTA works on
+// 32 x 8 (x, y) tiles of one group, marching along z; a single box runs a
+// persistent grid whose CTAs each take an equal contiguous range of the
+// (group, tile, plane) units.  Each thread keeps its own column's cells
+// z-1, z, z+1 in registers, so the closure is evaluated once per cell and
+// every z face flux once; the in-plane neighbours (and the one-cell halo
+// ring of the tile, recomputed by the ring threads) go through shared
+// memory, where every x and y face flux is also evaluated once.  Reads and
+// writes of the planes are coalesced 256-byte rows.  Per-CTA photon sums
+// (in the box after transport, net outflow through boundary faces) go to a
+// partials array reduced later in a fixed order, so the budget is
+// reproducible for a given grid.
 //
 // The kernel is templated on the state type S: double (the FP64 path) or
 // float (the mixed path, RT_MIXED: state stored and transported in FP32,
@@ -475,7 +477,7 @@ __device__ __noinline__ void transport_segment(PlaneSmem<S, TBX, TBY> &s, const 
     transport_tile<S, FLUX, TBX, TBY>(s, g, c, dtdx, N0, F0, N1, F1, tab, inf, x0, y0, z0, z1, inbox, outflow);
 }
 
-// Single box: a persistent grid (kTransportCtasPerSm CTAs per SM).  The
+// Single box: a persistent grid (transport_grid: 2 CTAs per SM in FP64, 4 in FP32).  The
 // (group, tile, plane) units, planes fastest, are cut into gridDim.x equal
 // contiguous ranges, one per CTA, so every CTA gets the same number of
 // planes (a launch of one CTA per tile chunk left a last, nearly empty wave);
@@ -534,9 +536,10 @@ __device__ __forceinline__ void transport_kernel_body(GridDev g, int G, S c, S d
     }
 }
 
-// FP64: capped at 128 registers so that two CTAs share an SM.  FP32: capped at 80
-// registers so that three CTAs share an SM and hide the shared-memory and
-// table-lookup latencies (the FP32 kernel is latency-bound).
+// FP64: capped at 128 registers so that two CTAs share an SM.  FP32: capped at 64
+// registers so that four CTAs share an SM and hide the shared-memory and
+// table-lookup latencies (the FP32 kernel is latency-bound; 2, 3 and 4 CTAs
+// per SM gave 0.39, 0.35 and 0.33 ms at 128^3 x 3 groups).
 template <typename S, int FLUX>
 __global__ void __launch_bounds__(256, 2)
 transport_kernel(GridDev g, int G, S c, S dtdx, double area_dt, const S *__restrict__ N0all,
@@ -549,7 +552,7 @@ transport_kernel(GridDev g, int G, S c, S dtdx, double area_dt, const S *__restr
 }
 
 template <int FLUX>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 transport_kernel_f32(GridDev g, int G, float c, float dtdx, double area_dt, const float *__restrict__ N0all,
                      const float *__restrict__ F0all, float *__restrict__ N1all, float *__restrict__ F1all,
                      const float *__restrict__ tab, const float *__restrict__ inflow,
@@ -591,7 +594,7 @@ transport_batch_kernel(const BatchItem *__restrict__ items, const BatchBox *__re
 
 int transport_grid(int n_sm, bool fp32)
 {
-    return (fp32 ? 3 : 2) * (n_sm > 0 ? n_sm : 1);
+    return (fp32 ? 4 : 2) * (n_sm > 0 ? n_sm : 1);
 }
 
 template <typename S, int TBX, int TBY>
