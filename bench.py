@@ -36,11 +36,13 @@ UNIT = "cell-group updates/s"
 # (oracle/make_counts.py writes tests/golden/op_counts.json): FP64 flops per
 # thermochemistry attempt and per transport cell-group, as the oracle states
 # the method.  Transport bytes: N, F read and written once per cell-group.
+# the library's default routing: attempts of the first pass, and of the
+# first lane-per-cell drain stage
 PASS1_ATTEMPTS = 6
-DRAIN1_BUDGET = 192
-# DRAM bytes (read + write) per launch of the dominant phase's kernels, from
-# an ncu capture of the current kernels (profiles/); None until captured
-TRAFFIC = {}   # attempts a queued cell spends in the first lane-per-cell drain stage
+DRAIN1_BUDGET = 96
+# DRAM bytes (read + write) per launch, from the ncu captures of the current
+# kernels summarised in profiles/ (128^3 x 3 groups, HLL)
+TRAFFIC = {"transport": 399427072 + 192599552}
 
 
 def _op_counts():
@@ -416,13 +418,15 @@ def main():
         "bound": "fp64" if tr_flop / fp64_peak > tr_bytes / hbm_peak else "hbm",
         "roof_ms_per_launch": roof_ms, "frac_of_roof": roof_ms / tr_ms,
         "hbm": {"achieved": tr_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": tr_gbs / hbm_peak,
-                "algorithmic_bytes_per_launch": tr_bytes, "peak_kind": peak_kind},
+                "algorithmic_bytes_per_launch": tr_bytes, "peak_kind": peak_kind,
+                "traffic": TRAFFIC.get("transport") if w.name == "cosmo128_s7" else None},
         "fp64": {"achieved": tr_gfl, "peak": fp64_peak, "unit": "GFLOP/s", "frac": tr_gfl / fp64_peak,
                  "flop_per_cell_group": tr_fpc, "algorithmic_flop_per_launch": tr_flop,
                  "peak_kind": "measured (cuBLAS DGEMM)"}}
     if dominant == "transport":
         roof = {"bound": "hbm", "achieved": tr_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": tr_gbs / hbm_peak,
-                "traffic": None, "kernel": "transport", "peak_kind": peak_kind,
+                "traffic": TRAFFIC.get("transport") if w.name == "cosmo128_s7" else None, "kernel": "transport",
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": tr_bytes}
     else:
         # thermochemistry: FP64-ALU work = algorithmic flops per attempt x
