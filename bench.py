@@ -39,7 +39,7 @@ UNIT = "cell-group updates/s"
 # the library's default routing: attempts of the first pass, and of the
 # first lane-per-cell drain stage
 PASS1_ATTEMPTS = 6
-DRAIN1_BUDGET = 96
+DRAIN1_BUDGET = 128
 # DRAM bytes (read + write) per launch, from the ncu captures of the current
 # kernels summarised in profiles/ (128^3 x 3 groups, HLL)
 TRAFFIC = {"transport": 399427072 + 192599552}

@@ -243,7 +243,7 @@ int rt_hll_table(int nf, int nmu, double *out);
  * and the attempt counts are identical for every routing, F may differ in
  * its last bits (the flux scale prod 1/(1 + h D_i) of the attempts run so
  * far is applied to F when a cell moves between kernels).  Values <= 0
- * (drain2_min_cells < 0) restore the defaults 6, 96, 512 and eight cells
+ * (drain2_min_cells < 0) restore the defaults 6, 128, 128 and eight cells
  * per warp of the warp-per-cell kernel.  Takes effect at the next step. */
 int rt_set_thermo_routing(rt_handle *h, int pass1_attempts, int drain_budget, int drain2_budget,
                           long long drain2_min_cells);

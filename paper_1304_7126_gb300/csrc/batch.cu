@@ -8,8 +8,8 @@
 // sources and number of photon groups.  Boxes with the same group count form
 // a class whose cells are stored back to back ([G][cells of the class]
 // photon arrays), so the thermochemistry of a whole class is one queue-
-// balanced pass, and the transport of all boxes is one launch per tile
-// shape over a work list of (box, group, tile, z range) items.  A step is
+// balanced pass, and the transport of all boxes is one launch over a work
+// list of (box, group, tile, z range) items of both tile shapes.  A step is
 // captured as one CUDA graph by rt_batch_run.  rt_batch_autotune picks, per
 // box side, the tile shape (32 x 8 or 16 x 16) and the planes per CTA that
 // transport fastest.
@@ -300,14 +300,10 @@ int enqueue_batch_step(rt_batch *b, double dt)
     }
     const int nxt = 1 - b->cur;
     const void *tab = f32 ? (const void *)b->hllf : (const void *)b->hll;
-    e = launch_transport_batch(b->d_items, b->d_boxes, 0, b->n_items_shape0, 0, f32, b->opt.flux, b->cr, dt, b->dx,
-                               (const void *const *)b->d_Ncls[b->cur], (const void *const *)b->d_Fcls[b->cur],
-                               b->d_Ncls[nxt], b->d_Fcls[nxt], tab, b->d_pin, b->d_pout, b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "transport");
-    e = launch_transport_batch(b->d_items, b->d_boxes, b->n_items_shape0, b->n_items - b->n_items_shape0, 1, f32,
-                               b->opt.flux, b->cr, dt, b->dx, (const void *const *)b->d_Ncls[b->cur],
-                               (const void *const *)b->d_Fcls[b->cur], b->d_Ncls[nxt], b->d_Fcls[nxt], tab,
-                               b->d_pin, b->d_pout, b->stream);
+    e = launch_transport_batch_all(b->d_items, b->d_boxes, b->n_items_shape0, b->n_items, f32, b->opt.flux, b->cr,
+                                   dt, b->dx, (const void *const *)b->d_Ncls[b->cur],
+                                   (const void *const *)b->d_Fcls[b->cur], b->d_Ncls[nxt], b->d_Fcls[nxt], tab,
+                                   b->d_pin, b->d_pout, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "transport");
     b->cur = nxt;
     for (ClassData &c : b->cls) {

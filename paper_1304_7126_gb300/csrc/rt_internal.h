@@ -103,8 +103,8 @@ inline void derive_group_terms(ThermoParams &p)
 inline void default_routing(ThermoParams &p)
 {
     p.pass1_attempts = 6;
-    p.drain_budget = 96;
-    p.drain2_budget = 512;
+    p.drain_budget = 128;
+    p.drain2_budget = 128;
     p.drain2_min = -1;
 }
 
@@ -157,6 +157,12 @@ cudaError_t launch_transport_batch(const BatchItem *items, const BatchBox *boxes
                                    int shape, bool fp32, int flux, double cr, double dt, double dx,
                                    const void *const *N0, const void *const *F0, void *const *N1,
                                    void *const *F1, const void *tab, double *pin, double *pout, cudaStream_t s);
+// ... all items of both tile shapes in one launch (items [0, n_shape0) of
+// shape 0, the rest of shape 1)
+cudaError_t launch_transport_batch_all(const BatchItem *items, const BatchBox *boxes, int n_shape0, int nitems,
+                                       bool fp32, int flux, double cr, double dt, double dx, const void *const *N0,
+                                       const void *const *F0, void *const *N1, void *const *F1, const void *tab,
+                                       double *pin, double *pout, cudaStream_t st);
 void transport_init();   // kernel attributes; called once per handle
 
 // ev (optional, 4 events): recorded around the first pass (0, 1) and

@@ -41,27 +41,40 @@ template <typename S> struct Vec2;
 template <> struct Vec2<double> { using T = double2; };
 template <> struct Vec2<float> { using T = float2; };
 
+// Every product, sum and fused multiply-add below is written out with a
+// rounded intrinsic, so the compiler fuses nothing on its own: the
+// single-box and batched kernels, which inline the same code in different
+// surroundings, then give the same bits.
+__device__ __forceinline__ double tmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float tmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double tadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float tadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double tsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float tsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 template <typename S>
 __device__ __forceinline__ void hll_lookup(const S *__restrict__ tab, S f, S mu, S &lo, S &hi)
 {
-    S fx = f * (S)(kHllNF - 1);
+    S fx = tmul(f, (S)(kHllNF - 1));
     int k = (int)floor(fx);
     k = k < 0 ? 0 : (k > kHllNF - 2 ? kHllNF - 2 : k);
-    S wf = fx - (S)k;
-    S mx = (mu + (S)1) * (S)0.5 * (S)(kHllNMU - 1);
+    S wf = tsub(fx, (S)k);
+    S mx = tmul(tadd(mu, (S)1), (S)(0.5 * (kHllNMU - 1)));
     int j = (int)floor(mx);
     j = j < 0 ? 0 : (j > kHllNMU - 2 ? kHllNMU - 2 : j);
-    S wm = mx - (S)j;
+    S wm = tsub(mx, (S)j);
     using V = typename Vec2<S>::T;
     const V *t = reinterpret_cast<const V *>(tab);
     V a = __ldg(&t[k * kHllNMU + j]);
     V b = __ldg(&t[k * kHllNMU + j + 1]);
     V c = __ldg(&t[(k + 1) * kHllNMU + j]);
     V d = __ldg(&t[(k + 1) * kHllNMU + j + 1]);
-    S lo0 = a.x + wm * (b.x - a.x), lo1 = c.x + wm * (d.x - c.x);
-    S hi0 = a.y + wm * (b.y - a.y), hi1 = c.y + wm * (d.y - c.y);
-    lo = lo0 + wf * (lo1 - lo0);
-    hi = hi0 + wf * (hi1 - hi0);
+    S lo0 = tfma(wm, tsub(b.x, a.x), a.x), lo1 = tfma(wm, tsub(d.x, c.x), c.x);
+    S hi0 = tfma(wm, tsub(b.y, a.y), a.y), hi1 = tfma(wm, tsub(d.y, c.y), c.y);
+    lo = tfma(wf, tsub(lo1, lo0), lo0);
+    hi = tfma(wf, tsub(hi1, hi0), hi0);
 }
 
 // Photon densities below this are no photons: the closure takes f = 0.
@@ -80,30 +93,32 @@ __device__ __forceinline__ void closure(S N, S Fx, S Fy, S Fz, S c, const S *__r
         S m = fmax(fabs(Fx), fmax(fabs(Fy), fabs(Fz)));
         sc = (m < (S)1e-15) ? (S)0x1p64 : ((m > (S)1e15) ? (S)0x1p-64 : (S)1);
     }
-    const S gx = Fx * sc, gy = Fy * sc, gz = Fz * sc;
-    S F2 = gx * gx + gy * gy + gz * gz;
+    const S gx = tmul(Fx, sc), gy = tmul(Fy, sc), gz = tmul(Fz, sc);
+    S F2 = tfma(gz, gz, tfma(gy, gy, tmul(gx, gx)));
     S f = 0, nx = 0, ny = 0, nz = 0;
     if (N > (S)kClosureFloorN && F2 > (S)0) {
         S inv = rsqrt(F2);
-        f = fmin((F2 * inv) / (c * N * sc), (S)1);
-        nx = gx * inv; ny = gy * inv; nz = gz * inv;
+        f = fmin(tmul(F2, inv) / tmul(tmul(c, N), sc), (S)1);
+        nx = tmul(gx, inv); ny = tmul(gy, inv); nz = tmul(gz, inv);
     }
-    S f2 = f * f;
-    S chi = ((S)3 + (S)4 * f2) / ((S)5 + (S)2 * sqrt((S)4 - (S)3 * f2));
-    S cN = c * c * N;
-    S ca = cN * (S)0.5 * ((S)1 - chi);
-    S cb = cN * (S)0.5 * ((S)3 * chi - (S)1);
-    q.Pxx = ca + cb * nx * nx;
-    q.Pyy = ca + cb * ny * ny;
-    q.Pzz = ca + cb * nz * nz;
-    q.Pxy = cb * nx * ny;
-    q.Pxz = cb * nx * nz;
-    q.Pyz = cb * ny * nz;
+    S f2 = tmul(f, f);
+    S chi = tfma((S)4, f2, (S)3) / tfma((S)2, sqrt(tfma((S)-3, f2, (S)4)), (S)5);
+    S cN = tmul(tmul(c, c), N);
+    S ch = tmul(cN, (S)0.5);
+    S ca = tmul(ch, tsub((S)1, chi));
+    S cb = tmul(ch, tfma((S)3, chi, (S)-1));
+    S bx = tmul(cb, nx), by = tmul(cb, ny);
+    q.Pxx = tfma(bx, nx, ca);
+    q.Pyy = tfma(by, ny, ca);
+    q.Pzz = tfma(tmul(cb, nz), nz, ca);
+    q.Pxy = tmul(bx, ny);
+    q.Pxz = tmul(bx, nz);
+    q.Pyz = tmul(by, nz);
     if (FLUX == RT_HLL) {
         S lo, hi;
-        hll_lookup<S>(tab, f, nx, lo, hi); q.lmin[0] = lo * c; q.lmax[0] = hi * c;
-        hll_lookup<S>(tab, f, ny, lo, hi); q.lmin[1] = lo * c; q.lmax[1] = hi * c;
-        hll_lookup<S>(tab, f, nz, lo, hi); q.lmin[2] = lo * c; q.lmax[2] = hi * c;
+        hll_lookup<S>(tab, f, nx, lo, hi); q.lmin[0] = tmul(lo, c); q.lmax[0] = tmul(hi, c);
+        hll_lookup<S>(tab, f, ny, lo, hi); q.lmin[1] = tmul(lo, c); q.lmax[1] = tmul(hi, c);
+        hll_lookup<S>(tab, f, nz, lo, hi); q.lmin[2] = tmul(lo, c); q.lmax[2] = tmul(hi, c);
     }
 }
 
@@ -127,20 +142,22 @@ __device__ __forceinline__ void face_flux(const CellQ<S> &L, const CellQ<S> &R, 
     if (FLUX == RT_HLL) {
         S lp = fmax((S)0, fmax(L.lmax[D], R.lmax[D]));
         S lm = fmin((S)0, fmin(L.lmin[D], R.lmin[D]));
-        S den = lp - lm;
+        S den = tsub(lp, lm);
         if (den > (S)0) {
             S inv = (S)1 / den;
-            S pm = lp * lm;
+            S pm = tmul(lp, lm);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) out[k] = (lp * fl[k] - lm * fr[k] + pm * (ur[k] - ul[k])) * inv;
+            for (int k = 0; k < 4; ++k)
+                out[k] = tmul(tfma(pm, tsub(ur[k], ul[k]), tfma(-lm, fr[k], tmul(lp, fl[k]))), inv);
         } else {
             // both speeds vanish only for f = 1 beams parallel to the face
 #pragma unroll
-            for (int k = 0; k < 4; ++k) out[k] = (S)0.5 * (fl[k] + fr[k]);
+            for (int k = 0; k < 4; ++k) out[k] = tmul((S)0.5, tadd(fl[k], fr[k]));
         }
     } else {
+        const S hc = tmul((S)0.5, c);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) out[k] = (S)0.5 * (fl[k] + fr[k]) - (S)0.5 * c * (ur[k] - ul[k]);
+        for (int k = 0; k < 4; ++k) out[k] = tfma(-hc, tsub(ur[k], ul[k]), tmul((S)0.5, tadd(fl[k], fr[k])));
     }
 }
 
@@ -270,8 +287,10 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
                                                const S *__restrict__ inf, int x0, int y0, int z0, int z1,
                                                double &inbox, double &outflow)
 {
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * TBX + tx;
+    // (tx, ty) from the linear thread index: 2-D blocks of TBX x TBY or 1-D
+    // blocks of TBX * TBY threads alike
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int tx = tid % TBX, ty = tid / TBX;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < g.nx) && (y < g.ny);
     // ghost-only position of this thread's smem slot (ragged tile edge)
@@ -392,9 +411,10 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (sizeof(S) == sizeof(double)) {
-                    S acc = (s.fxs[k][ty][tx] - s.fxs[k][ty][tx + 1]) +
-                            (s.fys[k][ty][tx] - s.fys[k][ty + 1][tx]) + (flo[k] - fhi[k]);
-                    nw[k] = u[k] + dtdx * acc;
+                    S acc = tadd(tadd(tsub(s.fxs[k][ty][tx], s.fxs[k][ty][tx + 1]),
+                                      tsub(s.fys[k][ty][tx], s.fys[k][ty + 1][tx])),
+                                 tsub(flo[k], fhi[k]));
+                    nw[k] = tfma(dtdx, acc, u[k]);
                 } else {
                     // compensated: U + sum of six dt/dx-scaled face fluxes
                     float d = (float)dtdx;
@@ -415,16 +435,16 @@ __device__ __forceinline__ void transport_tile(PlaneSmem<S, TBX, TBY> &s, const 
             if (nw[0] < (S)0) { nw[0] = 0; nw[1] = nw[2] = nw[3] = 0; }
             // squares of tiny values lose digits: compare tiny states scaled
             // by a power of two (exact), the factor is scale-free
-            S cn = c * nw[0];
+            S cn = tmul(c, nw[0]);
             S m = fmax(fmax(fabs(nw[1]), fabs(nw[2])), fmax(fabs(nw[3]), cn));
             const S tiny = sizeof(S) == sizeof(double) ? (S)1e-140 : (S)1e-15;
             const S big = sizeof(S) == sizeof(double) ? (S)0x1p600 : (S)0x1p60;
             S sc0 = (m < tiny) ? big : (S)1;
-            S f1 = nw[1] * sc0, f2 = nw[2] * sc0, f3 = nw[3] * sc0, cs = cn * sc0;
-            S F2 = f1 * f1 + f2 * f2 + f3 * f3;
-            if (F2 > cs * cs) {
-                S sc = (F2 > (S)0) ? cs * rsqrt(F2) : (S)0;
-                nw[1] *= sc; nw[2] *= sc; nw[3] *= sc;
+            S f1 = tmul(nw[1], sc0), f2 = tmul(nw[2], sc0), f3 = tmul(nw[3], sc0), cs = tmul(cn, sc0);
+            S F2 = tfma(f3, f3, tfma(f2, f2, tmul(f1, f1)));
+            if (F2 > tmul(cs, cs)) {
+                S sc = (F2 > (S)0) ? tmul(cs, rsqrt(F2)) : (S)0;
+                nw[1] = tmul(nw[1], sc); nw[2] = tmul(nw[2], sc); nw[3] = tmul(nw[3], sc);
             }
             long long i = ((long long)z * g.ny + y) * g.nx + x;
             N1[i] = nw[0];
@@ -590,6 +610,49 @@ transport_batch_kernel(const BatchItem *__restrict__ items, const BatchBox *__re
     }
 }
 
+// The same over both tile shapes in one launch: CTAs [0, n_shape0) take the
+// 32 x 8 items, the rest the 16 x 16 ones (1-D blocks of 256 threads, the
+// larger of the two shared-memory layouts).
+template <typename S, int FLUX>
+__global__ void __launch_bounds__(256)
+transport_batch_all_kernel(const BatchItem *__restrict__ items, const BatchBox *__restrict__ boxes, S c, S dtdx,
+                           double area_dt, const S *const *__restrict__ N0cls, const S *const *__restrict__ F0cls,
+                           S *const *__restrict__ N1cls, S *const *__restrict__ F1cls, const S *__restrict__ tab,
+                           double *__restrict__ part_inbox, double *__restrict__ part_out, int n_shape0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int it = blockIdx.x;
+    const BatchItem w = items[it];
+    const BatchBox b = boxes[w.box];
+    const long long base = (long long)w.grp * b.g.stride + b.cell_off;
+    const long long fbase = 3LL * w.grp * b.g.stride + b.cell_off;
+    double inbox, outflow;
+    if (it < n_shape0) {
+        PlaneSmem<S, 32, 8> &s = *reinterpret_cast<PlaneSmem<S, 32, 8> *>(smem_raw);
+        transport_tile<S, FLUX, 32, 8>(s, b.g, c, dtdx, N0cls[b.cls] + base, F0cls[b.cls] + fbase,
+                                       N1cls[b.cls] + base, F1cls[b.cls] + fbase, tab, nullptr, w.x0, w.y0, w.z0,
+                                       w.z1, inbox, outflow);
+        block_reduce2<256>(&s.red[0][0], inbox, outflow);
+    } else {
+        PlaneSmem<S, 16, 16> &s = *reinterpret_cast<PlaneSmem<S, 16, 16> *>(smem_raw);
+        transport_tile<S, FLUX, 16, 16>(s, b.g, c, dtdx, N0cls[b.cls] + base, F0cls[b.cls] + fbase,
+                                        N1cls[b.cls] + base, F1cls[b.cls] + fbase, tab, nullptr, w.x0, w.y0, w.z0,
+                                        w.z1, inbox, outflow);
+        block_reduce2<256>(&s.red[0][0], inbox, outflow);
+    }
+    if (threadIdx.x == 0) {
+        part_inbox[it] = inbox;
+        part_out[it] = outflow * area_dt;
+    }
+}
+
+template <typename S>
+constexpr int batch_all_smem()
+{
+    return (int)(sizeof(PlaneSmem<S, 32, 8>) > sizeof(PlaneSmem<S, 16, 16>) ? sizeof(PlaneSmem<S, 32, 8>)
+                                                                             : sizeof(PlaneSmem<S, 16, 16>));
+}
+
 }  // namespace
 
 int transport_grid(int n_sm, bool fp32)
@@ -612,6 +675,14 @@ void transport_init()
     cudaFuncSetAttribute(transport_kernel<double, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
     cudaFuncSetAttribute(transport_kernel_f32<RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
     cudaFuncSetAttribute(transport_kernel_f32<RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+    cudaFuncSetAttribute(transport_batch_all_kernel<double, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         batch_all_smem<double>());
+    cudaFuncSetAttribute(transport_batch_all_kernel<double, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         batch_all_smem<double>());
+    cudaFuncSetAttribute(transport_batch_all_kernel<float, RT_HLL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         batch_all_smem<float>());
+    cudaFuncSetAttribute(transport_batch_all_kernel<float, RT_GLF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         batch_all_smem<float>());
     set_smem_attr_batch<double, 32, 8>();
     set_smem_attr_batch<double, 16, 16>();
     set_smem_attr_batch<float, 32, 8>();
@@ -703,6 +774,49 @@ cudaError_t launch_transport_batch(const BatchItem *items, const BatchBox *boxes
                                static_cast<const float *>(tab), pin, pout, st);
     return launch_b<double>(items, boxes, item0, nitems, shape, flux, cr, dt, dx, N0, F0, N1, F1,
                             static_cast<const double *>(tab), pin, pout, st);
+}
+
+}  // namespace rtgb
+
+namespace rtgb {
+
+cudaError_t launch_transport_batch_all(const BatchItem *items, const BatchBox *boxes, int n_shape0, int nitems,
+                                       bool fp32, int flux, double cr, double dt, double dx, const void *const *N0,
+                                       const void *const *F0, void *const *N1, void *const *F1, const void *tab,
+                                       double *pin, double *pout, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    const double area_dt = dx * dx * dt;
+    if (fp32) {
+        using S = float;
+        const S dtdx = (S)(dt / dx);
+        auto n0 = reinterpret_cast<const S *const *>(N0);
+        auto f0 = reinterpret_cast<const S *const *>(F0);
+        auto n1 = reinterpret_cast<S *const *>(N1);
+        auto f1 = reinterpret_cast<S *const *>(F1);
+        const S *t = static_cast<const S *>(tab);
+        if (flux == RT_HLL)
+            transport_batch_all_kernel<S, RT_HLL><<<nitems, 256, batch_all_smem<S>(), st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, t, pin, pout, n_shape0);
+        else
+            transport_batch_all_kernel<S, RT_GLF><<<nitems, 256, batch_all_smem<S>(), st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, t, pin, pout, n_shape0);
+    } else {
+        using S = double;
+        const S dtdx = (S)(dt / dx);
+        auto n0 = reinterpret_cast<const S *const *>(N0);
+        auto f0 = reinterpret_cast<const S *const *>(F0);
+        auto n1 = reinterpret_cast<S *const *>(N1);
+        auto f1 = reinterpret_cast<S *const *>(F1);
+        const S *t = static_cast<const S *>(tab);
+        if (flux == RT_HLL)
+            transport_batch_all_kernel<S, RT_HLL><<<nitems, 256, batch_all_smem<S>(), st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, t, pin, pout, n_shape0);
+        else
+            transport_batch_all_kernel<S, RT_GLF><<<nitems, 256, batch_all_smem<S>(), st>>>(
+                items, boxes, (S)cr, dtdx, area_dt, n0, f0, n1, f1, t, pin, pout, n_shape0);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace rtgb
