@@ -42,7 +42,9 @@ PASS1_ATTEMPTS = 6
 DRAIN1_BUDGET = 128
 # DRAM bytes (read + write) per launch, from the ncu captures of the current
 # kernels summarised in profiles/ (128^3 x 3 groups, HLL)
-TRAFFIC = {"transport": 399427072 + 192599552}
+TRAFFIC = {"transport": 399427072 + 192599552,
+           # the two drains and thermo_hard of one step (the phase's three kernels)
+           "thermo_drain": 830720 + 77568 + 594688 + 5888}
 
 
 def _op_counts():
@@ -439,7 +441,8 @@ def main():
         fpa = th_ops["flop"]
         ach = fpa * att_per_launch / (ms_launch / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s",
-                "frac": ach / fp64_peak, "traffic": TRAFFIC.get(dominant),
+                "frac": ach / fp64_peak,
+                "traffic": TRAFFIC.get(dominant) if w.name == "cosmo128_s7" else None,
                 "kernel": dominant + " (two lane-per-cell drains + warp-per-cell thermo_hard)"
                 if dominant == "thermo_drain" else dominant,
                 "peak_kind": "measured (cuBLAS DGEMM, FP64)",
