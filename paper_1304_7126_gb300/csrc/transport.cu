@@ -54,6 +54,36 @@ __device__ __forceinline__ float tsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// 1/d for d > 0: in FP64 an FP32 reciprocal of d (the conversions through
+// integer operations, so nothing but the Newton steps uses the FP64 pipe)
+// refined by two Newton steps (within an ulp; the FP64 transport is bound
+// by its FP64 instructions, and the IEEE quotient takes about twice as
+// many); d outside the float range takes the IEEE quotient.  In FP32 the
+// hardware's approximate reciprocal.
+__device__ __forceinline__ float f32_of(double x)   // nearest float, x a normal float magnitude
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long a = (b & 0x7fffffffffffffffULL) + 0x10000000ULL;
+    return __uint_as_float(((unsigned)(b >> 63) << 31) | ((unsigned)((a >> 52) - 896) << 23) |
+                           (unsigned)((a >> 29) & 0x7fffff));
+}
+__device__ __forceinline__ double f64_of(float f)   // exact, f a normal float
+{
+    const unsigned u = __float_as_uint(f);
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)(((u >> 23) & 0xff) + 896) << 52) |
+                                            ((unsigned long long)(u & 0x7fffff) << 29)));
+}
+__device__ __forceinline__ double trcp(double d)
+{
+    const unsigned long long e = ((unsigned long long)__double_as_longlong(d) >> 52) & 0x7ff;
+    if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / d;   // |d| outside [2^-120, 2^121)
+    double r = f64_of(__fdividef(1.0f, f32_of(d)));
+    r = __fma_rn(r, __fma_rn(-d, r, 1.0), r);
+    return __fma_rn(r, __fma_rn(-d, r, 1.0), r);
+}
+__device__ __forceinline__ float trcp(float d) { return __fdividef(1.0f, d); }
+
 template <typename S>
 __device__ __forceinline__ void hll_lookup(const S *__restrict__ tab, S f, S mu, S &lo, S &hi)
 {
@@ -98,11 +128,11 @@ __device__ __forceinline__ void closure(S N, S Fx, S Fy, S Fz, S c, const S *__r
     S f = 0, nx = 0, ny = 0, nz = 0;
     if (N > (S)kClosureFloorN && F2 > (S)0) {
         S inv = rsqrt(F2);
-        f = fmin(tmul(F2, inv) / tmul(tmul(c, N), sc), (S)1);
+        f = fmin(tmul(tmul(F2, inv), trcp(tmul(tmul(c, N), sc))), (S)1);
         nx = tmul(gx, inv); ny = tmul(gy, inv); nz = tmul(gz, inv);
     }
     S f2 = tmul(f, f);
-    S chi = tfma((S)4, f2, (S)3) / tfma((S)2, sqrt(tfma((S)-3, f2, (S)4)), (S)5);
+    S chi = tmul(tfma((S)4, f2, (S)3), trcp(tfma((S)2, sqrt(tfma((S)-3, f2, (S)4)), (S)5)));
     S cN = tmul(tmul(c, c), N);
     S ch = tmul(cN, (S)0.5);
     S ca = tmul(ch, tsub((S)1, chi));
@@ -144,7 +174,7 @@ __device__ __forceinline__ void face_flux(const CellQ<S> &L, const CellQ<S> &R, 
         S lm = fmin((S)0, fmin(L.lmin[D], R.lmin[D]));
         S den = tsub(lp, lm);
         if (den > (S)0) {
-            S inv = (S)1 / den;
+            S inv = trcp(den);
             S pm = tmul(lp, lm);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
