@@ -169,11 +169,13 @@ __device__ __forceinline__ F2 sqrt2(F2 a)
 }
 
 // ---- elementary functions ----
-// The three functions below are out of line: inlined at every call site of
-// every thermochemistry kernel they made ptxas run for tens of minutes.
+// exp2d, log2f2 and log1pd are called out of line: inlined at every call
+// site of every thermochemistry kernel they made ptxas run for tens of
+// minutes.  The warp path of the rates (one call site per temperature)
+// inlines exp2d_inl and log2f2_inl, the same arithmetic.
 
 // e^x of a pair; a double result (subnormal, 0 and infinity as CUDA's exp)
-static __device__ __noinline__ double exp2d(F2 x)
+__device__ __forceinline__ double exp2d_inl(F2 x)
 {
     if (!(x.hi > -745.2f)) return (x.hi != x.hi) ? (double)x.hi : 0.0;
     if (x.hi > 709.78f) return __longlong_as_double(0x7ff0000000000000LL);
@@ -203,8 +205,10 @@ static __device__ __noinline__ double exp2d(F2 x)
     return ldexp(yd, m);
 }
 
+static __device__ __noinline__ double exp2d(F2 x) { return exp2d_inl(x); }
+
 // ln of a positive normal pair
-static __device__ __noinline__ F2 log2f2(F2 v)
+__device__ __forceinline__ F2 log2f2_inl(F2 v)
 {
     const unsigned bits = __float_as_uint(v.hi);
     const int e = (int)(bits >> 23) - 127;
@@ -232,6 +236,8 @@ static __device__ __noinline__ F2 log2f2(F2 v)
     s = add(s, F2{L.x, L.y});
     return add(s, q);
 }
+
+static __device__ __noinline__ F2 log2f2(F2 v) { return log2f2_inl(v); }
 
 // ln x of a double
 __device__ __forceinline__ F2 logd(double x)

@@ -236,7 +236,7 @@ struct TLevel {
     double invTd;
     float lnTf, invTf;
 };
-template <bool MIX>
+template <bool MIX, bool INL = false>
 __device__ __forceinline__ void t_level(double T, TLevel &L)
 {
     using namespace dfm;
@@ -250,13 +250,13 @@ __device__ __forceinline__ void t_level(double T, TLevel &L)
         L.invT = split_any(L.invTd);
     } else {
         const F2 T2 = split(T);
-        L.lnT = log2f2(T2);
+        L.lnT = INL ? log2f2_inl(T2) : log2f2(T2);
         L.invT = rcp(T2);
         L.invTd = to_double(L.invT);
     }
 }
 // the same from 1/T as a pair
-template <bool MIX>
+template <bool MIX, bool INL = false>
 __device__ __forceinline__ void t_level_inv(dfm::F2 invT, TLevel &L)
 {
     using namespace dfm;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void t_level_inv(dfm::F2 invT, TLevel &L)
     } else {
         L.invT = invT;
         L.invTd = to_double(invT);
-        if (invT.hi > 0.0f && splittable(L.invTd)) L.lnT = neg(log2f2(invT));
+        if (invT.hi > 0.0f && splittable(L.invTd)) L.lnT = neg(INL ? log2f2_inl(invT) : log2f2(invT));
         else L.lnT = split_any(-log(L.invTd));
     }
 }
@@ -395,8 +395,11 @@ __device__ __forceinline__ void rate_lane(const TLevel &L, int case_b, double &f
     if constexpr (MIX) {
         rate_value_f(q, L.lnTf, L.invTf, f, df);
     } else {
+        using namespace dfm;
         double sg;
-        f = rate_value(q, L, sg);
+        const F2 l = rate_softplus(q, L, sg);
+        const F2 arg = add(add(add(q.c0, mul(L.lnT, q.c1)), mul(L.invT, q.c2)), neg(mul(l, q.c3)));
+        f = rmul(q.Cc, exp2d_inl(arg));
         df = rate_deriv(q, L.invTd, f, sg);
     }
 }
@@ -565,7 +568,7 @@ __device__ __forceinline__ void cooling_warp(int case_b, double comp, double tg,
                                              double &L, double &dL)
 {
     TLevel Lv;
-    t_level<MIX>(T, Lv);
+    t_level<MIX, true>(T, Lv);
     double f, df;
     rate_lane<MIX>(Lv, case_b, f, df);
     double n[NSP];

@@ -179,7 +179,7 @@ template <bool WARP, bool MIX>
 __device__ __forceinline__ void get_rates(double T, int case_b, unsigned needF, unsigned needD, Rates &r)
 {
     TLevel L;
-    t_level<MIX>(T, L);
+    t_level<MIX, WARP>(T, L);
     rates_at<WARP, MIX>(L, case_b, needF, needD, r);
 }
 // Rates at T = (T/mu') mu_j given 1/mu_j = md and 1/(T/mu') = iT as a pair
@@ -205,7 +205,7 @@ __device__ __forceinline__ void rates_mu(double md, dfm::F2 iT, double, int case
                                          unsigned needD, Rates &r)
 {
     TLevel L;
-    t_level_inv<MIX>(dfm::mul(dfm::split_any(md), iT), L);
+    t_level_inv<MIX, WARP>(dfm::mul(dfm::split_any(md), iT), L);
     rates_at<WARP, MIX>(L, case_b, needF, needD, r);
 }
 
