@@ -229,22 +229,17 @@ static __device__ const RateFnTab g_rate_fn[2] = {make_rate_fns(0), make_rate_fn
 static __device__ const int g_cool_sp[16] = {SP_HI, SP_HI, SP_HII, SP_FF, SP_HEI, SP_HEII, SP_HEII, SP_HEII,
                                              SP_HEII, SP_HEII, SP_HEIII, 0, 0, 0, 0, 0};
 
-// ln T and 1/T of one temperature: as pairs and 1/T as a double (FP64
-// path), as floats (FP32 path)
+// ln T and 1/T of one temperature as pairs, 1/T as a double (both paths:
+// the FP32 one needs ln T and 1/T to better than a float, see rate_value_f)
 struct TLevel {
     dfm::F2 lnT, invT;
     double invTd;
-    float lnTf, invTf;
 };
 template <bool MIX, bool INL = false>
 __device__ __forceinline__ void t_level(double T, TLevel &L)
 {
     using namespace dfm;
-    if constexpr (MIX) {
-        const float Tf = narrow(T);
-        L.lnTf = logf(Tf);
-        L.invTf = 1.0f / Tf;
-    } else if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^60 K
+    if (!(T > 0.0) || !splittable(T)) {   // not reached by T >= 1 K below 2^60 K
         L.invTd = 1.0 / T;
         L.lnT = split_any(log(T));
         L.invT = split_any(L.invTd);
@@ -260,15 +255,10 @@ template <bool MIX, bool INL = false>
 __device__ __forceinline__ void t_level_inv(dfm::F2 invT, TLevel &L)
 {
     using namespace dfm;
-    if constexpr (MIX) {
-        L.invTf = invT.hi;
-        L.lnTf = -logf(L.invTf);
-    } else {
-        L.invT = invT;
-        L.invTd = to_double(invT);
-        if (invT.hi > 0.0f && splittable(L.invTd)) L.lnT = neg(INL ? log2f2_inl(invT) : log2f2(invT));
-        else L.lnT = split_any(-log(L.invTd));
-    }
+    L.invT = invT;
+    L.invTd = to_double(invT);
+    if (invT.hi > 0.0f && splittable(L.invTd)) L.lnT = neg(INL ? log2f2_inl(invT) : log2f2(invT));
+    else L.lnT = split_any(-log(L.invTd));
 }
 // f(T) of one function given l = softplus(z); all FP64 products rounded as
 // written
@@ -294,19 +284,26 @@ __device__ __forceinline__ double rate_deriv(const RateFn &q, double invT, doubl
     return rmul(f, rmul(rfma(-q.d34, sig, rfma(-q.d2, invT, q.d1)), invT));
 }
 
-// FP32 (the mixed-precision thermochemistry, RT_MIXED32): the same form in
-// single precision (the pairs' high parts), widened through integer
-// operations and scaled by Cc in FP64; relative accuracy ~1e-6.
-__device__ __forceinline__ void rate_value_f(const RateFn &q, float lnT, float invT, double &f, double &df)
+// FP32 (the mixed-precision thermochemistry, RT_MIXED32): the argument is
+// still formed in pairs (it reaches |20-60|, where a float's rounding alone
+// is 1e-6 of the rate, and over thousands of sub-steps that moved N by 2e-4
+// of the FP64 result), but the softplus correction ln(1 + e^-|z|) < ln 2
+// and the exponential run in FP32: e^arg = e^hi (1 + lo) with the float
+// exp of the high part; the log-derivative in FP32.  Relative accuracy
+// ~2e-7.
+__device__ __forceinline__ void rate_value_f(const RateFn &q, const TLevel &L, double &f, double &df)
 {
-    const float z = __fmaf_rn(q.c4.hi, lnT, q.c5.hi);
-    const float e = __expf(-fabsf(z));
-    const float l = fmaxf(z, 0.0f) + log1pf(e);
-    const float sg = (z >= 0.0f ? 1.0f : e) / (1.0f + e);
-    const float arg = __fmaf_rn(-q.c3.hi, l, __fmaf_rn(q.c2.hi, invT, __fmaf_rn(q.c1.hi, lnT, q.c0.hi)));
-    f = rmul(q.Cc, dfm::widen(expf(arg)));
-    const float g = __fmul_rn(__fmaf_rn(-q.g34, sg, __fmaf_rn(-q.c2.hi, invT, q.c1.hi)), invT);
-    df = rmul(f, dfm::widen(g));
+    using namespace dfm;
+    const F2 z = add(mul(L.lnT, q.c4), q.c5);
+    const float e = __expf(-fabsf(z.hi));
+    const float sg = (z.hi >= 0.0f ? 1.0f : e) / (1.0f + e);
+    const F2 l = add(z.hi >= 0.0f ? z : F2{0.0f, 0.0f}, log1pf(e));   // softplus = max(z, 0) + ln(1 + e^-|z|)
+    const F2 arg = add(add(add(q.c0, mul(L.lnT, q.c1)), mul(L.invT, q.c2)), neg(mul(l, q.c3)));
+    const double eh = widen(expf(arg.hi));
+    f = rmul(q.Cc, rfma(eh, widen(arg.lo), eh));
+    const float x = L.invT.hi;
+    const float g = __fmul_rn(__fmaf_rn(-q.g34, sg, __fmaf_rn(-q.c2.hi, x, q.c1.hi)), x);
+    df = rmul(f, widen(g));
 }
 // values (and derivatives) of several functions at one temperature
 template <typename S>
@@ -381,7 +378,7 @@ __device__ __forceinline__ void rates_serial_f(const TLevel &L, int case_b, unsi
     for (int k = 0; k < NRF; ++k) {
         if (needF & rf_bit(k)) {
             double df;
-            rate_value_f(R.f[k], L.lnTf, L.invTf, r.f[k], df);
+            rate_value_f(R.f[k], L, r.f[k], df);
             if (needD & rf_bit(k)) r.df[k] = df;
         }
     }
@@ -393,7 +390,7 @@ __device__ __forceinline__ void rate_lane(const TLevel &L, int case_b, double &f
 {
     const RateFn &q = g_rate_fn[case_b].f[threadIdx.x & 31];
     if constexpr (MIX) {
-        rate_value_f(q, L.lnTf, L.invTf, f, df);
+        rate_value_f(q, L, f, df);
     } else {
         using namespace dfm;
         double sg;
