@@ -42,7 +42,7 @@ PASS1_ATTEMPTS = 6
 DRAIN1_BUDGET = 128
 # DRAM bytes (read + write) per launch, from the ncu captures of the current
 # kernels summarised in profiles/ (128^3 x 3 groups, HLL)
-TRAFFIC = {"transport": 399427072 + 192599552,
+TRAFFIC = {"transport": 399187712 + 192541696,
            # the two drains and thermo_hard of one step (the phase's three kernels)
            "thermo_drain": 830720 + 77568 + 594688 + 5888}
 
