@@ -343,6 +343,20 @@ int rt_thermo_step_noalloc(long long ncells, int n_groups, const rt_options *opt
  * fn or null arrays. */
 int rt_fmath_eval(int fn, long long n, const double *x, double *y, void *stream);
 
+/* Host-side copy of the thermochemistry's rate functions (App. A rate
+ * fits, Cen 1992, Hui & Gnedin 1997, Black 1981, the cooling terms of Eq.
+ * (rate_cooling)), each evaluated on the GPU as
+ *     f(T) = Cc exp(c0 + c1 ln T + c2 / T - c3 ln(1 + exp(c4 ln T + c5))):
+ * out [32][7] = (Cc, c0, c1, c2, c3, c4, c5) per slot, the constants as the
+ * kernels hold them (c0..c5 as the sums of their float pairs).  Slots 0..10:
+ * the cooling terms zeta_HI, psi_HI, eta_HII, theta, zeta_HeI, zeta_HeII,
+ * psi_HeII, eta_HeII, the two omega_HeII terms, eta_HeIII (erg cm^3 s^-1,
+ * times their density); 16..21: beta_HI, alpha_HII, beta_HeI, beta_HeII,
+ * alpha_HeII, alpha_HeIII (cm^3 s^-1); the others zero.  case_b: 1 the
+ * case-B recombination fits, 0 case A.  Needs no GPU.  RT_EINVAL for a bad
+ * case or a null out. */
+int rt_rate_functions(int case_b, double *out);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 int rt_version(void);
 

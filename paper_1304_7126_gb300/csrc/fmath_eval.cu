@@ -1,10 +1,12 @@
 // rt_fmath_eval: the double-float exp, log, log1p, reciprocal, square root,
 // and softplus with its derivative of dfmath.cuh (the ones the FP64
 // thermochemistry uses) over a device array of doubles, so
-// that their accuracy can be checked against CUDA's own.
+// that their accuracy can be checked against CUDA's own; rt_rate_functions:
+// the rate-function table of rates.cuh, for host-side checks.
 #include <cuda_runtime.h>
 
 #include "dfmath.cuh"
+#include "rates.cuh"
 #include "rt.h"
 
 namespace rtgb {
@@ -48,5 +50,25 @@ extern "C" int rt_fmath_eval(int fn, long long n, const double *x, double *y, vo
     if (blocks > 4096) blocks = 4096;
     rtgb::fmath_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(fn, n, x, y);
     if (cudaGetLastError() != cudaSuccess) return RT_ECUDA;
+    return RT_OK;
+}
+
+extern "C" int rt_rate_functions(int case_b, double *out)
+{
+    using namespace rtgb;
+    if ((case_b != 0 && case_b != 1) || !out) return RT_EINVAL;
+    static constexpr RateFnTab tab[2] = {make_rate_fns(0), make_rate_fns(1)};
+    auto d = [](dfm::F2 v) { return (double)v.hi + (double)v.lo; };
+    for (int k = 0; k < 32; ++k) {
+        const RateFn &q = tab[case_b].f[k];
+        double *o = out + 7 * k;
+        o[0] = q.Cc;
+        o[1] = d(q.c0);
+        o[2] = d(q.c1);
+        o[3] = d(q.c2);
+        o[4] = d(q.c3);
+        o[5] = d(q.c4);
+        o[6] = d(q.c5);
+    }
     return RT_OK;
 }

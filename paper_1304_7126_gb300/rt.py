@@ -110,9 +110,11 @@ def load(build: bool = True):
     L.rt_set_profiling.argtypes = [vp, C.c_int]
     L.rt_get_profile.argtypes = [vp, dp, dp]
     L.rt_set_thermo_routing.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_longlong]
+    L.rt_rate_functions.argtypes = [C.c_int, dp]
     for name in ("rt_create", "rt_set_stream", "rt_set_state", "rt_get_state", "rt_set_sources",
                  "rt_courant_dt", "rt_step", "rt_run", "rt_get_budget", "rt_get_subcycles", "rt_sync",
-                 "rt_hll_table", "rt_version", "rt_set_profiling", "rt_get_profile", "rt_set_thermo_routing"):
+                 "rt_hll_table", "rt_version", "rt_set_profiling", "rt_get_profile", "rt_set_thermo_routing",
+                 "rt_rate_functions"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -150,6 +152,17 @@ def rt_thermo_step_noalloc(ncells, G, opt, cr, sigN, sigE, egy, dt, state: dict,
     return load().rt_thermo_step_noalloc(int(ncells), int(G), C.byref(opt), float(cr), _ptr(sn), _ptr(se),
                                          _ptr(eg), float(dt), *[_ptr(state[k]) for k in keys],
                                          _ptr(subcycles), stream)
+
+
+def rate_functions(case_b: bool = True) -> np.ndarray:
+    """rt_rate_functions: the kernels' rate-function constants, [32][7] =
+    (Cc, c0, c1, c2, c3, c4, c5) per slot (see include/rt.h)."""
+    L = load()
+    out = np.zeros((32, 7))
+    rc = L.rt_rate_functions(int(bool(case_b)), out.ctypes.data_as(C.c_void_p))
+    if rc != RT_OK:
+        raise RuntimeError("rt_rate_functions: %d" % rc)
+    return out
 
 
 def default_options(**kw) -> rt_options:
