@@ -47,6 +47,29 @@ def test_batch_equals_single_boxes(R, prec, flux):
         single.close()
 
 
+def test_batch_both_tile_shapes_in_one_launch(R):
+    """Boxes of side 32 take the 32 x 8 tiles and the others 16 x 16 (the
+    default shapes), so one step's single transport launch runs CTAs of
+    both: every box still equals its single-box run bit for bit."""
+    from paper_1304_7126_gb300 import workloads as W
+    boxes = W.batched(3, seed0=77, steps=3, sides=(32,), flux=1) + W.batched(3, seed0=90, steps=3, sides=(20,), flux=1)
+    bt = R.RTBatch.from_workloads(boxes)
+    shapes = []
+    for i in range(len(boxes)):
+        sh, _ = bt.tiling(i)
+        shapes.append(sh)
+    assert set(shapes) == {0, 1}, shapes
+    dt = bt.courant_dt()
+    bt.run(dt, 3)
+    for i, w in enumerate(boxes):
+        single = R.RT.from_workload(w)
+        single.run(dt, 3)
+        a, b = single.get_state(), bt.get_box_state(i)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (i, k)
+        single.close()
+
+
 def test_batch_box_vs_oracle(oracle_mod, R):
     boxes = _boxes(1, n=4)
     bt = R.RTBatch.from_workloads(boxes)
