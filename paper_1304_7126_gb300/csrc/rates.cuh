@@ -55,17 +55,6 @@ struct RateTable {           // one per recombination case (A, B)
     double A_aHeII, p_aHeII;  // alpha_HeII = A (570670/T)^p
 };
 
-// S: double, or Dual (dual.cuh) when the adjoint differentiates the rates
-template <typename S>
-struct TranscT {
-    S lnT, sqrtT, invT, u;   // u = 1 / (1 + sqrt(T / 1e5))
-    S e[NEXP];
-    S l[NHG];                 // log1p(w) = softplus(z), z = ln w
-    S s[NHG];                 // w / (1 + w), the derivative of softplus at z
-    S v[NHG];                 // exp(p ln lam - s log1p(w))
-};
-using Transc = TranscT<double>;
-
 // Rate tables: exp(a ln T + b/T + c) arguments and the Hui &
 // Gnedin parameters, case A then case B; the logarithms are of the fits'
 // temperature constants and pivots.

@@ -25,14 +25,16 @@
 //                 ThermoParams::drain_budget attempts here moves to queue B
 //                 (a second stage with its own budget runs when queue B is
 //                 long);
-//   thermo_hard   persistent; one warp per queue-B cell.  On GB300 a lone
-//                 FP64 dependent chain is slow (64 cycles per FMA, ~1000 per
-//                 exp), so the lanes of the warp evaluate the cell's
-//                 twenty-odd transcendentals of each temperature in parallel
-//                 (rates.cuh, transc_warp) while the scalar update runs
-//                 redundantly in all lanes.  The arithmetic is identical to
-//                 the one-thread path, so results do not depend on which
-//                 kernel finished a cell.
+//   thermo_hard   persistent; a pair of warps per queue-C cell.  On GB300
+//                 a lone dependent chain is slow (64 cycles per FP64 FMA),
+//                 so the lanes of a warp evaluate the cell's rate and
+//                 cooling functions of one temperature in parallel (rates.cuh,
+//                 one lane each) while the scalar update runs redundantly in
+//                 all lanes, and the second warp of the pair computes the
+//                 cooling while the first updates the photons.  The
+//                 arithmetic is identical to the one-thread path, and a
+//                 queued cell carries its flux scale, so results do not
+//                 depend on which kernel finished a cell.
 // Nothing waits on another thread; each kernel ends when its queue is empty.
 // The kernels live in thermo_kernels.cuh, instantiated per precision family
 // in thermo_f64.cu, thermo_mix.cu, thermo_mix32.cu and their smoothed-RT

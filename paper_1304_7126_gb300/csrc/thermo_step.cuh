@@ -418,8 +418,9 @@ __device__ __forceinline__ bool pair_wait(volatile int *seq_other, int n, unsign
 // holds; `small` then tells whether every checked change stayed below 5%.
 // The checks |dX| / den > 0.1 go through ratio_gt / ratio_lt (a division
 // only near the threshold).
-// MIX (RT_MIXED32): rate transcendentals and absorption coefficients in
-// FP32; the photon, T/mu, x_HII and helium updates and 1 - x in FP64.
+// MIX (RT_MIXED32): the rates' softplus corrections and exponentials and
+// the absorption coefficients in FP32 (rates.cuh, rate_value_f); the
+// photon, T/mu, x_HII and helium updates and 1 - x in FP64.
 //
 // S is double, or Dual for the adjoint's differentiated recomputation
 // (values bit-identical to the double path; MIX only with double).
@@ -443,8 +444,8 @@ __device__ __forceinline__ bool attempt(const ThermoParams &p, const S &nH, cons
     S gam0 = 0.0, gam1 = 0.0, gam2 = 0.0, heat = 0.0;
 
     // cooling at T(t) and the state at t (step 2 below), first: it depends on
-    // nothing this sub-step computes, so its FP32-pipe transcendentals can
-    // overlap the FP64 photon update; kept over rejected attempts
+    // nothing this sub-step computes, so its rate functions can overlap the
+    // photon update; kept over rejected attempts
     // recombination photons without the OTSA, Eq. (cool_N_cr), at T(t) with
     // the backward abundances; group i gains C_i = sum_j [rec_g[j] == i] rj[j]
     // (before the cooling: a pair of warps updates the photons there)
