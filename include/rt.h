@@ -237,12 +237,12 @@ int rt_hll_table(int nf, int nmu, double *out);
  * step: a first pass (one thread per cell, pass1_attempts attempts), a
  * lane-per-cell drain of the cells still sub-cycling (drain_budget more
  * attempts each), a second such drain (drain2_budget) that runs only when
- * more than drain2_min_cells cells are left for it, and a warp per cell
- * for the rest.  Routing decides which kernel runs which attempts of a
- * cell, never the arithmetic of an attempt: x_HII, x_HeII, x_HeIII, T, N
- * and the attempt counts are identical for every routing, F may differ in
- * its last bits (the flux scale prod 1/(1 + h D_i) of the attempts run so
- * far is applied to F when a cell moves between kernels).  Values <= 0
+ * more than drain2_min_cells cells are left for it, and a pair of warps
+ * per cell for the rest.  Routing decides which kernel runs which attempts
+ * of a cell, never the arithmetic of an attempt: x_HII, x_HeII, x_HeIII, T,
+ * N, F and the attempt counts are identical for every routing (a queued
+ * cell carries its flux scale prod 1/(1 + h D_i), and F is formed once,
+ * when the cell finishes).  Values <= 0
  * (drain2_min_cells < 0) restore the defaults 6, 128, 128 and eight cells
  * per warp of the warp-per-cell kernel.  Takes effect at the next step. */
 int rt_set_thermo_routing(rt_handle *h, int pass1_attempts, int drain_budget, int drain2_budget,
