@@ -244,7 +244,7 @@ int rt_hll_table(int nf, int nmu, double *out);
  * cell carries its flux scale prod 1/(1 + h D_i), and F is formed once,
  * when the cell finishes).  Values <= 0
  * (drain2_min_cells < 0) restore the defaults 6, 128, 128 and eight cells
- * per warp of the warp-per-cell kernel.  Takes effect at the next step. */
+ * per warp of the tail kernel.  Takes effect at the next step. */
 int rt_set_thermo_routing(rt_handle *h, int pass1_attempts, int drain_budget, int drain2_budget,
                           long long drain2_min_cells);
 

@@ -1,4 +1,4 @@
-// Thermochemistry kernels (first pass, lane-per-cell drains, warp-per-cell
+// Thermochemistry kernels (first pass, lane-per-cell drains, pair-of-warps
 // tail) and their launch sequence, templated on the group count G, the
 // photon storage type P (double: RT_FP64; float: RT_MIXED), FP32 rate
 // transcendentals R32 (RT_MIXED32) and smoothed RT SM (Sec. 3.4).  Each
@@ -341,7 +341,7 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
     long long need = (tp.nc + 127) / 128;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    // one warp per long sub-cycler: two 4-warp blocks per SM
+    // a pair of warps per long sub-cycler: two 4-warp blocks per SM
     long long hgrid = 2LL * n_sm;
     long long hneed = (tp.nc + 3) / 4;
     if (hgrid > hneed) hgrid = hneed;
@@ -352,9 +352,10 @@ cudaError_t launch_g(const ThermoParams &tp, const double *nH, double *xHII, dou
                                                               q, d1, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // many more long sub-cyclers than the warp-per-cell kernel has warps:
-    // they share the FP64 pipes anyway, so a lane per cell does more per
-    // cycle; up to twice its warps, the warps keep each cell's path short
+    // many more long sub-cyclers than the tail kernel has pairs: they share
+    // the FP64 pipes anyway, so a lane per cell does more per cycle; up to
+    // eight cells per tail block (four per pair), the pairs keep each
+    // cell's path short
     DrainStage d2{q.b, q.a, 2, 4, tp.drain2_budget, tp.drain2_min < 0 ? 8 * hgrid : tp.drain2_min};
     thermo_drain<G, P, R32, SM><<<(unsigned)grid, 128, 0, s>>>(tp, nH, xHII, xHeII, xHeIII, T, N, F, Npre, Fpre, sub,
                                                               q, d2, status);

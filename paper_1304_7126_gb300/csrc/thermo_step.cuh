@@ -365,7 +365,7 @@ __device__ __forceinline__ bool photons_serial(const ThermoParams &p, const Cell
     return true;
 }
 
-// The two warps of a pair of the warp-per-cell kernel: while one evaluates
+// The two warps of a pair of the tail kernel (thermo_hard): while one evaluates
 // the cooling at T(t) the other updates the photons; each posts its results
 // in shared memory with a sequence number and waits (bounded) for the
 // other's.  Both then hold the same values and run the rest of the attempt
