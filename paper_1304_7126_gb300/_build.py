@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, err in res:
             print(err)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), "-shared"] + ARCH + [o for o, _ in res] + ["-o", tmp, "-lcudart"]
+    cmd = [nvcc(), "-shared"] + ARCH + [o for o, _ in res] + ["-o", tmp, "-lcudart", "-lpthread"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

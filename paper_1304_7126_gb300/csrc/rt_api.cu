@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "rt_internal.h"
+#include "state_check.h"
 
 using namespace rtgb;
 
@@ -552,26 +553,14 @@ int rt_set_state(rt_handle *h, const double *nH, const double *xHII, const doubl
     const long long nc = h->g.nc;
     const int G = h->G;
     if (!device_ptrs) {
-        for (long long c = 0; c < nc; ++c) {
-            bool ok = std::isfinite(nH[c]) && nH[c] > 0.0 && std::isfinite(xHII[c]) && xHII[c] >= 1e-6 &&
-                      xHII[c] <= 1.0 && xHeII[c] >= 0.0 && xHeIII[c] >= 0.0 && xHeII[c] + xHeIII[c] <= 1.0 &&
-                      std::isfinite(T[c]) && T[c] > 0.0;
-            if (!ok) return fail(h, RT_EINVAL, "gas state out of range at cell " + std::to_string(c));
-            for (int g = 0; g < G; ++g) {
-                double n = N[(size_t)g * nc + c];
-                double fx = F[((size_t)3 * g) * nc + c], fy = F[((size_t)3 * g + 1) * nc + c],
-                       fz = F[((size_t)3 * g + 2) * nc + c];
-                if (!(std::isfinite(n) && n >= 0.0 && std::isfinite(fx) && std::isfinite(fy) && std::isfinite(fz)))
-                    return fail(h, RT_EINVAL, "photon state not finite / negative at cell " + std::to_string(c));
-                double mx = std::max(std::max(std::fabs(fx), std::fabs(fy)), std::fabs(fz));
-                double fm = 0.0;
-                if (mx > 0.0) {
-                    double a = fx / mx, b = fy / mx, d = fz / mx;
-                    fm = mx * std::sqrt(a * a + b * b + d * d);
-                }
-                if (fm > h->cr * (n * (1.0 + 1e-8) + 1e-290))
-                    return fail(h, RT_EINVAL, "|F| > c_r N at cell " + std::to_string(c));
-            }
+        const StateView sv{nc, G, h->cr, nH, xHII, xHeII, xHeIII, T, N, F};
+        long long bad = -1;
+        switch (check_state(sv, &bad)) {
+        case kStateGas: return fail(h, RT_EINVAL, "gas state out of range at cell " + std::to_string(bad));
+        case kStatePhotons:
+            return fail(h, RT_EINVAL, "photon state not finite / negative at cell " + std::to_string(bad));
+        case kStateFlux: return fail(h, RT_EINVAL, "|F| > c_r N at cell " + std::to_string(bad));
+        default: break;
         }
     }
     cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
