@@ -75,8 +75,9 @@ typedef struct {
  * flux: RT_GLF (default) or RT_HLL.  cfl: Courant factor (0.8).
  * precision: RT_FP64; RT_MIXED (photon state and transport in FP32 with
  * compensated face sums, thermochemistry in FP64); RT_MIXED32 (as
- * RT_MIXED, with the rate transcendentals and the absorption coefficients of the
- * thermochemistry in FP32 and its updates in FP64).  a_exp: expansion
+ * RT_MIXED, with the exponentials of the rate fits and the absorption
+ * coefficients of the thermochemistry in FP32, the fits' arguments in
+ * float pairs and its updates in FP64).  a_exp: expansion
  * factor in the Compton term (1).  max_subcycles: thermochemistry attempts
  * allowed per cell and step (1e6).  smooth: 0, or 1 for smoothed RT (Sec.
  * 3.4): the change of N_i, F_i over injection and transport enters the
